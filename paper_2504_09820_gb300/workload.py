@@ -1,0 +1,151 @@
+"""Seeded synthetic MIMO detection workloads.
+
+This module is the ONE piece shared by the CUDA path's tests/bench and the CPU
+oracle: it draws inputs and holds none of the detector's arithmetic (no Gram
+matrix, no solver, no slicer).  Both sides consume the identical complex64
+arrays it returns.
+
+Channel model (Section II, eq. channel_model): H = R_r^{1/2} Omega R_t^{1/2}
+with Omega i.i.d. CN(0, 1/N) and exponential correlation r_ij = rho^|i-j|
+(real rho, so R is real symmetric Toeplitz); the square roots are the
+principal ones (symmetric, as Appendix B uses).  rho = 0 is i.i.d. Rayleigh.
+The paper's (M, N) are (N, K) here: N receive antennas, K single-antenna users.
+
+Symbols: square Gray-mapped M-QAM with unit average energy, labels drawn
+uniformly.  Noise: CN(0, sigma^2) with sigma^2 = 10^(-SNR/10) (per-stream SNR
+with E||h_k||^2 = 1; the paper does not state its convention).
+
+Storage layout (what the C ABI takes): H of one system is column-major with
+leading dimension N, complex64 interleaved, i.e. a numpy array of shape
+(batch, K, N) with H_arr[s, k, n] = H_s[n, k]; y is (batch, N) complex64.
+
+Randomness: numpy PCG64 streams seeded by SeedSequence([seed, chunk]) for
+chunks of CHUNK systems, so a chunk can be regenerated on its own.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+CHUNK = 256
+
+
+def exp_corr(n, rho):
+    """Exponential correlation matrix r_ij = rho^|i-j| (eq. 2 with real rho)."""
+    i = np.arange(n)
+    return float(rho) ** np.abs(i[:, None] - i[None, :])
+
+
+def sqrt_psd(R):
+    """Principal square root of a real symmetric positive semidefinite matrix."""
+    w, V = np.linalg.eigh(R)
+    return (V * np.sqrt(np.clip(w, 0.0, None))) @ V.T
+
+
+def gray_decode(g):
+    """Inverse of the binary-reflected Gray code, elementwise on integers."""
+    j = np.asarray(g, dtype=np.int64).copy()
+    shift = 1
+    while shift < 16:
+        j ^= j >> shift
+        shift <<= 1
+    return j
+
+
+def qam_modulate(labels, M):
+    """Gray labels (high bits: in-phase, low bits: quadrature) -> unit-energy symbols."""
+    m = int(round(np.sqrt(M)))
+    b = int(np.log2(m))
+    labels = np.asarray(labels, dtype=np.int64)
+    ji = gray_decode(labels >> b)
+    jq = gray_decode(labels & (m - 1))
+    d = 1.0 / np.sqrt(2.0 * (M - 1) / 3.0)
+    return ((2 * ji - (m - 1)) + 1j * (2 * jq - (m - 1))) * d
+
+
+def snr_to_sigma2(snr_db):
+    return 10.0 ** (-np.asarray(snr_db, dtype=np.float64) / 10.0)
+
+
+@dataclass
+class Spec:
+    """A uniform batch: every system has the same (N, K, rho, QAM order, SNR)."""
+    N: int
+    K: int
+    batch: int
+    rho: float = 0.0          # same exponential correlation at both ends
+    qam: int = 16
+    snr_db: float = 10.0
+    seed: int = 1000
+    noiseless: bool = False   # y = H x exactly (sigma^2 still reported)
+    rho_t: float = field(default=None)  # override for the user side, if given
+
+    def __post_init__(self):
+        if self.rho_t is None:
+            self.rho_t = self.rho
+
+
+def _chunk(spec, c, Rr, Rt):
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([spec.seed, c])))
+    nb = min(CHUNK, spec.batch - c * CHUNK)
+    N, K = spec.N, spec.K
+    s = np.sqrt(0.5 / N)
+    om_r = rng.standard_normal((nb, N, K)) * s
+    om_i = rng.standard_normal((nb, N, K)) * s
+    if Rr is not None:   # R_r^{1/2} Omega: one real GEMM per component
+        om_r = (Rr @ om_r.transpose(1, 0, 2).reshape(N, nb * K)).reshape(N, nb, K).transpose(1, 0, 2)
+        om_i = (Rr @ om_i.transpose(1, 0, 2).reshape(N, nb * K)).reshape(N, nb, K).transpose(1, 0, 2)
+    if Rt is not None:   # (.) R_t^{1/2}
+        om_r = (om_r.reshape(nb * N, K) @ Rt).reshape(nb, N, K)
+        om_i = (om_i.reshape(nb * N, K) @ Rt).reshape(nb, N, K)
+    Hm = (om_r + 1j * om_i).astype(np.complex64)            # (nb, N, K)
+    tx = rng.integers(0, spec.qam, size=(nb, K)).astype(np.uint8)
+    x = qam_modulate(tx, spec.qam)
+    sigma2 = float(snr_to_sigma2(spec.snr_db))
+    yc = np.einsum("bnk,bk->bn", Hm.astype(np.complex128), x)
+    if not spec.noiseless:
+        sn = np.sqrt(sigma2 / 2.0)
+        yc = yc + (rng.standard_normal((nb, N)) + 1j * rng.standard_normal((nb, N))) * sn
+    H_store = np.ascontiguousarray(Hm.transpose(0, 2, 1))   # (nb, K, N): column-major per system
+    return H_store, yc.astype(np.complex64), tx, x
+
+
+def generate(spec, chunks=None):
+    """Draw the batch (or only the listed chunks, concatenated in order).
+
+    Returns a dict with H (batch, K, N) complex64, y (batch, N) complex64,
+    tx (batch, K) uint8 Gray labels, x (batch, K) complex128 transmitted
+    symbols, sigma2 (batch,) float64, qam (batch,) int32.
+    """
+    Rr = None if spec.rho == 0 else sqrt_psd(exp_corr(spec.N, spec.rho))
+    Rt = None if spec.rho_t == 0 else sqrt_psd(exp_corr(spec.K, spec.rho_t))
+    nchunks = -(-spec.batch // CHUNK)
+    ids = range(nchunks) if chunks is None else chunks
+    parts = [_chunk(spec, c, Rr, Rt) for c in ids]
+    H = np.concatenate([p[0] for p in parts])
+    y = np.concatenate([p[1] for p in parts])
+    tx = np.concatenate([p[2] for p in parts])
+    x = np.concatenate([p[3] for p in parts])
+    n = H.shape[0]
+    return {
+        "H": H, "y": y, "tx": tx, "x": x,
+        "sigma2": np.full(n, float(snr_to_sigma2(spec.snr_db))),
+        "qam": np.full(n, spec.qam, dtype=np.int32),
+        "N": spec.N, "K": spec.K,
+    }
+
+
+# The five workloads of the detection benchmarks, by what they are.
+def c1_rayleigh_64x16(batch=1024, seed=1001):
+    """N=64, K=16, i.i.d. Rayleigh, 16-QAM, SNR 10 dB."""
+    return Spec(N=64, K=16, batch=batch, rho=0.0, qam=16, snr_db=10.0, seed=seed)
+
+
+def c2_kron_128x32(batch=8192, snr_db=10.0, seed=1002):
+    """N=128, K=32, Kronecker rho=0.5 both ends, 64-QAM, SNR 0..20 dB."""
+    return Spec(N=128, K=32, batch=batch, rho=0.5, qam=64, snr_db=snr_db, seed=seed)
+
+
+def c3_kron_256x64(batch=16384, seed=1003):
+    """N=256, K=64, Kronecker rho=0.7 both ends, 64-QAM, SNR 18 dB."""
+    return Spec(N=256, K=64, batch=batch, rho=0.7, qam=64, snr_db=18.0, seed=seed)
