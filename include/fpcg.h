@@ -1,0 +1,197 @@
+/*
+ * fpcg.h -- C ABI of libfpcg: batched finite-precision CG detection for
+ * massive MIMO on NVIDIA GB300 (sm_103a).
+ *
+ * The library implements the detectors of "Finite-Precision Conjugate
+ * Gradient Method for Massive MIMO Detection" (arXiv 2504.09820):
+ *   - LMMSE detection as the linear system A x = b with
+ *     A = H^H H + sigma^2 I and b = H^H y (Section II, eq. inversion);
+ *   - FP-CG (Algorithm 2): CG with the matrix-vector product A p at precision
+ *     u_MV, the inner products at u_IP and every other step at u_W;
+ *   - FP-BJ-CG (Algorithm 3): FP-CG left-preconditioned by the block-Jacobi
+ *     matrix M_d = diag(A_1^{-1}, ..., A_d^{-1}) of eq. pre_BJ;
+ * plus three steps the paper does not have: the Gram matrix and matched
+ * filter formed from reduced-precision H and y with fp32 accumulation, an
+ * iterative-refinement outer loop (residual b - A x at an accuracy above the
+ * working precision, correction solve, x += d), and a Gray-QAM slicer with a
+ * bit-error counter.
+ *
+ * Conventions for every entry point
+ *   - All array arguments are DEVICE pointers into memory the caller owns
+ *     (e.g. torch tensors' data_ptr()); the library never frees or keeps them.
+ *     Inputs are never modified.  Structs passed by pointer are host memory.
+ *   - Complex numbers are interleaved (re, im): "c64" is float2, "c128" is
+ *     double2.
+ *   - Letters follow the build: N = receive antennas (the paper's M),
+ *     K = users = Gram dimension (the paper's N), L = block-Jacobi block size.
+ *   - H of one system is column-major with leading dimension N: element
+ *     (n, k) of system s sits at H[(s*K + k)*N + n].  y is [batch][N].
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  The return code reports argument errors and launch
+ *     failures only; numerical trouble in a system is reported through that
+ *     system's status word and never aborts the batch.
+ *   - Entry points are thread-safe; they allocate no device memory.
+ */
+#ifndef FPCG_H
+#define FPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FPCG_API __attribute__((visibility("default")))
+#else
+#define FPCG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+enum {
+  FPCG_OK = 0,
+  FPCG_EINVAL = 1,   /* bad argument: null pointer, size out of range, K > N, K % L != 0, ... */
+  FPCG_ENOTSUP = 2,  /* valid but not supported here (e.g. fp64 mode with K > 64) */
+  FPCG_ECUDA = 3,    /* a CUDA call or kernel launch failed; see fpcg_last_cuda_error() */
+  FPCG_ENOMEM = 4    /* reserved for entry points that allocate */
+};
+
+/* Number formats (Table I of the paper, plus OCP FP8 E4M3). */
+enum {
+  FPCG_FP64 = 0,
+  FPCG_FP32 = 1,
+  FPCG_FP16 = 2,
+  FPCG_BF16 = 3,
+  FPCG_FP8E4M3 = 4
+};
+
+/* Per-system status bits (status[s]). */
+#define FPCG_ST_BREAKDOWN 1  /* phi <= 0 or a non-finite scalar: the iterate was frozen */
+#define FPCG_ST_RHO_ZERO  2  /* rho == 0: the residual vanished (e.g. y = 0); not an error */
+#define FPCG_ST_NONFINITE 4  /* the returned x_hat has a non-finite entry */
+#define FPCG_ST_BJ_FAIL   8  /* a diagonal block of A is not positive definite */
+#define FPCG_ST_BAD_QAM  16  /* qam_order[s] not in {4,16,64,256}: sym_idx left 0 */
+
+/*
+ * Precision of each step (the roles u_MV, u_IP, u_W of Algorithms 2/3).
+ *   gram   format H and y are rounded to before the Gram/matched-filter
+ *          products (FP64 | FP32 | BF16 | FP16); products and sums are fp32
+ *          (fp64 for FP64).
+ *   mv     u_MV: A and p are rounded to this format before A p, the products
+ *          are summed at fp32 (FP64 | FP32 | BF16 | FP16 | FP8E4M3; e4m3 uses
+ *          one power-of-two fp32 scale per `fp8_block` consecutive real
+ *          components of a row of A and of p).
+ *   ip     u_IP: inner products are summed at fp32 and rounded to this
+ *          format (FP32 | BF16 | FP16), or FP64 in the fp64 mode.
+ *   w      u_W: vectors x, r, p, z, the block inverses and the scalars
+ *          (FP32, or FP64 for the all-fp64 parity mode, which needs
+ *          gram = mv = ip = w = FP64 and returns x_hat as c128).
+ *   refine_steps  iterative-refinement corrections after the main solve (>= 0).
+ *   refine_iters  CG iterations of each correction solve (< 0: same as iters).
+ *   alpha_num     FP-BJ-CG only: 0 = alpha's numerator r^H p as Algorithm 3
+ *                 writes it, 1 = r^H z (textbook PCG); equal in exact arithmetic.
+ *   fp8_block     e4m3 scale block in real components; must be 32.
+ *   resid         precision of the residual b - A x of the refinement and of
+ *                 rel_res: FP64 (fp64 units), or FP32 = fp32 products and a
+ *                 compensated (double-fp32) sum, which is as accurate as fp64
+ *                 for these inputs and far cheaper on GB300.  The fp64 mode
+ *                 always uses FP64.
+ */
+typedef struct fpcg_precision {
+  int32_t gram;
+  int32_t mv;
+  int32_t ip;
+  int32_t w;
+  int32_t refine_steps;
+  int32_t refine_iters;
+  int32_t alpha_num;
+  int32_t fp8_block;
+  int32_t resid;
+} fpcg_precision;
+
+/*
+ * fpcg_detect -- FP-CG detection (Algorithm 2) of `batch` independent systems.
+ *
+ * For each system s: A = fl(H)^H fl(H) + sigma2[s] I and b = fl(H)^H fl(y)
+ * (Section II, eq. inversion; fl = rounding to prec->gram), `iters`
+ * iterations of Algorithm 2 from x0 = 0 with no stopping test (Algorithm 1's
+ * fixed iteration count), then prec->refine_steps refinement corrections,
+ * then the hard Gray-QAM decision.
+ *
+ *   H          [batch][K][N] c64 channel matrices (column-major per system)
+ *   y          [batch][N] c64 received vectors
+ *   sigma2     [batch] double noise variances (>= 0)
+ *   qam_order  [batch] int32 constellation sizes in {4,16,64,256};
+ *              may be NULL when sym_idx and bit_errors are both NULL
+ *   n_rx, k    N and K: 1 <= K <= 128, K <= N <= 65536
+ *   batch      number of systems (>= 0; 0 is a no-op apart from zeroing
+ *              *bit_errors)
+ *   iters      CG iterations of the main solve (>= 0; 0 gives x = 0 before
+ *              refinement)
+ *   prec       step precisions (host pointer, required)
+ *   x_hat      [batch][K] c64 estimates (c128 when prec->w == FPCG_FP64); required
+ *   sym_idx    [batch][K] uint8 Gray labels: in-phase bits high, quadrature
+ *              bits low; nullable
+ *   rel_res    [batch] double ||b - A x_hat||_2 / ||b||_2 (0 when b = 0); nullable
+ *   res_hist   [batch][iters+1] float ||r_i||_2 of the main solve's recursive
+ *              residual, i = 0..iters; nullable
+ *   tx_idx     [batch][K] uint8 transmitted labels; nullable (needs bit_errors)
+ *   bit_errors one unsigned 64-bit counter: set to the number of bits in
+ *              which sym_idx differs from tx_idx over the batch; nullable
+ *   status     [batch] int32 FPCG_ST_* bits; nullable
+ *   stream     cudaStream_t
+ * Errors: FPCG_EINVAL for a bad argument (nothing is launched),
+ * FPCG_ENOTSUP for the fp64 mode with K > 64, FPCG_ECUDA if a launch fails.
+ */
+FPCG_API int fpcg_detect(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+                int32_t n_rx, int32_t k, int64_t batch, int32_t iters,
+                const fpcg_precision* prec,
+                void* x_hat, uint8_t* sym_idx, double* rel_res, float* res_hist,
+                const uint8_t* tx_idx, unsigned long long* bit_errors, int32_t* status,
+                void* stream);
+
+/*
+ * fpbjcg_detect -- FP-BJ-CG detection (Algorithm 3): as fpcg_detect, with
+ * the block-Jacobi preconditioner of eq. pre_BJ built from the L x L
+ * diagonal blocks of A (inverted at u_W) and applied as z = M_d r in every
+ * iteration.  block_L must divide K and satisfy 1 <= L <= 32 (L = K is a
+ * direct block solve).  A block that is not positive definite sets
+ * FPCG_ST_BJ_FAIL and that system falls back to M_d = I.
+ */
+FPCG_API int fpbjcg_detect(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+                  int32_t n_rx, int32_t k, int64_t batch, int32_t iters, int32_t block_L,
+                  const fpcg_precision* prec,
+                  void* x_hat, uint8_t* sym_idx, double* rel_res, float* res_hist,
+                  const uint8_t* tx_idx, unsigned long long* bit_errors, int32_t* status,
+                  void* stream);
+
+/*
+ * fpcg_solve_gram -- the paper's own interface (Algorithms 1-3 take A and b
+ * as inputs): solve A x = b for `batch` Hermitian positive definite K x K
+ * systems given directly.
+ *   A      [batch][K][K] row-major, c64 (c128 when prec->w == FPCG_FP64)
+ *   b      [batch][K] same element type
+ *   block_L  0 = FP-CG (Algorithm 2), else FP-BJ-CG (Algorithm 3) with this L
+ * prec->gram is ignored; everything else as fpcg_detect.  rel_res, res_hist
+ * and status are nullable.
+ */
+FPCG_API int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t batch, int32_t iters,
+                    int32_t block_L, const fpcg_precision* prec,
+                    void* x_hat, double* rel_res, float* res_hist, int32_t* status,
+                    void* stream);
+
+/* Human-readable text for a return code (static storage). */
+FPCG_API const char* fpcg_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread in an entry point, or "". */
+FPCG_API const char* fpcg_last_cuda_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+FPCG_API int fpcg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPCG_H */

@@ -1,0 +1,151 @@
+// C ABI entry points of libfpcg: argument validation and dispatch.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/fpcg.h"
+#include "detect_simt.cuh"
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return FPCG_ECUDA;
+}
+
+bool is_fmt(int f) { return f >= FPCG_FP64 && f <= FPCG_FP8E4M3; }
+
+// Checks the precision struct; returns FPCG_OK, FPCG_EINVAL or FPCG_ENOTSUP.
+int check_prec(const fpcg_precision* p) {
+  if (!p) return FPCG_EINVAL;
+  if (!is_fmt(p->gram) || !is_fmt(p->mv) || !is_fmt(p->ip) || !is_fmt(p->w) || !is_fmt(p->resid))
+    return FPCG_EINVAL;
+  if (p->refine_steps < 0 || p->alpha_num < 0 || p->alpha_num > 1) return FPCG_EINVAL;
+  if (p->mv == FPCG_FP8E4M3 && p->fp8_block != 32) return FPCG_ENOTSUP;
+  if (p->w == FPCG_FP64) {
+    if (p->gram != FPCG_FP64 || p->mv != FPCG_FP64 || p->ip != FPCG_FP64) return FPCG_EINVAL;
+    return FPCG_OK;
+  }
+  if (p->w != FPCG_FP32) return FPCG_EINVAL;
+  if (p->gram == FPCG_FP64 || p->gram == FPCG_FP8E4M3) return FPCG_EINVAL;
+  if (p->mv == FPCG_FP64) return FPCG_EINVAL;
+  if (p->ip == FPCG_FP64 || p->ip == FPCG_FP8E4M3) return FPCG_EINVAL;
+  if (p->resid != FPCG_FP64 && p->resid != FPCG_FP32) return FPCG_EINVAL;
+  return FPCG_OK;
+}
+
+int check_device_smem(size_t need) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return need <= (size_t)optin ? FPCG_OK : FPCG_ENOTSUP;
+}
+
+int run(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+        const void* Ain, const void* bin, int32_t n_rx, int32_t k, int64_t batch, int32_t iters,
+        int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
+        double* rel_res, float* res_hist, const uint8_t* tx_idx,
+        unsigned long long* bit_errors, int32_t* status, void* stream) {
+  int rc = check_prec(prec);
+  if (rc) return rc;
+  if (k < 1 || k > 128 || batch < 0 || iters < 0) return FPCG_EINVAL;
+  if (!Ain && (n_rx < k || n_rx > 65536)) return FPCG_EINVAL;
+  if (block_L < 0 || block_L > 32 || (block_L > 0 && k % block_L)) return FPCG_EINVAL;
+  if (!x_hat) return FPCG_EINVAL;
+  if (Ain ? (!bin) : (!H || !y || !sigma2)) return FPCG_EINVAL;
+  if ((sym_idx || bit_errors) && !qam_order) return FPCG_EINVAL;
+  if ((tx_idx != nullptr) != (bit_errors != nullptr)) return FPCG_EINVAL;
+  const int fp64 = prec->w == FPCG_FP64;
+  if (fp64 && k > 64) return FPCG_ENOTSUP;
+  const int refine_iters = prec->refine_iters < 0 ? iters : prec->refine_iters;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (bit_errors) {
+    cudaError_t e = cudaMemsetAsync(bit_errors, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (batch == 0) return FPCG_OK;
+  rc = check_device_smem(fpcg::simt_smem_bytes(fp64, k, block_L, prec->mv));
+  if (rc) return rc;
+  fpcg::SimtParams P;
+  memset(&P, 0, sizeof(P));
+  P.H = (const float2*)H;
+  P.y = (const float2*)y;
+  P.sigma2 = sigma2;
+  P.qam = qam_order;
+  P.Ain = Ain;
+  P.bin = bin;
+  P.N = Ain ? k : n_rx;
+  P.K = k;
+  P.iters = iters;
+  P.L = block_L;
+  P.refine_steps = prec->refine_steps;
+  P.refine_iters = refine_iters;
+  P.alpha_num = prec->alpha_num;
+  P.gram = prec->gram;
+  P.ip = prec->ip;
+  P.resid_fp64 = prec->resid == FPCG_FP64;
+  P.batch = batch;
+  P.x_hat = x_hat;
+  P.sym = sym_idx;
+  P.rel_res = rel_res;
+  P.res_hist = res_hist;
+  P.tx = tx_idx;
+  P.bit_errors = bit_errors;
+  P.status = status;
+  cudaError_t e = fpcg::launch_detect_simt(P, fp64, fp64 ? FPCG_FP64 : prec->mv, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return FPCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fpcg_detect(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+                int32_t n_rx, int32_t k, int64_t batch, int32_t iters, const fpcg_precision* prec,
+                void* x_hat, uint8_t* sym_idx, double* rel_res, float* res_hist,
+                const uint8_t* tx_idx, unsigned long long* bit_errors, int32_t* status,
+                void* stream) {
+  return run(H, y, sigma2, qam_order, nullptr, nullptr, n_rx, k, batch, iters, 0, prec, x_hat,
+             sym_idx, rel_res, res_hist, tx_idx, bit_errors, status, stream);
+}
+
+int fpbjcg_detect(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+                  int32_t n_rx, int32_t k, int64_t batch, int32_t iters, int32_t block_L,
+                  const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx, double* rel_res,
+                  float* res_hist, const uint8_t* tx_idx, unsigned long long* bit_errors,
+                  int32_t* status, void* stream) {
+  if (block_L < 1) return FPCG_EINVAL;
+  return run(H, y, sigma2, qam_order, nullptr, nullptr, n_rx, k, batch, iters, block_L, prec,
+             x_hat, sym_idx, rel_res, res_hist, tx_idx, bit_errors, status, stream);
+}
+
+int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t batch, int32_t iters,
+                    int32_t block_L, const fpcg_precision* prec, void* x_hat, double* rel_res,
+                    float* res_hist, int32_t* status, void* stream) {
+  if (!A || !b) return FPCG_EINVAL;
+  return run(nullptr, nullptr, nullptr, nullptr, A, b, k, k, batch, iters, block_L, prec, x_hat,
+             nullptr, rel_res, res_hist, nullptr, nullptr, status, stream);
+}
+
+const char* fpcg_strerror(int code) {
+  switch (code) {
+    case FPCG_OK: return "success";
+    case FPCG_EINVAL: return "invalid argument";
+    case FPCG_ENOTSUP: return "unsupported configuration";
+    case FPCG_ECUDA: return "CUDA error";
+    case FPCG_ENOMEM: return "out of device memory";
+    default: return "unknown error";
+  }
+}
+
+const char* fpcg_last_cuda_error(void) { return g_cuda_err; }
+
+int fpcg_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+"""ctypes binding of libfpcg (include/fpcg.h).
+
+The functions named like the C entry points (fpcg_detect, fpbjcg_detect,
+fpcg_solve_gram, fpcg_strerror, ...) only marshal arguments: torch CUDA
+tensors become device pointers, the current torch stream becomes the
+cudaStream_t, and a non-zero return code becomes an exception.  Every step of
+the detection runs in the library's kernels; there is no Python or CPU
+fallback, and a missing library raises.
+
+``detect`` is a convenience wrapper that allocates the outputs and calls
+fpcg_detect or fpbjcg_detect.
+"""
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfpcg.so")
+
+# format codes (FPCG_* in fpcg.h)
+FP64, FP32, FP16, BF16, FP8E4M3 = 0, 1, 2, 3, 4
+FORMAT = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16, "e4m3": FP8E4M3, "fp8": FP8E4M3}
+
+# status bits (FPCG_ST_*)
+ST_BREAKDOWN, ST_RHO_ZERO, ST_NONFINITE, ST_BJ_FAIL, ST_BAD_QAM = 1, 2, 4, 8, 16
+
+# return codes
+OK, EINVAL, ENOTSUP, ECUDA, ENOMEM = 0, 1, 2, 3, 4
+
+
+class FpcgError(RuntimeError):
+    def __init__(self, code, where):
+        msg = f"{where}: {fpcg_strerror(code)} (code {code})"
+        if code == ECUDA:
+            msg += ": " + fpcg_last_cuda_error()
+        super().__init__(msg)
+        self.code = code
+
+
+class Precision(ctypes.Structure):
+    _fields_ = [("gram", ctypes.c_int32), ("mv", ctypes.c_int32), ("ip", ctypes.c_int32),
+                ("w", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+                ("refine_iters", ctypes.c_int32), ("alpha_num", ctypes.c_int32),
+                ("fp8_block", ctypes.c_int32), ("resid", ctypes.c_int32)]
+
+
+def precision(gram="fp32", mv="fp32", ip="fp32", w="fp32", refine_steps=0, refine_iters=-1,
+              alpha_num=0, fp8_block=32, resid="fp32"):
+    """Build an fpcg_precision from format names ("fp64", "fp32", "fp16", "bf16", "e4m3")."""
+    if w == "fp64":
+        gram = mv = ip = resid = "fp64"
+    return Precision(FORMAT[gram], FORMAT[mv], FORMAT[ip], FORMAT[w], int(refine_steps),
+                     int(refine_iters), int(alpha_num), int(fp8_block), FORMAT[resid])
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+
+
+def lib():
+    """Load libfpcg.so (built in-tree by build.py); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2504_09820_gb300.build.build() (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        det = [_P, _P, _P, _P, _I32, _I32, _I64, _I32]
+        outs = [_P, _P, _P, _P, _P, _P, _P, _P]
+        L.fpcg_detect.argtypes = det + [ctypes.POINTER(Precision)] + outs
+        L.fpcg_detect.restype = ctypes.c_int
+        L.fpbjcg_detect.argtypes = det + [_I32, ctypes.POINTER(Precision)] + outs
+        L.fpbjcg_detect.restype = ctypes.c_int
+        L.fpcg_solve_gram.argtypes = [_P, _P, _I32, _I64, _I32, _I32, ctypes.POINTER(Precision),
+                                      _P, _P, _P, _P, _P]
+        L.fpcg_solve_gram.restype = ctypes.c_int
+        L.fpcg_strerror.argtypes = [ctypes.c_int]
+        L.fpcg_strerror.restype = ctypes.c_char_p
+        L.fpcg_last_cuda_error.argtypes = []
+        L.fpcg_last_cuda_error.restype = ctypes.c_char_p
+        L.fpcg_version.argtypes = []
+        L.fpcg_version.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def fpcg_strerror(code):
+    return lib().fpcg_strerror(int(code)).decode()
+
+
+def fpcg_last_cuda_error():
+    return lib().fpcg_last_cuda_error().decode()
+
+
+def fpcg_version():
+    return lib().fpcg_version()
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _xdtype(prec):
+    return torch.complex128 if prec.w == FP64 else torch.complex64
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise FpcgError(rc, where)
+
+
+def _detect_args(H, y, sigma2, qam_order, iters, prec, x_hat, sym_idx, rel_res, res_hist,
+                 tx_idx, bit_errors, status):
+    if H.dim() != 3:
+        raise ValueError("H must be [batch][K][N]")
+    batch, K, N = H.shape
+    return [_ptr(H, torch.complex64, "H"), _ptr(y, torch.complex64, "y"),
+            _ptr(sigma2, torch.float64, "sigma2"), _ptr(qam_order, torch.int32, "qam_order"),
+            int(N), int(K), int(batch), int(iters)], \
+           [ctypes.byref(prec), _ptr(x_hat, _xdtype(prec), "x_hat"),
+            _ptr(sym_idx, torch.uint8, "sym_idx"), _ptr(rel_res, torch.float64, "rel_res"),
+            _ptr(res_hist, torch.float32, "res_hist"), _ptr(tx_idx, torch.uint8, "tx_idx"),
+            _ptr(bit_errors, torch.int64, "bit_errors"), _ptr(status, torch.int32, "status")]
+
+
+def fpcg_detect(H, y, sigma2, qam_order, iters, prec, x_hat, sym_idx=None, rel_res=None,
+                res_hist=None, tx_idx=None, bit_errors=None, status=None, stream=None):
+    """Marshal a call to fpcg_detect (FP-CG, Algorithm 2); tensors on the GPU."""
+    a, b = _detect_args(H, y, sigma2, qam_order, iters, prec, x_hat, sym_idx, rel_res, res_hist,
+                        tx_idx, bit_errors, status)
+    _check(lib().fpcg_detect(*a, *b, _stream(stream)), "fpcg_detect")
+
+
+def fpbjcg_detect(H, y, sigma2, qam_order, iters, block_L, prec, x_hat, sym_idx=None,
+                  rel_res=None, res_hist=None, tx_idx=None, bit_errors=None, status=None,
+                  stream=None):
+    """Marshal a call to fpbjcg_detect (FP-BJ-CG, Algorithm 3)."""
+    a, b = _detect_args(H, y, sigma2, qam_order, iters, prec, x_hat, sym_idx, rel_res, res_hist,
+                        tx_idx, bit_errors, status)
+    _check(lib().fpbjcg_detect(*a, int(block_L), *b, _stream(stream)), "fpbjcg_detect")
+
+
+def fpcg_solve_gram(A, b, iters, block_L, prec, x_hat, rel_res=None, res_hist=None, status=None,
+                    stream=None):
+    """Marshal a call to fpcg_solve_gram (A, b given; Algorithms 2/3)."""
+    batch, K, _ = A.shape
+    dt = _xdtype(prec)
+    _check(lib().fpcg_solve_gram(_ptr(A, dt, "A"), _ptr(b, dt, "b"), int(K), int(batch),
+                                 int(iters), int(block_L), ctypes.byref(prec),
+                                 _ptr(x_hat, dt, "x_hat"), _ptr(rel_res, torch.float64, "rel_res"),
+                                 _ptr(res_hist, torch.float32, "res_hist"),
+                                 _ptr(status, torch.int32, "status"), _stream(stream)),
+           "fpcg_solve_gram")
+
+
+def detect(H, y, sigma2, qam_order, iters, prec, L=None, tx_idx=None, hist=False, stream=None):
+    """Allocate outputs and run fpcg_detect (L None) or fpbjcg_detect (L given).
+
+    Returns a dict of device tensors: x, sym, rel_res, status, and bit_errors
+    (when tx_idx is given) and hist (when requested).
+    """
+    batch, K, N = H.shape
+    dev = H.device
+    out = {
+        "x": torch.empty((batch, K), dtype=_xdtype(prec), device=dev),
+        "sym": torch.empty((batch, K), dtype=torch.uint8, device=dev),
+        "rel_res": torch.empty(batch, dtype=torch.float64, device=dev),
+        "status": torch.empty(batch, dtype=torch.int32, device=dev),
+    }
+    out["hist"] = torch.empty((batch, iters + 1), dtype=torch.float32, device=dev) if hist else None
+    out["bit_errors"] = torch.zeros(1, dtype=torch.int64, device=dev) if tx_idx is not None else None
+    kw = dict(sym_idx=out["sym"], rel_res=out["rel_res"], res_hist=out["hist"], tx_idx=tx_idx,
+              bit_errors=out["bit_errors"], status=out["status"], stream=stream)
+    if L is None:
+        fpcg_detect(H, y, sigma2, qam_order, iters, prec, out["x"], **kw)
+    else:
+        fpbjcg_detect(H, y, sigma2, qam_order, iters, L, prec, out["x"], **kw)
+    return out
