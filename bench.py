@@ -16,7 +16,6 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
 import time
 
@@ -59,44 +58,71 @@ def peaks():
 
 
 class Clocks:
-    """Sample SM clocks and throttle reasons with nvidia-smi during a region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """Sample the SM clock and the clock-event (throttle) reasons during a
+    region, through NVML's read-only queries, every ~2 ms from a thread."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, dev_index):
-        self.dev = dev_index
-        self.p = None
+    def __init__(self, torch_device):
+        self.dev = torch_device
+        self.samples = []
+        self.max_mhz = None
+        self.err = None
+
+    def _open(self):
+        import ctypes
+        import torch
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(self.dev).uuid)
+        if nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) != 0:
+            if nv.nvmlDeviceGetHandleByIndex_v2(self.dev.index, ctypes.byref(h)) != 0:
+                raise RuntimeError("no NVML handle")
+        fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        mx = ctypes.c_uint()
+        if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+            self.max_mhz = mx.value
+        return nv, h, fn
 
     def __enter__(self):
+        import ctypes
+        import threading
+        self.stop = threading.Event()
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.p = None
+            nv, h, fn = self._open()
+        except Exception as e:  # no NVML: report the region as unsampled
+            self.err = str(e)
+            self.t = None
+            return self
+
+        def poll():
+            mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+            while not self.stop.is_set():
+                if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and fn(h, ctypes.byref(rs)) == 0:
+                    self.samples.append((mhz.value, rs.value))
+                time.sleep(0.002)
+        self.nv = nv
+        self.t = threading.Thread(target=poll, daemon=True)
+        self.t.start()
+        time.sleep(0.01)
         return self
 
     def __exit__(self, *a):
-        self.out = ""
-        if self.p is not None:
-            self.p.terminate()
-            try:
-                self.out, _ = self.p.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.p.kill()
-                self.out, _ = self.p.communicate()
+        if self.t is not None:
+            self.stop.set()
+            self.t.join()
+            self.nv.nvmlShutdown()
 
     def summary(self):
-        rows = [r.split(",") for r in getattr(self, "out", "").strip().splitlines() if r.count(",") >= 8]
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"],
+                    "samples": 0, "note": self.err}
+        reasons = sorted({name for _, r in self.samples for bit, name in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples)}
 
 
 def run_reference(args):
@@ -218,7 +244,7 @@ def main():
 
     o_head = outputs()
     head = make_call(HEAD, o_head, g)
-    with Clocks(dev.index) as clk:
+    with Clocks(dev) as clk:
         total, per = timed(head, args.steps, args.warmup)
     clocks = clk.summary()
     det_s = world * B * args.steps / total
