@@ -72,6 +72,9 @@ enum {
 #define FPCG_ST_NONFINITE 4  /* the returned x_hat has a non-finite entry */
 #define FPCG_ST_BJ_FAIL   8  /* a diagonal block of A is not positive definite */
 #define FPCG_ST_BAD_QAM  16  /* qam_order[s] not in {4,16,64,256}: sym_idx left 0 */
+#define FPCG_ST_TIMEOUT  32  /* a pipeline wait of the tensor-core kernel gave up: outputs
+                                of this system are not valid (never expected; reported
+                                instead of hanging the GPU) */
 
 /*
  * Precision of each step (the roles u_MV, u_IP, u_W of Algorithms 2/3).
@@ -180,6 +183,21 @@ FPCG_API int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t ba
                     int32_t block_L, const fpcg_precision* prec,
                     void* x_hat, double* rel_res, float* res_hist, int32_t* status,
                     void* stream);
+
+/*
+ * fpcg_gram -- form the Gram matrix and matched filter only (Section II,
+ * eq. inversion): A = fl(H)^H fl(H) + sigma2[s] I and b = fl(H)^H fl(y) for
+ * every system, fl = rounding of H and y to `gram` (FPCG_BF16 or FPCG_FP16:
+ * fp32 accumulation on the tensor cores for K in {8,16,32,64}, in fp32 FMAs
+ * otherwise; FPCG_FP32: fp32; FPCG_FP64: fp64).  The Hermitian A is written in
+ * full.  Useful when one A serves many received vectors.
+ *   A       [batch][K][K] row-major, c64 (c128 for FPCG_FP64)
+ *   b       [batch][K] same element type
+ *   status  [batch] int32, nullable: 0, or FPCG_ST_TIMEOUT
+ * Other arguments as fpcg_detect.
+ */
+FPCG_API int fpcg_gram(const void* H, const void* y, const double* sigma2, int32_t n_rx, int32_t k,
+                       int64_t batch, int32_t gram, void* A, void* b, int32_t* status, void* stream);
 
 /* Human-readable text for a return code (static storage). */
 FPCG_API const char* fpcg_strerror(int code);

@@ -594,6 +594,13 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
 
   if (P.Ain) load_gram(P, S, sys);
   else gram_phase(P, S, sys);
+  if (P.A_out) {  // gram-only mode (fpcg_gram)
+    cplx<T>* Ao = (cplx<T>*)P.A_out + (size_t)sys * K * K;
+    cplx<T>* bo = (cplx<T>*)P.b_out + (size_t)sys * K;
+    for (int idx = threadIdx.x; idx < K * K; idx += NT) Ao[idx] = S.A[(idx / K) * (K + 1) + idx % K];
+    for (int k = threadIdx.x; k < K; k += NT) bo[k] = S.b[k];
+    return;
+  }
 
   if (P.L > 0 && bj_phase(P, S)) st |= 8;  // FPCG_ST_BJ_FAIL
   if (MV == E4M3) {

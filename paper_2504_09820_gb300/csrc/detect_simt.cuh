@@ -23,6 +23,8 @@ struct SimtParams {
   const uint8_t* tx;
   unsigned long long* bit_errors;
   int32_t* status;
+  void* A_out;              // gram-only mode: write A [batch][K][K] and b, then stop
+  void* b_out;
 };
 
 size_t simt_smem_bytes(int fp64, int K, int L, int mv);

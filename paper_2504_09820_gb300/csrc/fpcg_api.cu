@@ -5,6 +5,7 @@
 
 #include "../../include/fpcg.h"
 #include "detect_simt.cuh"
+#include "gram_tc.cuh"
 
 namespace {
 
@@ -44,6 +45,15 @@ int check_device_smem(size_t need) {
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return cuda_fail(e);
   return need <= (size_t)optin ? FPCG_OK : FPCG_ENOTSUP;
+}
+
+int device_sms(int* sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return FPCG_OK;
 }
 
 int run(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
@@ -131,6 +141,53 @@ int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t batch, int3
   if (!A || !b) return FPCG_EINVAL;
   return run(nullptr, nullptr, nullptr, nullptr, A, b, k, k, batch, iters, block_L, prec, x_hat,
              nullptr, rel_res, res_hist, nullptr, nullptr, status, stream);
+}
+
+int fpcg_gram(const void* H, const void* y, const double* sigma2, int32_t n_rx, int32_t k,
+              int64_t batch, int32_t gram, void* A, void* b, int32_t* status, void* stream) {
+  if (!H || !y || !sigma2 || !A || !b) return FPCG_EINVAL;
+  if (k < 1 || k > 128 || n_rx < k || n_rx > 65536 || batch < 0) return FPCG_EINVAL;
+  if (gram != FPCG_FP64 && gram != FPCG_FP32 && gram != FPCG_BF16 && gram != FPCG_FP16) return FPCG_EINVAL;
+  if (gram == FPCG_FP64 && k > 64) return FPCG_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (status) {
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)batch, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (batch == 0) return FPCG_OK;
+  if ((gram == FPCG_BF16 || gram == FPCG_FP16) && fpcg::gram_tc_supported(k)) {
+    int sms = 0;
+    int rc = device_sms(&sms);
+    if (rc) return rc;
+    rc = check_device_smem(fpcg::gram_tc_smem_bytes());
+    if (rc) return rc;
+    fpcg::GramTcParams P;
+    P.pipe = fpcg::make_pipe((const float2*)H, (const float2*)y, n_rx, k, batch, gram == FPCG_BF16);
+    P.sigma2 = sigma2;
+    P.A = (float2*)A;
+    P.b = (float2*)b;
+    P.status = status;
+    cudaError_t e = fpcg::launch_gram_tc(P, sms, s);
+    return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+  }
+  const int fp64 = gram == FPCG_FP64;
+  int rc = check_device_smem(fpcg::simt_smem_bytes(fp64, k, 0, FPCG_FP32));
+  if (rc) return rc;
+  fpcg::SimtParams P;
+  memset(&P, 0, sizeof(P));
+  P.H = (const float2*)H;
+  P.y = (const float2*)y;
+  P.sigma2 = sigma2;
+  P.N = n_rx;
+  P.K = k;
+  P.gram = gram;
+  P.ip = FPCG_FP32;
+  P.batch = batch;
+  P.A_out = A;
+  P.b_out = b;
+  P.x_hat = A;  // unused in gram-only mode
+  cudaError_t e = fpcg::launch_detect_simt(P, fp64, fp64 ? FPCG_FP64 : FPCG_FP32, s);
+  return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
 }
 
 const char* fpcg_strerror(int code) {

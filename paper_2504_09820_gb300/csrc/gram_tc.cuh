@@ -1,0 +1,25 @@
+// Internal interface of the tensor-core Gram kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "tc_pipeline.cuh"
+
+namespace fpcg {
+
+struct GramTcParams {
+  tcp::Pipe pipe;
+  const double* sigma2;
+  float2* A;        // [batch][K][K] row-major
+  float2* b;        // [batch][K]
+  int32_t* status;  // nullable: FPCG_ST_TIMEOUT for systems a timed-out CTA left
+};
+
+bool gram_tc_supported(int K);
+size_t gram_tc_smem_bytes();
+tcp::Pipe make_pipe(const float2* H, const float2* y, int N, int K, int64_t batch, int bf16);
+cudaError_t launch_gram_tc(const GramTcParams& P, int num_sms, cudaStream_t stream);
+
+}  // namespace fpcg

@@ -1,0 +1,262 @@
+// The tensor-core Gram pipeline shared by the Gram-only and the fused
+// detection kernels.
+//
+// Real embedding.  For one system with N antennas and K users, the rows of
+// the K-major operand are X^T[2k] = Re h_k and X^T[2k+1] = Im h_k (h_k = column
+// k of H, length N, the reduction axis), and two more rows hold Re y and Im y.
+// One UMMA product D = X^T [X | Y] (M = 128 rows, N_mma = 128 + 16 columns,
+// K = antennas) then contains, with D[i][j] = sum_n row_i[n] row_j[n]:
+//   Re A_kl = D[2k][2l] + D[2k+1][2l+1]      Im A_kl = D[2k][2l+1] - D[2k+1][2l]
+//   Re b_k  = D[2k][Y0] + D[2k+1][Y1]        Im b_k  = D[2k][Y1]   - D[2k+1][Y0]
+// (Section II, eq. inversion: A = H^H H, b = H^H y; sigma^2 is added after).
+// Rows 2k and 2k+1 live in adjacent TMEM lanes, so one shuffle per column pair
+// combines them.  P = floor(64/K) systems are packed into one 128-row tile
+// (they are consecutive columns of the [batch*K][N] matrix); their cross blocks
+// of D are ignored.  Operands are bf16 or fp16 (the u_gram rounding), the
+// accumulator fp32.
+//
+// Stages: 64 antennas each, rows of 128 bytes in the 128B-swizzled K-major
+// layout, 144 rows (128 of X, 16 of Y) = 18 KiB.  Roles:
+//   converter warps: coalesced 16-byte loads of H and y, round to bf16/fp16,
+//                    store into the stage, fence.proxy.async, arrive `full`;
+//   MMA thread:      wait `full`, 4 UMMAs (K = 16 each), commit to `empty`;
+//                    after a tile's last stage commit to `acc_full`;
+//   drain warps:     wait `acc_full`, tcgen05.ld, combine, consume, arrive
+//                    `acc_empty`.
+// Every wait is bounded; a timeout raises the CTA's abort flag and all roles
+// leave their loops.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "tc.cuh"
+
+namespace fpcg {
+namespace tcp {
+
+constexpr int kStages = 4;
+constexpr int kStageRows = 144;
+constexpr int kStageBytes = kStageRows * 128;  // 18432, a multiple of 1024
+constexpr int kChunk = 64;                     // antennas per stage
+constexpr int kConvWarps = 8;
+constexpr int kMmaN = 144;
+constexpr int kAccCols = 256;                  // TMEM columns per accumulator buffer
+
+struct Pipe {
+  const float2* H;
+  const float2* y;
+  int N, K, P, nchunks;
+  int64_t batch, ntiles;
+  int bf16;
+  int vec4;  // 16-byte loads allowed (N even, 16-byte aligned bases)
+};
+
+struct Bars {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t done;
+};
+
+__device__ __forceinline__ uint32_t pack2(float a, float b, int bf16) {
+  if (bf16) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Load two consecutive complex samples v[n], v[n+1] of a length-N vector
+// (zero beyond N or when !valid).
+__device__ __forceinline__ float4 load2(const float2* v, int n, int N, bool valid, int vec4) {
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!valid) return r;
+  if (vec4 && n + 1 < N) return __ldcs(reinterpret_cast<const float4*>(v + n));
+  if (n < N) {
+    float2 a = __ldcs(v + n);
+    r.x = a.x;
+    r.y = a.y;
+  }
+  if (n + 1 < N) {
+    float2 b = __ldcs(v + n + 1);
+    r.z = b.x;
+    r.w = b.y;
+  }
+  return r;
+}
+
+// Converter warp `cw` (0..7): its columns of the tile are cl = cw + 8 m.
+struct ConvRegs {
+  float4 h[8];
+  float4 y;
+};
+
+__device__ __forceinline__ void conv_load(const Pipe& p, int64_t tile, int c, int cw, int lane, ConvRegs& R) {
+  const int n = c * kChunk + 2 * lane;
+  const int64_t col0 = tile * (int64_t)(p.P * p.K);
+  const int64_t ncols = p.batch * (int64_t)p.K;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int cl = cw + 8 * m;
+    const int64_t col = col0 + cl;
+    const bool ok = cl < p.P * p.K && col < ncols;
+    R.h[m] = load2(p.H + (ok ? col : 0) * (int64_t)p.N, n, p.N, ok, p.vec4);
+  }
+  const int64_t sys = tile * p.P + cw;  // converter warp cw also loads y of system cw of the tile
+  const bool oky = cw < p.P && sys < p.batch;
+  R.y = load2(p.y + (oky ? sys : 0) * (int64_t)p.N, n, p.N, oky, p.vec4);
+}
+
+__device__ __forceinline__ void conv_store(const Pipe& p, uint8_t* stage, int cw, int lane, const ConvRegs& R) {
+  // k-positions 2*lane, 2*lane+1 of the 64-antenna chunk
+  const uint32_t kpos = 2u * lane;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int cl = cw + 8 * m;
+    if (cl < p.P * p.K) {
+      const float4 v = R.h[m];
+      *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(2 * cl, kpos)) = pack2(v.x, v.z, p.bf16);
+      *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(2 * cl + 1, kpos)) = pack2(v.y, v.w, p.bf16);
+    }
+  }
+  if (cw < p.P) {
+    const float4 v = R.y;
+    *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(128 + 2 * cw, kpos)) = pack2(v.x, v.z, p.bf16);
+    *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(129 + 2 * cw, kpos)) = pack2(v.y, v.w, p.bf16);
+  }
+}
+
+// Converter role: tiles this CTA owns are tile0, tile0 + tstep, ...
+__device__ inline void converter_role(const Pipe& p, uint8_t* stages, Bars& B, volatile int* abort,
+                                      int64_t tile0, int64_t tstep, int cw, int lane) {
+  ConvRegs cur, nxt;
+  int64_t j = 0;
+  int c = 0;
+  int64_t tile = tile0;
+  if (tile >= p.ntiles) return;
+  conv_load(p, tile, c, cw, lane, cur);
+  uint32_t u = 0;  // stage use counter
+  while (true) {
+    // prefetch the next chunk's loads before waiting for the stage
+    int c2 = c + 1;
+    int64_t tile2 = tile, j2 = j;
+    if (c2 == p.nchunks) {
+      c2 = 0;
+      tile2 = tile + tstep;
+      ++j2;
+    }
+    const bool more = tile2 < p.ntiles;
+    if (more) conv_load(p, tile2, c2, cw, lane, nxt);
+    const uint32_t st = u % kStages, q = u / kStages;
+    if (q > 0 && !tc::mbar_wait(&B.empty[st], (q - 1) & 1u, abort)) {
+      *abort = 1;
+      return;
+    }
+    conv_store(p, stages + st * kStageBytes, cw, lane, cur);
+    tc::fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive(&B.full[st]);
+    ++u;
+    if (!more) return;
+    cur = nxt;
+    c = c2;
+    tile = tile2;
+    j = j2;
+  }
+}
+
+// MMA role (one thread).
+__device__ inline void mma_role(const Pipe& p, uint8_t* stages, Bars& B, volatile int* abort, uint32_t tmem,
+                                int64_t tile0, int64_t tstep) {
+  const uint32_t idesc = tc::idesc_f16(128, kMmaN, p.bf16 != 0);
+  uint32_t u = 0;
+  int64_t j = 0;
+  for (int64_t tile = tile0; tile < p.ntiles; tile += tstep, ++j) {
+    const uint32_t b = (uint32_t)(j & 1), qa = (uint32_t)(j >> 1);
+    if (qa > 0 && !tc::mbar_wait(&B.acc_empty[b], (qa - 1) & 1u, abort)) {
+      *abort = 1;
+      break;
+    }
+    tc::tc_fence_after();
+    const uint32_t dt = tmem + b * kAccCols;
+    for (int c = 0; c < p.nchunks; ++c, ++u) {
+      const uint32_t st = u % kStages, q = u / kStages;
+      if (!tc::mbar_wait(&B.full[st], q & 1u, abort)) {
+        *abort = 1;
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t sa = tc::smem_u32(stages + st * kStageBytes);
+      const uint64_t d0 = tc::sdesc_k_sw128(sa);
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint64_t d = d0 + (uint64_t)(ks * 2);  // +32 bytes along K
+        tc::mma_f16(dt, d, d, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+      }
+      tc::mma_commit(&B.empty[st]);
+    }
+    if (*abort) break;
+    tc::mma_commit(&B.acc_full[b]);
+  }
+  // make sure nothing is in flight before the TMEM is released
+  tc::mma_commit(&B.done);
+  tc::mbar_wait(&B.done, 0, abort, 2000000000LL);
+}
+
+// Drain helper: for the calling thread (TMEM lane `row` of the tile) combine
+// column pairs of its own system block into A entries.  `emit(l, value)` gets
+// Re A[k][l] on even rows and Im A[k][l] on odd rows; `emit_b(value)` gets
+// Re b_k / Im b_k.  Must be called by whole warps of a warpgroup (all lanes
+// take part in the shuffles).
+template <typename EmitA, typename EmitB>
+__device__ __forceinline__ void drain_tile(const Pipe& p, uint32_t tmem_acc, int q, int lane, EmitA emit,
+                                           EmitB emit_b) {
+  const int row = 32 * q + lane;
+  const int twoK = 2 * p.K;
+  const int sys = row / twoK;         // system of this lane within the tile
+  const int blk0 = sys * twoK;        // first column of its block
+  const bool odd = row & 1;
+  const uint32_t lane_base = tmem_acc + ((uint32_t)(32 * q) << 16);
+  // columns the warp needs: its lanes' blocks
+  int c_lo, c_hi;
+  if (twoK >= 32) {
+    c_lo = (32 * q / twoK) * twoK;
+    c_hi = c_lo + twoK;
+  } else {
+    c_lo = 32 * q;
+    c_hi = 32 * q + 32;
+  }
+  for (int cb = c_lo; cb < c_hi; cb += 16) {
+    float v[16];
+    tc::tmem_ld16(lane_base + (uint32_t)cb, v);
+#pragma unroll
+    for (int m = 0; m < 16; m += 2) {
+      const float other = __shfl_xor_sync(0xffffffffu, v[m + 1], 1);
+      const int j = cb + m;
+      if (sys < p.P && j >= blk0 && j < blk0 + twoK) {
+        const int l = (j - blk0) >> 1;
+        emit(l, odd ? (other - v[m]) : (v[m] + other));
+      }
+    }
+  }
+  {
+    float v[16];
+    tc::tmem_ld16(lane_base + 128u, v);
+    float mine0 = 0.f, mine1 = 0.f;
+#pragma unroll
+    for (int m = 0; m < 16; m += 2)
+      if (m == 2 * (sys & 7)) {
+        mine0 = v[m];
+        mine1 = v[m + 1];
+      }
+    const float other = __shfl_xor_sync(0xffffffffu, mine1, 1);
+    if (sys < p.P) emit_b(odd ? (other - mine0) : (mine0 + other));
+  }
+}
+
+}  // namespace tcp
+}  // namespace fpcg

@@ -23,7 +23,7 @@ FP64, FP32, FP16, BF16, FP8E4M3 = 0, 1, 2, 3, 4
 FORMAT = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16, "e4m3": FP8E4M3, "fp8": FP8E4M3}
 
 # status bits (FPCG_ST_*)
-ST_BREAKDOWN, ST_RHO_ZERO, ST_NONFINITE, ST_BJ_FAIL, ST_BAD_QAM = 1, 2, 4, 8, 16
+ST_BREAKDOWN, ST_RHO_ZERO, ST_NONFINITE, ST_BJ_FAIL, ST_BAD_QAM, ST_TIMEOUT = 1, 2, 4, 8, 16, 32
 
 # return codes
 OK, EINVAL, ENOTSUP, ECUDA, ENOMEM = 0, 1, 2, 3, 4
@@ -77,6 +77,8 @@ def lib():
         L.fpcg_solve_gram.argtypes = [_P, _P, _I32, _I64, _I32, _I32, ctypes.POINTER(Precision),
                                       _P, _P, _P, _P, _P]
         L.fpcg_solve_gram.restype = ctypes.c_int
+        L.fpcg_gram.argtypes = [_P, _P, _P, _I32, _I32, _I64, _I32, _P, _P, _P, _P]
+        L.fpcg_gram.restype = ctypes.c_int
         L.fpcg_strerror.argtypes = [ctypes.c_int]
         L.fpcg_strerror.restype = ctypes.c_char_p
         L.fpcg_last_cuda_error.argtypes = []
@@ -169,6 +171,16 @@ def fpcg_solve_gram(A, b, iters, block_L, prec, x_hat, rel_res=None, res_hist=No
                                  _ptr(res_hist, torch.float32, "res_hist"),
                                  _ptr(status, torch.int32, "status"), _stream(stream)),
            "fpcg_solve_gram")
+
+
+def fpcg_gram(H, y, sigma2, gram, A, b, status=None, stream=None):
+    """Marshal a call to fpcg_gram (A = fl(H)^H fl(H) + sigma^2 I, b = fl(H)^H fl(y))."""
+    batch, K, N = H.shape
+    dt = torch.complex128 if FORMAT[gram] == FP64 else torch.complex64
+    _check(lib().fpcg_gram(_ptr(H, torch.complex64, "H"), _ptr(y, torch.complex64, "y"),
+                           _ptr(sigma2, torch.float64, "sigma2"), int(N), int(K), int(batch),
+                           FORMAT[gram], _ptr(A, dt, "A"), _ptr(b, dt, "b"),
+                           _ptr(status, torch.int32, "status"), _stream(stream)), "fpcg_gram")
 
 
 def detect(H, y, sigma2, qam_order, iters, prec, L=None, tx_idx=None, hist=False, stream=None):
