@@ -122,8 +122,10 @@ def test_solve_gram_interface():
         # unpreconditioned fp32 CG before convergence moves by ~1e-3 under a one-ulp
         # change of A (measured with the oracle), so fp32 iterates agree to that level
         assert rel_err(x.cpu().numpy(), xr).max() < (5e-3 if L == 0 else 1e-4)
-        ref_rr = np.linalg.norm(D.resid(A, xr, b), axis=1) / np.linalg.norm(b, axis=1)
-        assert np.allclose(rr.cpu().numpy(), ref_rr, rtol=1e-2, atol=1e-6)
+        # the reported residual is that of the GPU's own estimate
+        xg = x.cpu().numpy()
+        ref_rr = np.linalg.norm(D.resid(A, xg, b), axis=1) / np.linalg.norm(b, axis=1)
+        assert np.allclose(rr.cpu().numpy(), ref_rr, rtol=1e-3, atol=1e-7)
 
 
 def test_edge_cases():
@@ -134,9 +136,10 @@ def test_edge_cases():
         for pk in (dict(w="fp64"), dict(gram="fp32", mv="fp32")):
             res = gpu_detect(d, K, pk)
             ref = oracle_detect(d, K, pk)
-            # N = K: kappa ~ 40, so K fp64 CG steps stop short of the roundoff floor
-            # and two valid fp64 runs differ at ~1e-8
-            assert rel_err(res["x"], ref["x"]).max() < (1e-6 if pk.get("w") else 5e-3)
+            # N = K: kappa ~ 42, K fp64 CG steps stop short of the roundoff floor
+            # (error 2.6e-7 vs the exact solve) and a one-ulp change of A moves
+            # the iterate by ~1e-6 (measured with the oracle)
+            assert rel_err(res["x"], ref["x"]).max() < (5e-6 if pk.get("w") else 5e-3)
     # y = 0: x = 0, status RHO_ZERO, rel_res 0
     d = wl.generate(wl.Spec(N=32, K=8, batch=4, qam=16, seed=2))
     d["y"][:] = 0
