@@ -199,6 +199,20 @@ FPCG_API int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t ba
 FPCG_API int fpcg_gram(const void* H, const void* y, const double* sigma2, int32_t n_rx, int32_t k,
                        int64_t batch, int32_t gram, void* A, void* b, int32_t* status, void* stream);
 
+/*
+ * fpcg_path -- which kernel fpcg_detect / fpbjcg_detect (block_L = 0 for
+ * FP-CG) would use for this configuration: FPCG_PATH_TENSOR_CORE (the fused
+ * tcgen05 Gram + mma.sync CG kernel: gram and mv in {BF16, FP16}, w = FP32,
+ * K in {16, 32, 64}, L dividing 16) or FPCG_PATH_SIMT (one CTA per system, every
+ * other configuration); FPCG_EINVAL (negative) for an invalid configuration.
+ * Setting the environment variable FPCG_FORCE_SIMT=1 makes every call take
+ * the SIMT kernel (same results within rounding; for A/B comparisons).
+ * Host only, no GPU needed.
+ */
+#define FPCG_PATH_SIMT 0
+#define FPCG_PATH_TENSOR_CORE 1
+FPCG_API int fpcg_path(int32_t k, int32_t block_L, const fpcg_precision* prec);
+
 /* Human-readable text for a return code (static storage). */
 FPCG_API const char* fpcg_strerror(int code);
 

@@ -1,11 +1,13 @@
 // C ABI entry points of libfpcg: argument validation and dispatch.
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "../../include/fpcg.h"
 #include "detect_simt.cuh"
 #include "gram_tc.cuh"
+#include "detect_tc.cuh"
 
 namespace {
 
@@ -47,6 +49,16 @@ int check_device_smem(size_t need) {
   return need <= (size_t)optin ? FPCG_OK : FPCG_ENOTSUP;
 }
 
+bool force_simt() {
+  const char* v = getenv("FPCG_FORCE_SIMT");
+  return v && v[0] && v[0] != '0';
+}
+
+bool uses_tc(int k, int block_L, const fpcg_precision* prec) {
+  return !force_simt() && prec->w == FPCG_FP32 && (prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) &&
+         (prec->mv == FPCG_BF16 || prec->mv == FPCG_FP16) && fpcg::detect_tc_supported(k, block_L);
+}
+
 int device_sms(int* sms) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -79,6 +91,35 @@ int run(const void* H, const void* y, const double* sigma2, const int32_t* qam_o
     if (e != cudaSuccess) return cuda_fail(e);
   }
   if (batch == 0) return FPCG_OK;
+  const bool tc_ok = !Ain && uses_tc(k, block_L, prec);
+  if (tc_ok) {
+    int sms = 0;
+    rc = device_sms(&sms);
+    if (rc) return rc;
+    rc = check_device_smem(fpcg::detect_tc_smem_bytes(k, block_L));
+    if (rc) return rc;
+    fpcg::DetectTcParams T;
+    memset(&T, 0, sizeof(T));
+    T.pipe = fpcg::make_pipe((const float2*)H, (const float2*)y, n_rx, k, batch, prec->gram == FPCG_BF16);
+    T.sigma2 = sigma2;
+    T.qam = qam_order;
+    T.iters = iters;
+    T.L = block_L;
+    T.refine_steps = prec->refine_steps;
+    T.refine_iters = refine_iters;
+    T.alpha_num = prec->alpha_num;
+    T.ip = prec->ip;
+    T.resid_comp = prec->resid == FPCG_FP64;
+    T.x_hat = (float2*)x_hat;
+    T.sym = sym_idx;
+    T.rel_res = rel_res;
+    T.res_hist = res_hist;
+    T.tx = tx_idx;
+    T.bit_errors = bit_errors;
+    T.status = status;
+    cudaError_t e = fpcg::launch_detect_tc(T, sms, prec->mv == FPCG_BF16, s);
+    return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+  }
   rc = check_device_smem(fpcg::simt_smem_bytes(fp64, k, block_L, prec->mv));
   if (rc) return rc;
   fpcg::SimtParams P;
@@ -188,6 +229,12 @@ int fpcg_gram(const void* H, const void* y, const double* sigma2, int32_t n_rx, 
   P.x_hat = A;  // unused in gram-only mode
   cudaError_t e = fpcg::launch_detect_simt(P, fp64, fp64 ? FPCG_FP64 : FPCG_FP32, s);
   return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+}
+
+int fpcg_path(int32_t k, int32_t block_L, const fpcg_precision* prec) {
+  if (check_prec(prec)) return -FPCG_EINVAL;
+  if (k < 1 || k > 128 || block_L < 0 || block_L > 32 || (block_L > 0 && k % block_L)) return -FPCG_EINVAL;
+  return uses_tc(k, block_L, prec) ? FPCG_PATH_TENSOR_CORE : FPCG_PATH_SIMT;
 }
 
 const char* fpcg_strerror(int code) {

@@ -16,6 +16,7 @@ namespace fpcg {
 namespace {
 
 constexpr int kThreads = 512;
+constexpr int kConv = 8;  // converter warps 8-15
 
 struct Smem {
   uint8_t* stages;
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcParams P) {
     reinterpret_cast<uint4*>(S.stages)[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
     for (int s = 0; s < tcp::kStages; ++s) {
-      tc::mbar_init(&S.bars->full[s], tcp::kConvWarps);
+      tc::mbar_init(&S.bars->full[s], kConv);
       tc::mbar_init(&S.bars->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcParams P) {
     if (lane == 0) tcp::mma_role(pp, S.stages, *S.bars, S.abort, tmem, tile0, tstep);
     __syncwarp();
   } else if (warp >= 8) {
-    tcp::converter_role(pp, S.stages, *S.bars, S.abort, tile0, tstep, warp - 8, lane);
+    tcp::converter_role<kConv>(pp, S.stages, *S.bars, S.abort, tile0, tstep, warp - 8, lane);
   } else if (warp >= 4) {
     const int q = warp - 4;
     const int row = 32 * q + lane;

@@ -40,7 +40,6 @@ constexpr int kStages = 4;
 constexpr int kStageRows = 144;
 constexpr int kStageBytes = kStageRows * 128;  // 18432, a multiple of 1024
 constexpr int kChunk = 64;                     // antennas per stage
-constexpr int kConvWarps = 8;
 constexpr int kMmaN = 144;
 constexpr int kAccCols = 256;                  // TMEM columns per accumulator buffer
 
@@ -89,51 +88,65 @@ __device__ __forceinline__ float4 load2(const float2* v, int n, int N, bool vali
   return r;
 }
 
-// Converter warp `cw` (0..7): its columns of the tile are cl = cw + 8 m.
+// Converter warp `cw` of NC: its columns of the tile are cl = cw + NC m, and
+// it loads y of systems cw, cw + NC of the tile (P <= 8 <= 2 NC).
+template <int NC>
 struct ConvRegs {
-  float4 h[8];
-  float4 y;
+  static constexpr int NM = (64 + NC - 1) / NC;
+  float4 h[NM];
+  float4 y[2];
 };
 
-__device__ __forceinline__ void conv_load(const Pipe& p, int64_t tile, int c, int cw, int lane, ConvRegs& R) {
+template <int NC>
+__device__ __forceinline__ void conv_load(const Pipe& p, int64_t tile, int c, int cw, int lane, ConvRegs<NC>& R) {
   const int n = c * kChunk + 2 * lane;
   const int64_t col0 = tile * (int64_t)(p.P * p.K);
   const int64_t ncols = p.batch * (int64_t)p.K;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int cl = cw + 8 * m;
+  for (int m = 0; m < ConvRegs<NC>::NM; ++m) {
+    const int cl = cw + NC * m;
     const int64_t col = col0 + cl;
     const bool ok = cl < p.P * p.K && col < ncols;
     R.h[m] = load2(p.H + (ok ? col : 0) * (int64_t)p.N, n, p.N, ok, p.vec4);
   }
-  const int64_t sys = tile * p.P + cw;  // converter warp cw also loads y of system cw of the tile
-  const bool oky = cw < p.P && sys < p.batch;
-  R.y = load2(p.y + (oky ? sys : 0) * (int64_t)p.N, n, p.N, oky, p.vec4);
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int ps = cw + NC * m;
+    const int64_t sys = tile * p.P + ps;
+    const bool oky = ps < p.P && sys < p.batch;
+    R.y[m] = load2(p.y + (oky ? sys : 0) * (int64_t)p.N, n, p.N, oky, p.vec4);
+  }
 }
 
-__device__ __forceinline__ void conv_store(const Pipe& p, uint8_t* stage, int cw, int lane, const ConvRegs& R) {
+template <int NC>
+__device__ __forceinline__ void conv_store(const Pipe& p, uint8_t* stage, int cw, int lane, const ConvRegs<NC>& R) {
   // k-positions 2*lane, 2*lane+1 of the 64-antenna chunk
   const uint32_t kpos = 2u * lane;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int cl = cw + 8 * m;
+  for (int m = 0; m < ConvRegs<NC>::NM; ++m) {
+    const int cl = cw + NC * m;
     if (cl < p.P * p.K) {
       const float4 v = R.h[m];
       *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(2 * cl, kpos)) = pack2(v.x, v.z, p.bf16);
       *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(2 * cl + 1, kpos)) = pack2(v.y, v.w, p.bf16);
     }
   }
-  if (cw < p.P) {
-    const float4 v = R.y;
-    *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(128 + 2 * cw, kpos)) = pack2(v.x, v.z, p.bf16);
-    *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(129 + 2 * cw, kpos)) = pack2(v.y, v.w, p.bf16);
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int ps = cw + NC * m;
+    if (ps < p.P) {
+      const float4 v = R.y[m];
+      *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(128 + 2 * ps, kpos)) = pack2(v.x, v.z, p.bf16);
+      *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(129 + 2 * ps, kpos)) = pack2(v.y, v.w, p.bf16);
+    }
   }
 }
 
 // Converter role: tiles this CTA owns are tile0, tile0 + tstep, ...
+template <int NC>
 __device__ inline void converter_role(const Pipe& p, uint8_t* stages, Bars& B, volatile int* abort,
                                       int64_t tile0, int64_t tstep, int cw, int lane) {
-  ConvRegs cur, nxt;
+  ConvRegs<NC> cur, nxt;
   int64_t j = 0;
   int c = 0;
   int64_t tile = tile0;

@@ -79,6 +79,8 @@ def lib():
         L.fpcg_solve_gram.restype = ctypes.c_int
         L.fpcg_gram.argtypes = [_P, _P, _P, _I32, _I32, _I64, _I32, _P, _P, _P, _P]
         L.fpcg_gram.restype = ctypes.c_int
+        L.fpcg_path.argtypes = [_I32, _I32, ctypes.POINTER(Precision)]
+        L.fpcg_path.restype = ctypes.c_int
         L.fpcg_strerror.argtypes = [ctypes.c_int]
         L.fpcg_strerror.restype = ctypes.c_char_p
         L.fpcg_last_cuda_error.argtypes = []
@@ -87,6 +89,17 @@ def lib():
         L.fpcg_version.restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+PATH_SIMT, PATH_TENSOR_CORE = 0, 1
+
+
+def fpcg_path(K, block_L, prec):
+    """Which kernel a detection call with these settings uses (no GPU needed)."""
+    rc = lib().fpcg_path(int(K), int(block_L or 0), ctypes.byref(prec))
+    if rc < 0:
+        raise FpcgError(-rc, "fpcg_path")
+    return rc
 
 
 def fpcg_strerror(code):

@@ -1,0 +1,136 @@
+"""Fused tensor-core detector (tcgen05 Gram + mma.sync FP-(BJ-)CG) against the
+oracle's emulation of the same precisions.  Bar: x_hat within 2e-3 relative
+(99th percentile; 1e-2 for every system), labels equal to the oracle's slicer on
+the same estimates, bit-error counter and residual consistent with them."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import detect as D
+from oracle import qam as Q
+from paper_2504_09820_gb300 import fpcg as F
+from paper_2504_09820_gb300 import workload as wl
+
+from gpu_helpers import gpu_detect, oracle_detect, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    F.lib()
+
+
+def _check(d, res, ref, tol=2e-3):
+    e = rel_err(res["x"], ref["x"])
+    assert np.quantile(e, 0.99) < tol and e.max() < 5 * tol, (np.quantile(e, 0.99), e.max())
+    M = int(d["qam"][0])
+    assert np.array_equal(Q.slice_symbols(res["x"], M, "fp32"), res["sym"])
+    assert int(res["bit_errors"][0]) == Q.bit_errors(res["sym"], d["tx"])
+    assert np.all(res["status"] & ~F.ST_RHO_ZERO == 0)
+
+
+def _own_residual(d, res, gram):
+    A, b = D.gram_emul(d["H"], d["y"], d["sigma2"], gram)
+    return np.linalg.norm(D.resid(A, res["x"], b), axis=1) / np.linalg.norm(b, axis=1)
+
+
+CASES = [
+    # K, gram, mv, L, iters, refine
+    (64, "bf16", "bf16", 8, 6, 1),
+    (64, "fp16", "fp16", 8, 6, 1),
+    (64, "bf16", "bf16", 0, 10, 1),
+    (64, "bf16", "fp16", 16, 5, 2),
+    (64, "fp16", "bf16", 4, 6, 0),
+    (32, "bf16", "bf16", 8, 8, 1),
+    (32, "fp16", "fp16", 16, 6, 1),
+    (16, "bf16", "bf16", 4, 8, 1),
+    (16, "bf16", "bf16", 0, 12, 1),
+    (64, "bf16", "bf16", 1, 6, 1),
+    (64, "bf16", "bf16", 2, 6, 1),
+]
+
+
+@pytest.mark.parametrize("K,gram,mv,L,iters,refine", CASES)
+def test_fused_matches_oracle(K, gram, mv, L, iters, refine):
+    N = 4 * K
+    P = 64 // K
+    batch = 152 * P * 2 + P // 2 + 1       # every CTA reuses both accumulators; ragged last tile
+    d = wl.generate(wl.Spec(N=N, K=K, batch=batch, rho=0.5, qam=64, snr_db=14.0, seed=500 + K + L))
+    pk = dict(gram=gram, mv=mv, refine_steps=refine)
+    assert F.fpcg_path(K, L, F.precision(**pk)) == F.PATH_TENSOR_CORE
+    res = gpu_detect(d, iters, pk, L=(L or None))
+    ref = oracle_detect(d, iters, pk, L=(L or None))
+    _check(d, res, ref)
+    own = _own_residual(d, res, gram)
+    assert np.allclose(res["rel_res"], own, rtol=2e-3, atol=1e-6)
+
+
+def test_fused_headline_config_full_size_sampled():
+    """The benchmark's workload and launch: N=256, K=64, 16384 Kronecker
+    channels, BF16 Gram and A p, BJ L=8, 6 + 6 iterations; oracle on a sample."""
+    from bench import HEAD
+    spec = wl.c3_kron_256x64()
+    d = wl.generate(spec)
+    pk = dict(HEAD["prec"])
+    assert F.fpcg_path(64, HEAD["L"], F.precision(**pk)) == F.PATH_TENSOR_CORE
+    res = gpu_detect(d, HEAD["iters"], pk, L=HEAD["L"])
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(spec.batch, 96, replace=False))
+    ref = oracle_detect(d, HEAD["iters"], pk, L=HEAD["L"], sel=sel)
+    e = rel_err(res["x"][sel], ref["x"])
+    assert np.quantile(e, 0.99) < 2e-3 and e.max() < 1e-2, (np.quantile(e, 0.99), e.max())
+    assert np.array_equal(Q.slice_symbols(res["x"], 64, "fp32"), res["sym"])
+    assert int(res["bit_errors"][0]) == Q.bit_errors(res["sym"], d["tx"])
+    # BER of the fused path within 5% of the fp64 direct LMMSE solve (sample)
+    xs = D.lmmse(d["H"][:1024], d["y"][:1024], d["sigma2"][:1024])
+    e_ref = Q.bit_errors(Q.slice_symbols(xs, 64, "fp64"), d["tx"][:1024])
+    e_gpu = Q.bit_errors(res["sym"][:1024], d["tx"][:1024])
+    assert abs(e_gpu / e_ref - 1) < 0.05
+
+
+def test_fused_hist_alpha_ip_and_compensated_residual():
+    d = wl.generate(wl.Spec(N=128, K=32, batch=700, rho=0.7, qam=16, snr_db=16.0, seed=77))
+    for pk, L in ((dict(gram="bf16", mv="bf16", alpha_num=1, refine_steps=1), 8),
+                  (dict(gram="bf16", mv="bf16", ip="bf16", refine_steps=1), 8),
+                  (dict(gram="fp16", mv="fp16", resid="fp64", refine_steps=2), 4)):
+        res = gpu_detect(d, 6, pk, L=L, hist=True)
+        ref = oracle_detect(d, 6, pk, L=L)
+        _check(d, res, ref, tol=(5e-3 if pk.get("ip") == "bf16" else 2e-3))
+        assert np.allclose(res["hist"], ref["hist"], rtol=2e-2, atol=1e-4 * ref["hist"][:, :1])
+
+
+def test_fused_matches_simt_path(monkeypatch):
+    """Same semantics on both kernels: the tensor-core path against the SIMT
+    path (forced with FPCG_FORCE_SIMT) on identical inputs."""
+    d = wl.generate(wl.Spec(N=256, K=64, batch=600, rho=0.7, qam=64, snr_db=18.0, seed=99))
+    pk = dict(gram="bf16", mv="bf16", refine_steps=1)
+    assert F.fpcg_path(64, 8, F.precision(**pk)) == F.PATH_TENSOR_CORE
+    tc = gpu_detect(d, 6, pk, L=8)
+    monkeypatch.setenv("FPCG_FORCE_SIMT", "1")
+    assert F.fpcg_path(64, 8, F.precision(**pk)) == F.PATH_SIMT
+    simt = gpu_detect(d, 6, pk, L=8)
+    monkeypatch.delenv("FPCG_FORCE_SIMT")
+    e = rel_err(tc["x"], simt["x"])
+    assert np.quantile(e, 0.99) < 2e-3 and e.max() < 1e-2
+
+
+def test_fused_edge_cases():
+    # y = 0 -> x = 0, RHO_ZERO; iters = 0 -> x = 0 (then refinement) ; determinism
+    d = wl.generate(wl.Spec(N=64, K=16, batch=300, qam=16, snr_db=10.0, seed=3))
+    d0 = dict(d)
+    d0["y"] = np.zeros_like(d["y"])
+    res = gpu_detect(d0, 5, dict(gram="bf16", mv="bf16", refine_steps=1), L=4)
+    assert np.all(res["x"] == 0) and np.all(res["status"] & F.ST_RHO_ZERO) and np.all(res["rel_res"] == 0)
+    res = gpu_detect(d, 0, dict(gram="bf16", mv="bf16"), L=4)
+    assert np.all(res["x"] == 0) and np.allclose(res["rel_res"], 1.0)
+    a = gpu_detect(d, 6, dict(gram="bf16", mv="bf16", refine_steps=1), L=4)
+    b = gpu_detect(d, 6, dict(gram="bf16", mv="bf16", refine_steps=1), L=4)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["sym"], b["sym"])
+    # batch smaller than one tile and than the SM count
+    d1 = wl.generate(wl.Spec(N=64, K=16, batch=3, qam=16, snr_db=10.0, seed=4))
+    res = gpu_detect(d1, 8, dict(gram="bf16", mv="bf16"), L=4)
+    ref = oracle_detect(d1, 8, dict(gram="bf16", mv="bf16"), L=4)
+    assert rel_err(res["x"], ref["x"]).max() < 1e-2
