@@ -171,6 +171,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--batch", type=int, default=None, help="override the batch (profiling runs)")
+    ap.add_argument("--only-head", action="store_true",
+                    help="time only the headline detector (profiling runs; no comparator, BER, e2e)")
+    ap.add_argument("--breakdown", action="store_true",
+                    help="also time the Gram alone and the detector without CG iterations")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -191,6 +196,8 @@ def main():
     F.lib()
 
     spec = workload_spec(rank)
+    if args.batch:
+        spec.batch = args.batch
     d = wl.generate(spec)
     g = {k: torch.from_numpy(d[k]).to(dev) for k in ("H", "y", "sigma2", "qam", "tx")}
     B, K, N = g["H"].shape
@@ -250,6 +257,25 @@ def main():
     det_s = world * B * args.steps / total
     ms_step = 1e3 * total / args.steps
     launch_avg = statistics.mean(per)
+    if args.only_head:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": det_s, "unit": UNIT, "ms_per_step": ms_step,
+                              "batch": B, "steps": args.steps, "clocks": clocks}), flush=True)
+        return
+    breakdown = None
+    if args.breakdown:
+        A = torch.empty((B, K, K), dtype=torch.complex64, device=dev)
+        bb = torch.empty((B, K), dtype=torch.complex64, device=dev)
+
+        def gram_only():
+            F.fpcg_gram(g["H"], g["y"], g["sigma2"], HEAD["prec"]["gram"], A, bb, stream=stream)
+        t_gram, _ = timed(gram_only, max(2, args.steps // 2), 1)
+        no_cg = dict(HEAD, iters=0, prec=dict(HEAD["prec"], refine_steps=0))
+        t_nocg, _ = timed(make_call(no_cg, outputs(), g), max(2, args.steps // 2), 1)
+        n2 = max(2, args.steps // 2)
+        breakdown = {"gram_only_ms": 1e3 * t_gram / n2, "detect_without_cg_ms": 1e3 * t_nocg / n2,
+                     "detect_ms": ms_step,
+                     "gram_only_hbm_frac": B * bytes_per_detection(N, K) / (t_gram / n2) / 1e9 / peaks()["hbm_gbs"]}
 
     # comparator: plain fp32 CG on the same batch
     o_comp = outputs()
@@ -328,7 +354,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "comparator": {"name": COMP["name"], "iters": COMP["iters"], "value": comp_det_s, "unit": UNIT,
                        "speedup_of_head": det_s / comp_det_s},
-        "ber": ber, "clocks": clocks, "gpu_launches": args.steps,
+        "ber": ber, "clocks": clocks, "gpu_launches": args.steps, "breakdown": breakdown,
     }
     print(json.dumps(line), flush=True)
     if dist:
