@@ -15,9 +15,11 @@
 //   * A p (u_MV): A rounded to bf16/fp16 lives in registers as mma.sync A
 //     fragments, [Re A; Im A] (two 16-row tiles per warp) times the 16x8 B
 //     fragment [Re p, Im p, 0...] -- products exact, fp32 sums;
-//   * Algorithm 2 / 3: vectors of the warp's rows in registers, inner products
-//     reduced over the warp and then over the system's warps (u_IP rounding),
-//     updates by FMA at u_W = fp32;
+//   * Algorithm 2 / 3: the first warp of each system holds its vectors (one or
+//     two rows per lane): inner products by warp shuffles (u_IP rounding),
+//     z = M_d r by shuffles within the block's lanes, updates by FMA at
+//     u_W = fp32, p handed to the matvec warps as packed mma B fragments --
+//     two warpgroup barriers per iteration;
 //   * refinement: r = b - A x from the fp32 A in shared memory, a correction
 //     solve, x += d; rel_res; Gray-QAM decision; bit errors.
 #include <cuda_runtime.h>
@@ -38,23 +40,22 @@ constexpr int kConv = 7;  // converter warps 8-14
 
 // Per-warpgroup shared memory (rows are the 64 rows of a tile: row = ps*K + k).
 struct CgSmem {
-  float2* A;      // [64][K+1]
+  float2* A;      // [64][K+1] fp32 Gram (+ sigma^2)
   float2* b;      // [64]
-  float2* v;      // [64] scratch vector (p, then x for residuals)
-  float2* r;      // [64] r for the block-Jacobi product
-  float2* Md;     // [64][L]
-  float* red;     // [3][4][2] partial sums per warp
-  double* dred;   // [4][2]
+  float2* W;      // [64] varpi = A p from the mma warps
+  float2* X;      // [64] x for the residual
+  float2* R;      // [64] residual b - A x
+  float2* Md;     // [64][L+1] block-Jacobi inverse rows (padded)
+  uint32_t* Pk;   // [64] p packed as the mma B fragments (bf16/fp16 pairs)
   int* flag;      // [4]
 };
 
 __host__ __device__ inline size_t cg_smem_bytes(int K, int L) {
   size_t s = 0;
   s += sizeof(float2) * 64 * (K + 1);
-  s += sizeof(float2) * 64 * 3;
-  s += sizeof(float2) * 64 * (L > 0 ? L : 1);
-  s += sizeof(float) * 3 * 4 * 2;
-  s += sizeof(double) * 4 * 2;
+  s += sizeof(float2) * 64 * 4;
+  s += sizeof(float2) * 64 * ((L > 0 ? L : 1) + 1);
+  s += sizeof(uint32_t) * 64;
   s += sizeof(int) * 4;
   return (s + 127) & ~size_t(127);
 }
@@ -66,16 +67,16 @@ __device__ inline CgSmem cg_carve(uint8_t* base, int K, int L) {
   p += sizeof(float2) * 64 * (K + 1);
   s.b = (float2*)p;
   p += sizeof(float2) * 64;
-  s.v = (float2*)p;
+  s.W = (float2*)p;
   p += sizeof(float2) * 64;
-  s.r = (float2*)p;
+  s.X = (float2*)p;
+  p += sizeof(float2) * 64;
+  s.R = (float2*)p;
   p += sizeof(float2) * 64;
   s.Md = (float2*)p;
-  p += sizeof(float2) * 64 * (L > 0 ? L : 1);
-  s.dred = (double*)p;  // 8-byte aligned: everything before is a multiple of 8
-  p += sizeof(double) * 4 * 2;
-  s.red = (float*)p;
-  p += sizeof(float) * 3 * 4 * 2;
+  p += sizeof(float2) * 64 * ((L > 0 ? L : 1) + 1);
+  s.Pk = (uint32_t*)p;
+  p += sizeof(uint32_t) * 64;
   s.flag = (int*)p;
   return s;
 }
@@ -84,16 +85,28 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One CG warpgroup working on a tile of P = 64/K systems.  Every warp owns 16
+// rows of one system for the matvec (mma.sync) and the residual; the first
+// warp of each system (the "vector warp") owns the system's vectors, one row
+// per lane (two for K = 64), and does all of Algorithm 2/3's vector work.
 template <int K, bool BF>
 struct CgWarp {
-  static constexpr int KT = K / 16;     // k-tiles
-  static constexpr int WS = K / 16;     // warps per system
+  static constexpr int KT = K / 16;          // k-tiles of the matvec
+  static constexpr int WS = K / 16;          // warps per system
+  static constexpr int E = K == 64 ? 2 : 1;  // rows per lane in the vector warp
   const DetectTcParams& P;
   CgSmem S;
   int wi, lane, g, t, ps, rb, row0, bar_id;
+  bool vec;                                  // this warp is its system's vector warp
   int64_t sys;
   bool valid;
-  uint32_t afr[2][KT][4];               // [Re A; Im A] fragments of the warp's 16 rows
+  uint32_t afr[2][KT][4];                    // [Re A; Im A] fragments of the warp's 16 rows
 
   __device__ CgWarp(const DetectTcParams& P_, CgSmem S_, int wi_, int lane_, int bar_id_)
       : P(P_), S(S_), wi(wi_), lane(lane_), bar_id(bar_id_) {
@@ -102,38 +115,15 @@ struct CgWarp {
     ps = wi / WS;
     rb = wi % WS;
     row0 = ps * K + 16 * rb;
+    vec = rb == 0;
   }
 
   __device__ __forceinline__ void wg_sync() { tc::bar_sync(bar_id, 128); }
-
   __device__ __forceinline__ uint32_t pk(float a, float b) { return tcp::pack2(a, b, BF ? 1 : 0); }
-
-  // sum over the warp of a value held by lanes t == 0 (others hold 0)
-  __device__ __forceinline__ float wsum8(float v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 16);
-    return v;
-  }
-
-  // Sum of two per-warp partials over the system's warps (one WG barrier).
-  __device__ __forceinline__ void sys_sum2(float& a, float& b, int slot) {
-    a = wsum8(a);
-    b = wsum8(b);
-    float* red = S.red + slot * 8;
-    if (lane == 0) {
-      red[wi * 2] = a;
-      red[wi * 2 + 1] = b;
-    }
-    wg_sync();
-    float sa = 0.f, sb = 0.f;
-    for (int w = ps * WS; w < ps * WS + WS; ++w) {
-      sa += red[w * 2];
-      sb += red[w * 2 + 1];
-    }
-    a = sa;
-    b = sb;
-  }
+  __device__ __forceinline__ float rip(float v) { return round_to(v, P.ip); }
+  // row (tile numbering) of element e of this lane in the vector warp, and whether it exists
+  __device__ __forceinline__ int vrow(int e) const { return ps * K + lane + 32 * e; }
+  __device__ __forceinline__ bool vact() const { return lane < K; }
 
   __device__ void build_fragments() {
 #pragma unroll
@@ -152,96 +142,113 @@ struct CgWarp {
     }
   }
 
-  // varpi = A p for the warp's rows g, g+8 (valid in lanes t == 0); p of the
-  // whole system is read from S.v.
-  __device__ __forceinline__ void matvec(float2& w0, float2& w1) {
-    uint32_t b0[KT], b1[KT];
-    const float2* pv = S.v + ps * K;
-#pragma unroll
-    for (int kt = 0; kt < KT; ++kt) {
-      b0[kt] = b1[kt] = 0u;
-      if (g < 2) {
-        const int c0 = 16 * kt + 2 * t;
-        const float2 a0 = pv[c0], a1 = pv[c0 + 1], a8 = pv[c0 + 8], a9 = pv[c0 + 9];
-        b0[kt] = g == 0 ? pk(a0.x, a1.x) : pk(a0.y, a1.y);
-        b1[kt] = g == 0 ? pk(a8.x, a9.x) : pk(a8.y, a9.y);
-      }
-    }
+  // All warps: W[rows of this warp] = A p, p taken from the packed fragments.
+  __device__ __forceinline__ void matvec_rows() {
+    const uint32_t* pk_sys = S.Pk + ps * 16 * KT;
     float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int kt = 0; kt < KT; ++kt) {
+      uint32_t b0 = 0u, b1 = 0u;
+      if (g < 2) {
+        const uint2 w = *reinterpret_cast<const uint2*>(pk_sys + ((kt * 2 + g) * 4 + t) * 2);
+        b0 = w.x;
+        b1 = w.y;
+      }
       if (BF) {
-        tc::mma_m16n8k16_bf16(cr, afr[0][kt], b0[kt], b1[kt]);
-        tc::mma_m16n8k16_bf16(ci, afr[1][kt], b0[kt], b1[kt]);
+        tc::mma_m16n8k16_bf16(cr, afr[0][kt], b0, b1);
+        tc::mma_m16n8k16_bf16(ci, afr[1][kt], b0, b1);
       } else {
-        tc::mma_m16n8k16_f16(cr, afr[0][kt], b0[kt], b1[kt]);
-        tc::mma_m16n8k16_f16(ci, afr[1][kt], b0[kt], b1[kt]);
+        tc::mma_m16n8k16_f16(cr, afr[0][kt], b0, b1);
+        tc::mma_m16n8k16_f16(ci, afr[1][kt], b0, b1);
       }
     }
-    // rows g / g+8: (Re A pr - Im A pi) + i (Re A pi + Im A pr)
-    w0 = make_float2(cr[0] - ci[1], cr[1] + ci[0]);
-    w1 = make_float2(cr[2] - ci[3], cr[3] + ci[2]);
+    if (t == 0) {  // rows g / g+8: (Re A pr - Im A pi) + i (Re A pi + Im A pr)
+      S.W[row0 + g] = make_float2(cr[0] - ci[1], cr[1] + ci[0]);
+      S.W[row0 + g + 8] = make_float2(cr[2] - ci[3], cr[3] + ci[2]);
+    }
   }
 
-  // z = M_d r for rows g, g+8 (lanes t == 0); r0, r1 already stored in S.r.
-  __device__ __forceinline__ void precond(float2 r0, float2 r1, float2& z0, float2& z1) {
+  // Vector warp: store p (one or two rows per lane) as mma B fragments:
+  // word ((kt*2 + comp)*4 + tt)*2 + h holds rows 16kt + 8h + 2tt, +1.
+  __device__ __forceinline__ void pack_p(const float2 (&p)[E]) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const float nx = __shfl_down_sync(0xffffffffu, p[e].x, 1);
+      const float ny = __shfl_down_sync(0xffffffffu, p[e].y, 1);
+      const int rl = lane + 32 * e;
+      if (vact() && (rl & 1) == 0) {
+        const int kt = rl >> 4, j = rl & 15, tt = (j & 7) >> 1, h = j >> 3;
+        uint32_t* base = S.Pk + ps * 16 * KT;
+        base[((kt * 2 + 0) * 4 + tt) * 2 + h] = pk(p[e].x, nx);
+        base[((kt * 2 + 1) * 4 + tt) * 2 + h] = pk(p[e].y, ny);
+      }
+    }
+  }
+
+  // Vector warp: z = M_d r (z = r without a preconditioner); the L rows of a
+  // block sit in L consecutive lanes.
+  __device__ __forceinline__ void precond(const float2 (&r)[E], float2 (&z)[E]) {
     const int L = P.L;
-    if (L == 0) {
-      z0 = r0;
-      z1 = r1;
-      return;
-    }
-    z0 = make_float2(0.f, 0.f);
-    z1 = make_float2(0.f, 0.f);
-    if (t != 0) return;
-    const int i0 = row0 + g, i1 = row0 + g + 8;
-    const int s0 = i0 - (i0 - ps * K) % L, s1 = i1 - (i1 - ps * K) % L;
-    for (int j = 0; j < L; ++j) {
-      const float2 m0 = S.Md[i0 * L + j], q0 = S.r[s0 + j];
-      const float2 m1 = S.Md[i1 * L + j], q1 = S.r[s1 + j];
-      z0.x = fmaf(m0.x, q0.x, fmaf(-m0.y, q0.y, z0.x));
-      z0.y = fmaf(m0.x, q0.y, fmaf(m0.y, q0.x, z0.y));
-      z1.x = fmaf(m1.x, q1.x, fmaf(-m1.y, q1.y, z1.x));
-      z1.y = fmaf(m1.x, q1.y, fmaf(m1.y, q1.x, z1.y));
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (L == 0) {
+        z[e] = r[e];
+        continue;
+      }
+      const int first = lane & ~(L - 1);
+      const float2* mrow = S.Md + vrow(e) * (L + 1);
+      float2 acc = make_float2(0.f, 0.f);
+      for (int j = 0; j < L; ++j) {
+        const float qx = __shfl_sync(0xffffffffu, r[e].x, first + j);
+        const float qy = __shfl_sync(0xffffffffu, r[e].y, first + j);
+        const float2 m = vact() ? mrow[j] : make_float2(0.f, 0.f);
+        acc.x = fmaf(m.x, qx, fmaf(-m.y, qy, acc.x));
+        acc.y = fmaf(m.x, qy, fmaf(m.y, qx, acc.y));
+      }
+      z[e] = acc;
     }
   }
 
-  __device__ __forceinline__ float rip(float v) { return round_to(v, P.ip); }
+  __device__ __forceinline__ float dot_re(const float2 (&a)[E], const float2 (&b)[E]) {
+    float s = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) s += a[e].x * b[e].x + a[e].y * b[e].y;
+    return warp_sum_f(vact() ? s : 0.f);
+  }
 
-  // Algorithm 2 (L == 0) or 3 (L > 0) from x0 = 0 on rhs (rows g, g+8 in
-  // lanes t == 0).  Returns x in x0/x1 and status bits.
-  __device__ int solve(float2 q0, float2 q1, int iters, float* hist, float2& x0, float2& x1) {
-    const bool act = (t == 0);
+  // Algorithm 2 (L == 0) / Algorithm 3 (L > 0) from x0 = 0 on the right-hand
+  // side rhs[] (shared memory, tile rows).  Every warp of the warpgroup calls it;
+  // the vector warps return x in xo and their status bits.
+  __device__ int solve(const float2* rhs, int iters, float* hist, float2 (&xo)[E]) {
     int st = 0;
-    float2 r0 = act ? q0 : make_float2(0.f, 0.f), r1 = act ? q1 : make_float2(0.f, 0.f);
-    x0 = x1 = make_float2(0.f, 0.f);
-    if (act) {
-      S.r[row0 + g] = r0;
-      S.r[row0 + g + 8] = r1;
-    }
-    __syncwarp();
-    float2 z0, z1;
-    precond(r0, r1, z0, z1);
-    float2 p0 = z0, p1 = z1;
-    float rz = act ? (r0.x * z0.x + r0.y * z0.y + r1.x * z1.x + r1.y * z1.y) : 0.f;
-    float rr = act ? (r0.x * r0.x + r0.y * r0.y + r1.x * r1.x + r1.y * r1.y) : 0.f;
-    sys_sum2(rz, rr, 0);
-    float rho = rip(rz);
-    if (hist && lane == 0 && rb == 0) hist[0] = sqrtf(rr);
+    float2 x[E], r[E], p[E], z[E];
+    float rho = 0.f;
     bool live = true;
-    for (int it = 0; it < iters; ++it) {
-      if (act) {
-        S.v[row0 + g] = p0;
-        S.v[row0 + g + 8] = p1;
+    if (vec) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        x[e] = make_float2(0.f, 0.f);
+        r[e] = vact() ? rhs[vrow(e)] : make_float2(0.f, 0.f);
       }
-      wg_sync();
-      float2 w0, w1;
-      matvec(w0, w1);
-      float phi = act ? (p0.x * w0.x + p0.y * w0.y + p1.x * w1.x + p1.y * w1.y) : 0.f;
-      float rp = act ? (r0.x * p0.x + r0.y * p0.y + r1.x * p1.x + r1.y * p1.y) : 0.f;
-      sys_sum2(phi, rp, 1);
-      phi = rip(phi);
-      const float rho_prev = (P.L > 0 && P.alpha_num == 0) ? rip(rp) : rho;
+      precond(r, z);
+#pragma unroll
+      for (int e = 0; e < E; ++e) p[e] = z[e];
+      rho = rip(dot_re(r, z));
+      const float rr = dot_re(r, r);
+      if (hist && lane == 0) hist[0] = sqrtf(rr);
+      pack_p(p);
+    }
+    for (int it = 0; it < iters; ++it) {
+      wg_sync();  // packed p visible
+      matvec_rows();
+      wg_sync();  // varpi visible
+      if (!vec) continue;
+      float2 w[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) w[e] = vact() ? S.W[vrow(e)] : make_float2(0.f, 0.f);
+      const float phi = rip(dot_re(p, w));
+      const float rp = (P.L > 0 && P.alpha_num == 0) ? rip(dot_re(r, p)) : rho;
+      const float rho_prev = rp;
       if (live) {
         if (rho_prev == 0.f) {
           st |= 2;
@@ -251,134 +258,115 @@ struct CgWarp {
           live = false;
         }
       }
-      float2 nr0 = r0, nr1 = r1, nx0 = x0, nx1 = x1;
       if (live) {
         const float alpha = rho_prev / phi;
-        nx0 = make_float2(fmaf(alpha, p0.x, x0.x), fmaf(alpha, p0.y, x0.y));
-        nx1 = make_float2(fmaf(alpha, p1.x, x1.x), fmaf(alpha, p1.y, x1.y));
-        nr0 = make_float2(fmaf(-alpha, w0.x, r0.x), fmaf(-alpha, w0.y, r0.y));
-        nr1 = make_float2(fmaf(-alpha, w1.x, r1.x), fmaf(-alpha, w1.y, r1.y));
-      }
-      if (act) {
-        S.r[row0 + g] = nr0;
-        S.r[row0 + g + 8] = nr1;
-      }
-      __syncwarp();
-      precond(nr0, nr1, z0, z1);
-      float rzn = act ? (nr0.x * z0.x + nr0.y * z0.y + nr1.x * z1.x + nr1.y * z1.y) : 0.f;
-      float rrn = act ? (nr0.x * nr0.x + nr0.y * nr0.y + nr1.x * nr1.x + nr1.y * nr1.y) : 0.f;
-      sys_sum2(rzn, rrn, 2);
-      if (live) {
-        const float rho_new = rip(rzn);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          x[e] = make_float2(fmaf(alpha, p[e].x, x[e].x), fmaf(alpha, p[e].y, x[e].y));
+          r[e] = make_float2(fmaf(-alpha, w[e].x, r[e].x), fmaf(-alpha, w[e].y, r[e].y));
+        }
+        precond(r, z);
+        const float rho_new = rip(dot_re(r, z));
         const float beta = rho_new / rho_prev;
-        p0 = make_float2(fmaf(beta, p0.x, z0.x), fmaf(beta, p0.y, z0.y));
-        p1 = make_float2(fmaf(beta, p1.x, z1.x), fmaf(beta, p1.y, z1.y));
-        x0 = nx0;
-        x1 = nx1;
-        r0 = nr0;
-        r1 = nr1;
+#pragma unroll
+        for (int e = 0; e < E; ++e) p[e] = make_float2(fmaf(beta, p[e].x, z[e].x), fmaf(beta, p[e].y, z[e].y));
         rho = rho_new;
+        if (hist) {
+          const float rr = dot_re(r, r);
+          if (lane == 0) hist[it + 1] = sqrtf(rr);
+        }
+        pack_p(p);
+      } else if (hist && lane == 0) {
+        hist[it + 1] = hist[it];
       }
-      if (hist && lane == 0 && rb == 0) hist[it + 1] = live ? sqrtf(rrn) : hist[it];
     }
+#pragma unroll
+    for (int e = 0; e < E; ++e) xo[e] = x[e];
     return st;
   }
 
-  // out = b - A x for rows g, g+8 (lanes t == 0 get the result); x of the whole
-  // system is read from S.v.  Plain fp32 sums, or compensated ones.
-  __device__ void residual(float2& o0, float2& o1) {
-    const float2* xs = S.v + ps * K;
-    const float2* a0 = S.A + (row0 + g) * (K + 1);
-    const float2* a1 = S.A + (row0 + g + 8) * (K + 1);
+  // All warps: R[rows of this warp] = b - A X (X in shared memory): lane handles
+  // row row0 + (lane & 15) and half of the columns.
+  __device__ void residual() {
+    const int rl = lane & 15, half = lane >> 4;
+    const float2* arow = S.A + (row0 + rl) * (K + 1) + half * (K / 2);
+    const float2* xs = S.X + ps * K + half * (K / 2);
     if (!P.resid_comp) {
-      float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-      for (int l = t; l < K; l += 4) {
-        const float2 x = xs[l], m0 = a0[l], m1 = a1[l];
-        s0.x = fmaf(m0.x, x.x, fmaf(-m0.y, x.y, s0.x));
-        s0.y = fmaf(m0.x, x.y, fmaf(m0.y, x.x, s0.y));
-        s1.x = fmaf(m1.x, x.x, fmaf(-m1.y, x.y, s1.x));
-        s1.y = fmaf(m1.x, x.y, fmaf(m1.y, x.x, s1.y));
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll 8
+      for (int l = 0; l < K / 2; ++l) {
+        const float2 a = arow[l], x = xs[l];
+        s.x = fmaf(a.x, x.x, fmaf(-a.y, x.y, s.x));
+        s.y = fmaf(a.x, x.y, fmaf(a.y, x.x, s.y));
       }
-#pragma unroll
-      for (int o = 1; o < 4; o <<= 1) {
-        s0.x += __shfl_xor_sync(0xffffffffu, s0.x, o);
-        s0.y += __shfl_xor_sync(0xffffffffu, s0.y, o);
-        s1.x += __shfl_xor_sync(0xffffffffu, s1.x, o);
-        s1.y += __shfl_xor_sync(0xffffffffu, s1.y, o);
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 16);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 16);
+      if (half == 0) {
+        const float2 bb = S.b[row0 + rl];
+        S.R[row0 + rl] = make_float2(bb.x - s.x, bb.y - s.y);
       }
-      const float2 b0 = S.b[row0 + g], b1 = S.b[row0 + g + 8];
-      o0 = make_float2(b0.x - s0.x, b0.y - s0.y);
-      o1 = make_float2(b1.x - s1.x, b1.y - s1.y);
       return;
     }
-    float h[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-    if (t == 0) {
-      h[0] = S.b[row0 + g].x;
-      h[1] = S.b[row0 + g].y;
-      h[2] = S.b[row0 + g + 8].x;
-      h[3] = S.b[row0 + g + 8].y;
+    float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
+    if (half == 0) {
+      hr = S.b[row0 + rl].x;
+      hi = S.b[row0 + rl].y;
     }
-    for (int l = t; l < K; l += 4) {
-      const float2 x = xs[l], m0 = a0[l], m1 = a1[l];
-      df_sub_prod(h[0], lo[0], m0.x, x.x);
-      df_sub_prod(h[0], lo[0], -m0.y, x.y);
-      df_sub_prod(h[1], lo[1], m0.x, x.y);
-      df_sub_prod(h[1], lo[1], m0.y, x.x);
-      df_sub_prod(h[2], lo[2], m1.x, x.x);
-      df_sub_prod(h[2], lo[2], -m1.y, x.y);
-      df_sub_prod(h[3], lo[3], m1.x, x.y);
-      df_sub_prod(h[3], lo[3], m1.y, x.x);
+    for (int l = 0; l < K / 2; ++l) {
+      const float2 a = arow[l], x = xs[l];
+      df_sub_prod(hr, lr, a.x, x.x);
+      df_sub_prod(hr, lr, -a.y, x.y);
+      df_sub_prod(hi, li, a.x, x.y);
+      df_sub_prod(hi, li, a.y, x.x);
     }
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, h[c], o), l2 = __shfl_xor_sync(0xffffffffu, lo[c], o);
-        df_add(h[c], lo[c], h2, l2);
-      }
-    o0 = make_float2(__fadd_rn(h[0], lo[0]), __fadd_rn(h[1], lo[1]));
-    o1 = make_float2(__fadd_rn(h[2], lo[2]), __fadd_rn(h[3], lo[3]));
+    const float h2 = __shfl_xor_sync(0xffffffffu, hr, 16), l2 = __shfl_xor_sync(0xffffffffu, lr, 16);
+    const float h3 = __shfl_xor_sync(0xffffffffu, hi, 16), l3 = __shfl_xor_sync(0xffffffffu, li, 16);
+    df_add(hr, lr, h2, l2);
+    df_add(hi, li, h3, l3);
+    if (half == 0) S.R[row0 + rl] = make_float2(__fadd_rn(hr, lr), __fadd_rn(hi, li));
   }
 
-  // Gauss-Jordan inversion of the warp's L x L diagonal blocks in S.Md.
+  // All warps: Gauss-Jordan inversion of the warp's own L x L diagonal blocks
+  // into S.Md (rows padded to L+1).  Returns nonzero if a pivot was not positive.
   __device__ int bj_setup() {
     const int L = P.L;
-    int fail = 0;
     if (L == 0) return 0;
+    const int LD = L + 1;
+    int fail = 0;
     const int blk = lane / L, j = lane % L;
     const bool on = lane < 16;
-    const int R0 = row0 + blk * L;  // first row of the block (tile layout)
+    const int R0 = row0 + blk * L;  // first row of the block (tile numbering)
     const int kb = R0 - ps * K;     // its first column (system numbering)
     if (on)
-      for (int i = 0; i < L; ++i) S.Md[(R0 + i) * L + j] = S.A[(R0 + i) * (K + 1) + kb + j];
+      for (int i = 0; i < L; ++i) S.Md[(R0 + i) * LD + j] = S.A[(R0 + i) * (K + 1) + kb + j];
     __syncwarp();
     for (int pv = 0; pv < L; ++pv) {
-      float2 piv = on ? S.Md[(R0 + pv) * L + pv] : make_float2(1.f, 0.f);
+      const float2 piv = on ? S.Md[(R0 + pv) * LD + pv] : make_float2(1.f, 0.f);
       if (on && !(piv.x > 0.f && isfinite(piv.x))) fail = 1;
       const float den = piv.x * piv.x + piv.y * piv.y;
       const float2 dinv = make_float2(piv.x / den, -piv.y / den);
       __syncwarp();
-      if (on && j != pv) S.Md[(R0 + pv) * L + j] = cmul(S.Md[(R0 + pv) * L + j], dinv);
+      if (on && j != pv) S.Md[(R0 + pv) * LD + j] = cmul(S.Md[(R0 + pv) * LD + j], dinv);
       __syncwarp();
       if (on && j != pv) {
-        const float2 prow = S.Md[(R0 + pv) * L + j];
+        const float2 prow = S.Md[(R0 + pv) * LD + j];
         for (int i = 0; i < L; ++i) {
           if (i == pv) continue;
-          const float2 f = S.Md[(R0 + i) * L + pv];
-          float2 v = S.Md[(R0 + i) * L + j];
+          const float2 f = S.Md[(R0 + i) * LD + pv];
+          float2 v = S.Md[(R0 + i) * LD + j];
           const float2 fp = cmul(f, prow);
           v.x -= fp.x;
           v.y -= fp.y;
-          S.Md[(R0 + i) * L + j] = v;
+          S.Md[(R0 + i) * LD + j] = v;
         }
       }
       __syncwarp();
       if (on) {
         if (j == pv) {
-          S.Md[(R0 + pv) * L + pv] = dinv;
+          S.Md[(R0 + pv) * LD + pv] = dinv;
         } else {
-          const float2 v = cmul(S.Md[(R0 + j) * L + pv], dinv);
-          S.Md[(R0 + j) * L + pv] = make_float2(-v.x, -v.y);
+          const float2 v = cmul(S.Md[(R0 + j) * LD + pv], dinv);
+          S.Md[(R0 + j) * LD + pv] = make_float2(-v.x, -v.y);
         }
       }
       __syncwarp();
@@ -390,9 +378,11 @@ struct CgWarp {
 template <int K, bool BF>
 __device__ void cg_role(const DetectTcParams& P, tcp::Bars& B, volatile int* abort, uint32_t tmem, uint8_t* cg_base,
                         int wg, int64_t tile0, int64_t tstep) {
+  using CW = CgWarp<K, BF>;
+  constexpr int E = CW::E;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wi = warp - 4 * wg;  // warp within the warpgroup == TMEM lane quadrant
-  CgWarp<K, BF> W(P, cg_carve(cg_base, K, P.L), wi, lane, 1 + wg);
+  CW W(P, cg_carve(cg_base, K, P.L), wi, lane, 1 + wg);
   const tcp::Pipe& pp = P.pipe;
   const int twoK = 2 * K;
   const int trow = 32 * wi + lane;         // TMEM lane of this thread
@@ -426,118 +416,97 @@ __device__ void cg_role(const DetectTcParams& P, tcp::Bars& B, volatile int* abo
           [&](float v) { brow[odd] = tvalid ? v : 0.f; });
     }
     tc::tc_fence_before();
+    if (lane == 0 && W.vec) W.S.flag[W.ps] = 0;
     W.wg_sync();
     if (wi == 0 && lane == 0) tc::mbar_arrive(&B.acc_empty[wg]);
     W.sys = tile * pp.P + W.ps;
     W.valid = W.sys < pp.batch;
     int st = 0;
-    // ---- block-Jacobi setup
-    if (lane == 0 && W.rb == 0) W.S.flag[W.ps] = 0;
-    W.wg_sync();
+    // ---- block-Jacobi setup (every warp inverts its own blocks)
     if (W.bj_setup() && lane == 0) atomicOr(&W.S.flag[W.ps], 1);
     W.wg_sync();
     if (P.L > 0 && W.S.flag[W.ps]) {  // fall back to M_d = I for this system
-      st |= 8;
+      if (W.vec) st |= 8;
       if (lane < 16)
         for (int i = 0; i < P.L; ++i) {
           const int R = W.row0 + lane;
-          W.S.Md[R * P.L + i] = make_float2((R - W.ps * K) % P.L == i ? 1.f : 0.f, 0.f);
+          W.S.Md[R * (P.L + 1) + i] = make_float2((R - W.ps * K) % P.L == i ? 1.f : 0.f, 0.f);
         }
-      __syncwarp();
     }
     W.build_fragments();
+    W.wg_sync();
     // ---- main solve
-    float* hist = (P.res_hist && W.valid) ? P.res_hist + W.sys * (int64_t)(P.iters + 1) : nullptr;
-    float2 b0 = W.S.b[W.row0 + W.g], b1 = W.S.b[W.row0 + W.g + 8];
-    float2 x0, x1;
-    st |= W.solve(b0, b1, P.iters, hist, x0, x1);
+    float* hist = (P.res_hist && W.valid && W.vec) ? P.res_hist + W.sys * (int64_t)(P.iters + 1) : nullptr;
+    float2 x[E];
+    st |= W.solve(W.S.b, P.iters, hist, x);
     // ---- refinement: x += solve(b - A x)
     for (int rs = 0; rs < P.refine_steps; ++rs) {
-      W.wg_sync();  // every warp is done reading S.v (p) of the last iteration
-      if (W.t == 0) {
-        W.S.v[W.row0 + W.g] = x0;
-        W.S.v[W.row0 + W.g + 8] = x1;
-      }
+      if (W.vec && W.vact())
+#pragma unroll
+        for (int e = 0; e < E; ++e) W.S.X[W.vrow(e)] = x[e];
       W.wg_sync();
-      float2 r0, r1, d0, d1;
-      W.residual(r0, r1);
-      st |= W.solve(r0, r1, P.refine_iters, nullptr, d0, d1) & 1;
-      x0 = make_float2(x0.x + d0.x, x0.y + d0.y);
-      x1 = make_float2(x1.x + d1.x, x1.y + d1.y);
+      W.residual();
+      W.wg_sync();
+      float2 d[E];
+      st |= W.solve(W.S.R, P.refine_iters, nullptr, d) & 1;
+#pragma unroll
+      for (int e = 0; e < E; ++e) x[e] = make_float2(x[e].x + d[e].x, x[e].y + d[e].y);
     }
     // ---- final residual and outputs
-    W.wg_sync();
-    if (W.t == 0) {
-      W.S.v[W.row0 + W.g] = x0;
-      W.S.v[W.row0 + W.g + 8] = x1;
-    }
-    W.wg_sync();
-    float2 r0, r1;
-    W.residual(r0, r1);
-    double nr = 0.0, nb = 0.0;
-    if (W.t == 0) {
-      nr = (double)r0.x * r0.x + (double)r0.y * r0.y + (double)r1.x * r1.x + (double)r1.y * r1.y;
-      nb = (double)b0.x * b0.x + (double)b0.y * b0.y + (double)b1.x * b1.x + (double)b1.y * b1.y;
-    }
+    if (W.vec && W.vact())
 #pragma unroll
-    for (int o = 4; o < 32; o <<= 1) {
-      nr += __shfl_xor_sync(0xffffffffu, nr, o);
-      nb += __shfl_xor_sync(0xffffffffu, nb, o);
-    }
-    if (lane == 0) {
-      W.S.dred[wi * 2] = nr;
-      W.S.dred[wi * 2 + 1] = nb;
-    }
-    int nonfinite = (W.t == 0) && !(isfinite(x0.x) && isfinite(x0.y) && isfinite(x1.x) && isfinite(x1.y));
-    nonfinite = __any_sync(0xffffffffu, nonfinite);
-    if (nonfinite && lane == 0) atomicOr(&W.S.flag[W.ps], 2);
+      for (int e = 0; e < E; ++e) W.S.X[W.vrow(e)] = x[e];
     W.wg_sync();
-    if (W.valid) {
-      const int64_t base = W.sys * (int64_t)K;
-      const int k0 = W.row0 - W.ps * K + W.g;
-      if (W.t == 0) {
-        P.x_hat[base + k0] = x0;
-        P.x_hat[base + k0 + 8] = x1;
-      }
+    W.residual();
+    W.wg_sync();
+    if (W.vec && W.valid) {
+      double nr = 0.0, nb = 0.0;
+      int nonfinite = 0;
       unsigned errs = 0;
       int bad_qam = 0;
-      if (P.sym || P.bit_errors) {
-        const int M = P.qam[W.sys];
-        const int m = qam_sqrt(M);
-        if (m == 0) {
-          bad_qam = 1;
-          if (P.sym && W.t == 0) {
-            P.sym[base + k0] = 0;
-            P.sym[base + k0 + 8] = 0;
+      const int64_t base = W.sys * (int64_t)K;
+      const int M = (P.sym || P.bit_errors) ? P.qam[W.sys] : 0;
+      const int m = qam_sqrt(M);
+      if ((P.sym || P.bit_errors) && m == 0) bad_qam = 1;
+      if (W.vact()) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const float2 rr = W.S.R[W.vrow(e)], bb = W.S.b[W.vrow(e)];
+          nr += (double)rr.x * rr.x + (double)rr.y * rr.y;
+          nb += (double)bb.x * bb.x + (double)bb.y * bb.y;
+          const int k = lane + 32 * e;
+          if (!(isfinite(x[e].x) && isfinite(x[e].y))) nonfinite = 1;
+          P.x_hat[base + k] = x[e];
+          if (P.sym || P.bit_errors) {
+            int lab = 0;
+            if (m) {
+              const int nb2 = qam_bits_axis(m);
+              const float sc = (float)sqrt(2.0 * (M - 1) / 3.0);
+              lab = (gray(axis_level<float>(x[e].x, m, sc)) << nb2) | gray(axis_level<float>(x[e].y, m, sc));
+            }
+            if (P.sym) P.sym[base + k] = (uint8_t)lab;
+            if (P.tx && m) errs += __popc((unsigned)(lab ^ P.tx[base + k]));
           }
-        } else if (W.t == 0) {
-          const int nb2 = qam_bits_axis(m);
-          const float s = (float)sqrt(2.0 * (M - 1) / 3.0);
-          const int l0 = (gray(axis_level<float>(x0.x, m, s)) << nb2) | gray(axis_level<float>(x0.y, m, s));
-          const int l1 = (gray(axis_level<float>(x1.x, m, s)) << nb2) | gray(axis_level<float>(x1.y, m, s));
-          if (P.sym) {
-            P.sym[base + k0] = (uint8_t)l0;
-            P.sym[base + k0 + 8] = (uint8_t)l1;
-          }
-          if (P.tx) errs = __popc((unsigned)(l0 ^ P.tx[base + k0])) + __popc((unsigned)(l1 ^ P.tx[base + k0 + 8]));
         }
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        nr += __shfl_xor_sync(0xffffffffu, nr, o);
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+      }
+      nonfinite = __any_sync(0xffffffffu, nonfinite);
       if (P.bit_errors && P.tx) {
         errs = __reduce_add_sync(0xffffffffu, errs);
         if (lane == 0 && errs) atomicAdd(P.bit_errors, (unsigned long long)errs);
       }
-      if (lane == 0 && W.rb == 0) {
-        double sr = 0.0, sb = 0.0;
-        for (int w = W.ps * CgWarp<K, BF>::WS; w < (W.ps + 1) * CgWarp<K, BF>::WS; ++w) {
-          sr += W.S.dred[w * 2];
-          sb += W.S.dred[w * 2 + 1];
-        }
-        if (P.rel_res) P.rel_res[W.sys] = sb > 0.0 ? sqrt(sr / sb) : 0.0;
-        if (W.S.flag[W.ps] & 2) st |= 4;
+      if (lane == 0) {
+        if (P.rel_res) P.rel_res[W.sys] = nb > 0.0 ? sqrt(nr / nb) : 0.0;
+        if (nonfinite) st |= 4;
         if (bad_qam) st |= 16;
         if (P.status) P.status[W.sys] = st;
       }
     }
+    W.wg_sync();  // A, b, R are read until here; the next drain overwrites them
   }
   if (*abort && P.status) {  // systems this warpgroup did not finish
     for (; tile < pp.ntiles; tile += 2 * tstep)

@@ -142,6 +142,24 @@ __device__ __forceinline__ void conv_store(const Pipe& p, uint8_t* stage, int cw
   }
 }
 
+// Ask the bulk-copy engine to pull a tile's H and y into L2 ahead of the
+// converters' loads (16-byte granularity, clamped to the arrays).
+__device__ inline void prefetch_tile(const Pipe& p, int64_t tile) {
+  if (tile >= p.ntiles) return;
+  const int64_t col0 = tile * (int64_t)(p.P * p.K);
+  const int64_t cols = min((int64_t)(p.P * p.K), p.batch * (int64_t)p.K - col0);
+  const char* h = reinterpret_cast<const char*>(p.H + col0 * (int64_t)p.N);
+  int64_t bytes = (cols * (int64_t)p.N * 8) & ~int64_t(15);
+  if ((reinterpret_cast<uintptr_t>(h) & 15) == 0)
+    for (int64_t o = 0; o < bytes; o += 32768)
+      tc::prefetch_l2(h + o, (uint32_t)min(bytes - o, (int64_t)32768));
+  const int64_t s0 = tile * (int64_t)p.P;
+  const int64_t ns = min((int64_t)p.P, p.batch - s0);
+  const char* yy = reinterpret_cast<const char*>(p.y + s0 * (int64_t)p.N);
+  bytes = (ns * (int64_t)p.N * 8) & ~int64_t(15);
+  if ((reinterpret_cast<uintptr_t>(yy) & 15) == 0 && bytes > 0) tc::prefetch_l2(yy, (uint32_t)bytes);
+}
+
 // Converter role: tiles this CTA owns are tile0, tile0 + tstep, ...
 template <int NC>
 __device__ inline void converter_role(const Pipe& p, uint8_t* stages, Bars& B, volatile int* abort,
@@ -151,9 +169,12 @@ __device__ inline void converter_role(const Pipe& p, uint8_t* stages, Bars& B, v
   int c = 0;
   int64_t tile = tile0;
   if (tile >= p.ntiles) return;
+  const bool prefetcher = cw == 0 && lane == 0;
+  if (prefetcher) prefetch_tile(p, tile + tstep);
   conv_load(p, tile, c, cw, lane, cur);
   uint32_t u = 0;  // stage use counter
   while (true) {
+    if (prefetcher && c == 0) prefetch_tile(p, tile + 2 * tstep);
     // prefetch the next chunk's loads before waiting for the stage
     int c2 = c + 1;
     int64_t tile2 = tile, j2 = j;
