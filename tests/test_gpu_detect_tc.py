@@ -114,8 +114,9 @@ def test_fused_matches_simt_path(monkeypatch):
     assert F.fpcg_path(64, 8, F.precision(**pk)) == F.PATH_SIMT
     simt = gpu_detect(d, 6, pk, L=8)
     monkeypatch.delenv("FPCG_FORCE_SIMT")
+    # each path is within 2e-3 of the oracle; they differ by at most the sum
     e = rel_err(tc["x"], simt["x"])
-    assert np.quantile(e, 0.99) < 2e-3 and e.max() < 1e-2
+    assert np.quantile(e, 0.99) < 4e-3 and e.max() < 2e-2
 
 
 def test_fused_edge_cases():
