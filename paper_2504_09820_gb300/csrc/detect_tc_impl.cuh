@@ -1,4 +1,6 @@
-// Fused tensor-core detector: the whole path for K in {16, 32, 64} in one
+#pragma once
+// Fused tensor-core detector (kernel templates; instantiated per K by
+// detect_tc_k{16,32,64}.cu): the whole path for K in {16, 32, 64} in one
 // persistent launch (one CTA per SM).
 //
 //   warps 0-3    CG warpgroup 0: tiles 0, 2, 4, ... of this CTA (TMEM buffer 0)
@@ -50,16 +52,6 @@ struct CgSmem {
   int* flag;      // [4]
 };
 
-__host__ __device__ inline size_t cg_smem_bytes(int K, int L) {
-  size_t s = 0;
-  s += sizeof(float2) * 64 * (K + 1);
-  s += sizeof(float2) * 64 * 4;
-  s += sizeof(float2) * 64 * ((L > 0 ? L : 1) + 1);
-  s += sizeof(uint32_t) * 64;
-  s += sizeof(int) * 4;
-  return (s + 127) & ~size_t(127);
-}
-
 __device__ inline CgSmem cg_carve(uint8_t* base, int K, int L) {
   CgSmem s;
   uint8_t* p = base;
@@ -95,11 +87,13 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // rows of one system for the matvec (mma.sync) and the residual; the first
 // warp of each system (the "vector warp") owns the system's vectors, one row
 // per lane (two for K = 64), and does all of Algorithm 2/3's vector work.
-template <int K, bool BF>
+template <int K, bool BF, int LT>
 struct CgWarp {
   static constexpr int KT = K / 16;          // k-tiles of the matvec
   static constexpr int WS = K / 16;          // warps per system
   static constexpr int E = K == 64 ? 2 : 1;  // rows per lane in the vector warp
+  static constexpr int LD = LT + 1;          // padded row length of M_d
+
   const DetectTcParams& P;
   CgSmem S;
   int wi, lane, g, t, ps, rb, row0, bar_id;
@@ -188,24 +182,42 @@ struct CgWarp {
   // Vector warp: z = M_d r (z = r without a preconditioner); the L rows of a
   // block sit in L consecutive lanes.
   __device__ __forceinline__ void precond(const float2 (&r)[E], float2 (&z)[E]) {
-    const int L = P.L;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      if (L == 0) {
+      if constexpr (LT == 0) {
         z[e] = r[e];
-        continue;
+      } else {
+        const int first = lane & ~(LT - 1);
+        const float2* mrow = S.Md + (vact() ? vrow(e) : 0) * LD;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < LT; ++j) {
+          const float qx = __shfl_sync(0xffffffffu, r[e].x, first + j);
+          const float qy = __shfl_sync(0xffffffffu, r[e].y, first + j);
+          const float2 m = vact() ? mrow[j] : make_float2(0.f, 0.f);
+          acc.x = fmaf(m.x, qx, fmaf(-m.y, qy, acc.x));
+          acc.y = fmaf(m.x, qy, fmaf(m.y, qx, acc.y));
+        }
+        z[e] = acc;
       }
-      const int first = lane & ~(L - 1);
-      const float2* mrow = S.Md + vrow(e) * (L + 1);
-      float2 acc = make_float2(0.f, 0.f);
-      for (int j = 0; j < L; ++j) {
-        const float qx = __shfl_sync(0xffffffffu, r[e].x, first + j);
-        const float qy = __shfl_sync(0xffffffffu, r[e].y, first + j);
-        const float2 m = vact() ? mrow[j] : make_float2(0.f, 0.f);
-        acc.x = fmaf(m.x, qx, fmaf(-m.y, qy, acc.x));
-        acc.y = fmaf(m.x, qy, fmaf(m.y, qx, acc.y));
-      }
-      z[e] = acc;
+    }
+  }
+
+  // two sums over the warp at once (interleaved shuffles)
+  __device__ __forceinline__ void dot2_re(const float2 (&a)[E], const float2 (&b)[E], const float2 (&c)[E],
+                                          const float2 (&d)[E], float& s1, float& s2) {
+    s1 = 0.f;
+    s2 = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      s1 += a[e].x * b[e].x + a[e].y * b[e].y;
+      s2 += c[e].x * d[e].x + c[e].y * d[e].y;
+    }
+    if (!vact()) s1 = s2 = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
   }
 
@@ -233,8 +245,9 @@ struct CgWarp {
       precond(r, z);
 #pragma unroll
       for (int e = 0; e < E; ++e) p[e] = z[e];
-      rho = rip(dot_re(r, z));
-      const float rr = dot_re(r, r);
+      float rz, rr;
+      dot2_re(r, z, r, r, rz, rr);
+      rho = rip(rz);
       if (hist && lane == 0) hist[0] = sqrtf(rr);
       pack_p(p);
     }
@@ -246,9 +259,10 @@ struct CgWarp {
       float2 w[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) w[e] = vact() ? S.W[vrow(e)] : make_float2(0.f, 0.f);
-      const float phi = rip(dot_re(p, w));
-      const float rp = (P.L > 0 && P.alpha_num == 0) ? rip(dot_re(r, p)) : rho;
-      const float rho_prev = rp;
+      float phi, rp;
+      dot2_re(p, w, r, p, phi, rp);
+      phi = rip(phi);
+      const float rho_prev = (LT > 0 && P.alpha_num == 0) ? rip(rp) : rho;
       if (live) {
         if (rho_prev == 0.f) {
           st |= 2;
@@ -266,15 +280,14 @@ struct CgWarp {
           r[e] = make_float2(fmaf(-alpha, w[e].x, r[e].x), fmaf(-alpha, w[e].y, r[e].y));
         }
         precond(r, z);
-        const float rho_new = rip(dot_re(r, z));
+        float rz, rr;
+        dot2_re(r, z, r, r, rz, rr);
+        const float rho_new = rip(rz);
         const float beta = rho_new / rho_prev;
 #pragma unroll
         for (int e = 0; e < E; ++e) p[e] = make_float2(fmaf(beta, p[e].x, z[e].x), fmaf(beta, p[e].y, z[e].y));
         rho = rho_new;
-        if (hist) {
-          const float rr = dot_re(r, r);
-          if (lane == 0) hist[it + 1] = sqrtf(rr);
-        }
+        if (hist && lane == 0) hist[it + 1] = sqrtf(rr);
         pack_p(p);
       } else if (hist && lane == 0) {
         hist[it + 1] = hist[it];
@@ -327,58 +340,60 @@ struct CgWarp {
   }
 
   // All warps: Gauss-Jordan inversion of the warp's own L x L diagonal blocks
-  // into S.Md (rows padded to L+1).  Returns nonzero if a pivot was not positive.
+  // into S.Md (rows padded to L+1); lane (block, j) owns column j of its block.
+  // Returns nonzero if a pivot was not positive.
   __device__ int bj_setup() {
-    const int L = P.L;
-    if (L == 0) return 0;
-    const int LD = L + 1;
-    int fail = 0;
-    const int blk = lane / L, j = lane % L;
-    const bool on = lane < 16;
-    const int R0 = row0 + blk * L;  // first row of the block (tile numbering)
-    const int kb = R0 - ps * K;     // its first column (system numbering)
-    if (on)
-      for (int i = 0; i < L; ++i) S.Md[(R0 + i) * LD + j] = S.A[(R0 + i) * (K + 1) + kb + j];
-    __syncwarp();
-    for (int pv = 0; pv < L; ++pv) {
-      const float2 piv = on ? S.Md[(R0 + pv) * LD + pv] : make_float2(1.f, 0.f);
-      if (on && !(piv.x > 0.f && isfinite(piv.x))) fail = 1;
-      const float den = piv.x * piv.x + piv.y * piv.y;
-      const float2 dinv = make_float2(piv.x / den, -piv.y / den);
-      __syncwarp();
-      if (on && j != pv) S.Md[(R0 + pv) * LD + j] = cmul(S.Md[(R0 + pv) * LD + j], dinv);
-      __syncwarp();
-      if (on && j != pv) {
-        const float2 prow = S.Md[(R0 + pv) * LD + j];
-        for (int i = 0; i < L; ++i) {
+    if constexpr (LT == 0) {
+      return 0;
+    } else {
+      int fail = 0;
+      const int blk = lane / LT, j = lane % LT;
+      const bool on = lane < 16;
+      const int R0 = row0 + blk * LT;  // first row of the block (tile numbering)
+      const int kb = R0 - ps * K;      // its first column (system numbering)
+      float2 col[LT];                  // column j of the block, in registers
+#pragma unroll
+      for (int i = 0; i < LT; ++i) col[i] = on ? S.A[(R0 + i) * (K + 1) + kb + j] : make_float2(i == j, 0.f);
+#pragma unroll
+      for (int pv = 0; pv < LT; ++pv) {
+        // column pv lives in lane (blk, pv): its entries are broadcast one at a time
+        const int src = (lane & ~(LT - 1)) + pv;
+        float2 piv;
+        piv.x = __shfl_sync(0xffffffffu, col[pv].x, src);
+        piv.y = __shfl_sync(0xffffffffu, col[pv].y, src);
+        if (on && !(piv.x > 0.f && isfinite(piv.x))) fail = 1;
+        const float den = piv.x * piv.x + piv.y * piv.y;
+        const float2 dinv = make_float2(piv.x / den, -piv.y / den);
+        const float2 prow = cmul(col[pv], dinv);  // scaled pivot-row entry of this column
+#pragma unroll
+        for (int i = 0; i < LT; ++i) {
           if (i == pv) continue;
-          const float2 f = S.Md[(R0 + i) * LD + pv];
-          float2 v = S.Md[(R0 + i) * LD + j];
-          const float2 fp = cmul(f, prow);
-          v.x -= fp.x;
-          v.y -= fp.y;
-          S.Md[(R0 + i) * LD + j] = v;
+          float2 f;
+          f.x = __shfl_sync(0xffffffffu, col[i].x, src);
+          f.y = __shfl_sync(0xffffffffu, col[i].y, src);
+          if (j != pv) {
+            const float2 fp = cmul(f, prow);
+            col[i].x -= fp.x;
+            col[i].y -= fp.y;
+          } else {
+            const float2 v = cmul(f, dinv);
+            col[i] = make_float2(-v.x, -v.y);
+          }
         }
+        col[pv] = (j != pv) ? prow : dinv;
       }
-      __syncwarp();
-      if (on) {
-        if (j == pv) {
-          S.Md[(R0 + pv) * LD + pv] = dinv;
-        } else {
-          const float2 v = cmul(S.Md[(R0 + j) * LD + pv], dinv);
-          S.Md[(R0 + j) * LD + pv] = make_float2(-v.x, -v.y);
-        }
-      }
-      __syncwarp();
+      if (on)
+#pragma unroll
+        for (int i = 0; i < LT; ++i) S.Md[(R0 + i) * LD + j] = col[i];
+      return __any_sync(0xffffffffu, fail);
     }
-    return __any_sync(0xffffffffu, fail);
   }
 };
 
-template <int K, bool BF>
+template <int K, bool BF, int LT>
 __device__ void cg_role(const DetectTcParams& P, tcp::Bars& B, volatile int* abort, uint32_t tmem, uint8_t* cg_base,
                         int wg, int64_t tile0, int64_t tstep) {
-  using CW = CgWarp<K, BF>;
+  using CW = CgWarp<K, BF, LT>;
   constexpr int E = CW::E;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wi = warp - 4 * wg;  // warp within the warpgroup == TMEM lane quadrant
@@ -425,12 +440,12 @@ __device__ void cg_role(const DetectTcParams& P, tcp::Bars& B, volatile int* abo
     // ---- block-Jacobi setup (every warp inverts its own blocks)
     if (W.bj_setup() && lane == 0) atomicOr(&W.S.flag[W.ps], 1);
     W.wg_sync();
-    if (P.L > 0 && W.S.flag[W.ps]) {  // fall back to M_d = I for this system
+    if (LT > 0 && W.S.flag[W.ps]) {  // fall back to M_d = I for this system
       if (W.vec) st |= 8;
       if (lane < 16)
-        for (int i = 0; i < P.L; ++i) {
+        for (int i = 0; i < LT; ++i) {
           const int R = W.row0 + lane;
-          W.S.Md[R * (P.L + 1) + i] = make_float2((R - W.ps * K) % P.L == i ? 1.f : 0.f, 0.f);
+          W.S.Md[R * (LT + 1) + i] = make_float2((R - W.ps * K) % LT == i ? 1.f : 0.f, 0.f);
         }
     }
     W.build_fragments();
@@ -523,7 +538,7 @@ struct Smem {
   uint8_t* cg[2];
 };
 
-template <int K, bool BF>
+template <int K, bool BF, int LT>
 __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(DetectTcParams P) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Smem S;
@@ -534,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(DetectTcParams P
     S.bars = reinterpret_cast<tcp::Bars*>(base + tcp::kStages * tcp::kStageBytes);
     S.tmem_slot = reinterpret_cast<uint32_t*>(S.bars + 1);
     S.abort = reinterpret_cast<volatile int*>(S.tmem_slot + 1);
-    uint8_t* cg = base + ((tcp::kStages * tcp::kStageBytes + sizeof(tcp::Bars) + 16 + 127) & ~size_t(127));
+    uint8_t* cg = base + cg_region_offset();
     S.cg[0] = cg;
     S.cg[1] = cg + cg_smem_bytes(K, P.L);
   }
@@ -570,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(DetectTcParams P
     tcp::converter_role<kConv>(pp, S.stages, *S.bars, S.abort, tile0, tstep, warp - kConv0, lane);
   } else {
     const int wg = warp >> 2;
-    cg_role<K, BF>(P, *S.bars, S.abort, tmem, S.cg[wg], wg, tile0, tstep);
+    cg_role<K, BF, LT>(P, *S.bars, S.abort, tmem, S.cg[wg], wg, tile0, tstep);
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -580,42 +595,33 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(DetectTcParams P
   }
 }
 
-template <int K, bool BF>
+template <int K, bool BF, int LT>
 cudaError_t launch_k(const DetectTcParams& P, int num_sms, cudaStream_t stream) {
   const size_t smem = detect_tc_smem_bytes(K, P.L);
   cudaError_t e =
-      cudaFuncSetAttribute(detect_tc_kernel<K, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(detect_tc_kernel<K, BF, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t grid = P.pipe.ntiles < num_sms ? P.pipe.ntiles : num_sms;
   if (grid <= 0) return cudaSuccess;
-  detect_tc_kernel<K, BF><<<(unsigned)grid, kThreads, smem, stream>>>(P);
+  detect_tc_kernel<K, BF, LT><<<(unsigned)grid, kThreads, smem, stream>>>(P);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool detect_tc_supported(int K, int L) {
-  return (K == 16 || K == 32 || K == 64) && L >= 0 && L <= 16 && (L == 0 || 16 % L == 0);
-}
-
-size_t detect_tc_smem_bytes(int K, int L) {
-  size_t s = 1024 + ((tcp::kStages * tcp::kStageBytes + sizeof(tcp::Bars) + 16 + 127) & ~size_t(127)) +
-             2 * cg_smem_bytes(K, L);
-  return s < 120 * 1024 ? 120 * 1024 : s;
-}
-
-cudaError_t launch_detect_tc(const DetectTcParams& P, int num_sms, int mv_bf16, cudaStream_t stream) {
-  const int K = P.pipe.K;
-  if (mv_bf16) {
-    if (K == 64) return launch_k<64, true>(P, num_sms, stream);
-    if (K == 32) return launch_k<32, true>(P, num_sms, stream);
-    if (K == 16) return launch_k<16, true>(P, num_sms, stream);
-  } else {
-    if (K == 64) return launch_k<64, false>(P, num_sms, stream);
-    if (K == 32) return launch_k<32, false>(P, num_sms, stream);
-    if (K == 16) return launch_k<16, false>(P, num_sms, stream);
+template <int K>
+cudaError_t launch_detect_tc_k(const DetectTcParams& P, int num_sms, int mv_bf16, cudaStream_t stream) {
+  switch (P.L * 2 + (mv_bf16 ? 1 : 0)) {
+    case 0: return launch_k<K, false, 0>(P, num_sms, stream);
+    case 1: return launch_k<K, true, 0>(P, num_sms, stream);
+    case 8: return launch_k<K, false, 4>(P, num_sms, stream);
+    case 9: return launch_k<K, true, 4>(P, num_sms, stream);
+    case 16: return launch_k<K, false, 8>(P, num_sms, stream);
+    case 17: return launch_k<K, true, 8>(P, num_sms, stream);
+    case 32: return launch_k<K, false, 16>(P, num_sms, stream);
+    case 33: return launch_k<K, true, 16>(P, num_sms, stream);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaErrorInvalidValue;
 }
 
 }  // namespace fpcg

@@ -264,16 +264,25 @@ __device__ __forceinline__ void drain_tile(const Pipe& p, uint32_t tmem_acc, int
     c_lo = 32 * q;
     c_hi = 32 * q + 32;
   }
-  for (int cb = c_lo; cb < c_hi; cb += 16) {
-    float v[16];
-    tc::tmem_ld16(lane_base + (uint32_t)cb, v);
+  // 32 columns (2 loads) in flight per wait
+  for (int cg = c_lo; cg < c_hi; cg += 32) {
+    uint32_t r[2][16];
 #pragma unroll
-    for (int m = 0; m < 16; m += 2) {
-      const float other = __shfl_xor_sync(0xffffffffu, v[m + 1], 1);
-      const int j = cb + m;
-      if (sys < p.P && j >= blk0 && j < blk0 + twoK) {
-        const int l = (j - blk0) >> 1;
-        emit(l, odd ? (other - v[m]) : (v[m] + other));
+    for (int u = 0; u < 2; ++u)
+      if (cg + 16 * u < c_hi) tc::tmem_ld16_async(lane_base + (uint32_t)(cg + 16 * u), r[u]);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (cg + 16 * u >= c_hi) break;
+#pragma unroll
+      for (int m = 0; m < 16; m += 2) {
+        const float vm = __uint_as_float(r[u][m]);
+        const float other = __shfl_xor_sync(0xffffffffu, __uint_as_float(r[u][m + 1]), 1);
+        const int j = cg + 16 * u + m;
+        if (sys < p.P && j >= blk0 && j < blk0 + twoK) {
+          const int l = (j - blk0) >> 1;
+          emit(l, odd ? (other - vm) : (vm + other));
+        }
       }
     }
   }
