@@ -13,7 +13,7 @@ struct DetectTcParams {
   tcp::Pipe pipe;
   const double* sigma2;
   const int32_t* qam;
-  int iters, L, refine_steps, refine_iters, alpha_num, ip, resid_comp;
+  int iters, L, refine_steps, refine_iters, alpha_num, ip;
   float2* x_hat;
   uint8_t* sym;
   double* rel_res;

@@ -233,6 +233,7 @@ struct CgWarp {
   // the vector warps return x in xo and their status bits.
   __device__ int solve(const float2* rhs, int iters, float* hist, float2 (&xo)[E]) {
     int st = 0;
+    build_fragments();  // live only inside the solve (the residual between solves needs the registers)
     float2 x[E], r[E], p[E], z[E];
     float rho = 0.f;
     bool live = true;
@@ -298,49 +299,30 @@ struct CgWarp {
     return st;
   }
 
-  // All warps: R[rows of this warp] = b - A X (X in shared memory): lane handles
-  // row row0 + (lane & 15) and half of the columns.
+  // All warps: R[rows of this warp] = b - A X (X in shared memory) with fp32
+  // sums: lane handles row row0 + (lane & 15) and half of the columns.
   __device__ void residual() {
     const int rl = lane & 15, half = lane >> 4;
     const float2* arow = S.A + (row0 + rl) * (K + 1) + half * (K / 2);
     const float2* xs = S.X + ps * K + half * (K / 2);
-    if (!P.resid_comp) {
-      float2 s = make_float2(0.f, 0.f);
+    float2 s = make_float2(0.f, 0.f);
 #pragma unroll 8
-      for (int l = 0; l < K / 2; ++l) {
-        const float2 a = arow[l], x = xs[l];
-        s.x = fmaf(a.x, x.x, fmaf(-a.y, x.y, s.x));
-        s.y = fmaf(a.x, x.y, fmaf(a.y, x.x, s.y));
-      }
-      s.x += __shfl_xor_sync(0xffffffffu, s.x, 16);
-      s.y += __shfl_xor_sync(0xffffffffu, s.y, 16);
-      if (half == 0) {
-        const float2 bb = S.b[row0 + rl];
-        S.R[row0 + rl] = make_float2(bb.x - s.x, bb.y - s.y);
-      }
-      return;
-    }
-    float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
-    if (half == 0) {
-      hr = S.b[row0 + rl].x;
-      hi = S.b[row0 + rl].y;
-    }
     for (int l = 0; l < K / 2; ++l) {
       const float2 a = arow[l], x = xs[l];
-      df_sub_prod(hr, lr, a.x, x.x);
-      df_sub_prod(hr, lr, -a.y, x.y);
-      df_sub_prod(hi, li, a.x, x.y);
-      df_sub_prod(hi, li, a.y, x.x);
+      s.x = fmaf(a.x, x.x, fmaf(-a.y, x.y, s.x));
+      s.y = fmaf(a.x, x.y, fmaf(a.y, x.x, s.y));
     }
-    const float h2 = __shfl_xor_sync(0xffffffffu, hr, 16), l2 = __shfl_xor_sync(0xffffffffu, lr, 16);
-    const float h3 = __shfl_xor_sync(0xffffffffu, hi, 16), l3 = __shfl_xor_sync(0xffffffffu, li, 16);
-    df_add(hr, lr, h2, l2);
-    df_add(hi, li, h3, l3);
-    if (half == 0) S.R[row0 + rl] = make_float2(__fadd_rn(hr, lr), __fadd_rn(hi, li));
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, 16);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, 16);
+    if (half == 0) {
+      const float2 bb = S.b[row0 + rl];
+      S.R[row0 + rl] = make_float2(bb.x - s.x, bb.y - s.y);
+    }
   }
 
-  // All warps: Gauss-Jordan inversion of the warp's own L x L diagonal blocks
-  // into S.Md (rows padded to L+1); lane (block, j) owns column j of its block.
+  // All warps: Gauss-Jordan inversion (in place, no pivoting: the blocks are
+  // Hermitian positive definite) of the warp's own L x L diagonal blocks in
+  // S.Md (rows padded to L+1); lane (block, j) owns column j of its block.
   // Returns nonzero if a pivot was not positive.
   __device__ int bj_setup() {
     if constexpr (LT == 0) {
@@ -351,40 +333,47 @@ struct CgWarp {
       const bool on = lane < 16;
       const int R0 = row0 + blk * LT;  // first row of the block (tile numbering)
       const int kb = R0 - ps * K;      // its first column (system numbering)
-      float2 col[LT];                  // column j of the block, in registers
+      float2* M = S.Md + R0 * LD;      // M[i*LD + c] = block entry (i, c)
+      if (on)
 #pragma unroll
-      for (int i = 0; i < LT; ++i) col[i] = on ? S.A[(R0 + i) * (K + 1) + kb + j] : make_float2(i == j, 0.f);
+        for (int i = 0; i < LT; ++i) M[i * LD + j] = S.A[(R0 + i) * (K + 1) + kb + j];
+      __syncwarp();
 #pragma unroll
       for (int pv = 0; pv < LT; ++pv) {
-        // column pv lives in lane (blk, pv): its entries are broadcast one at a time
-        const int src = (lane & ~(LT - 1)) + pv;
-        float2 piv;
-        piv.x = __shfl_sync(0xffffffffu, col[pv].x, src);
-        piv.y = __shfl_sync(0xffffffffu, col[pv].y, src);
+        const float2 piv = on ? M[pv * LD + pv] : make_float2(1.f, 0.f);
         if (on && !(piv.x > 0.f && isfinite(piv.x))) fail = 1;
         const float den = piv.x * piv.x + piv.y * piv.y;
         const float2 dinv = make_float2(piv.x / den, -piv.y / den);
-        const float2 prow = cmul(col[pv], dinv);  // scaled pivot-row entry of this column
+        float2 prow = make_float2(0.f, 0.f);
+        if (on && j != pv) prow = cmul(M[pv * LD + j], dinv);  // scaled pivot row
+        float2 f[LT];
 #pragma unroll
-        for (int i = 0; i < LT; ++i) {
-          if (i == pv) continue;
-          float2 f;
-          f.x = __shfl_sync(0xffffffffu, col[i].x, src);
-          f.y = __shfl_sync(0xffffffffu, col[i].y, src);
+        for (int i = 0; i < LT; ++i) f[i] = on ? M[i * LD + pv] : make_float2(0.f, 0.f);  // pivot column
+        __syncwarp();
+        if (on) {
           if (j != pv) {
-            const float2 fp = cmul(f, prow);
-            col[i].x -= fp.x;
-            col[i].y -= fp.y;
+#pragma unroll
+            for (int i = 0; i < LT; ++i) {
+              if (i == pv) continue;
+              float2 v = M[i * LD + j];
+              const float2 fp = cmul(f[i], prow);
+              v.x -= fp.x;
+              v.y -= fp.y;
+              M[i * LD + j] = v;
+            }
+            M[pv * LD + j] = prow;
           } else {
-            const float2 v = cmul(f, dinv);
-            col[i] = make_float2(-v.x, -v.y);
+#pragma unroll
+            for (int i = 0; i < LT; ++i) {
+              if (i == pv) continue;
+              const float2 v = cmul(f[i], dinv);
+              M[i * LD + pv] = make_float2(-v.x, -v.y);
+            }
+            M[pv * LD + pv] = dinv;
           }
         }
-        col[pv] = (j != pv) ? prow : dinv;
+        __syncwarp();
       }
-      if (on)
-#pragma unroll
-        for (int i = 0; i < LT; ++i) S.Md[(R0 + i) * LD + j] = col[i];
       return __any_sync(0xffffffffu, fail);
     }
   }
@@ -448,7 +437,6 @@ __device__ void cg_role(const DetectTcParams& P, tcp::Bars& B, volatile int* abo
           W.S.Md[R * (LT + 1) + i] = make_float2((R - W.ps * K) % LT == i ? 1.f : 0.f, 0.f);
         }
     }
-    W.build_fragments();
     W.wg_sync();
     // ---- main solve
     float* hist = (P.res_hist && W.valid && W.vec) ? P.res_hist + W.sys * (int64_t)(P.iters + 1) : nullptr;

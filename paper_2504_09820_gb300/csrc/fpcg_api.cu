@@ -55,7 +55,7 @@ bool force_simt() {
 }
 
 bool uses_tc(int k, int block_L, const fpcg_precision* prec) {
-  return !force_simt() && prec->w == FPCG_FP32 && (prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) &&
+  return !force_simt() && prec->w == FPCG_FP32 && prec->resid == FPCG_FP32 && (prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) &&
          (prec->mv == FPCG_BF16 || prec->mv == FPCG_FP16) && fpcg::detect_tc_supported(k, block_L);
 }
 
@@ -109,7 +109,6 @@ int run(const void* H, const void* y, const double* sigma2, const int32_t* qam_o
     T.refine_iters = refine_iters;
     T.alpha_num = prec->alpha_num;
     T.ip = prec->ip;
-    T.resid_comp = prec->resid == FPCG_FP64;
     T.x_hat = (float2*)x_hat;
     T.sym = sym_idx;
     T.rel_res = rel_res;

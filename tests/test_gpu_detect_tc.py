@@ -48,9 +48,21 @@ CASES = [
     (32, "fp16", "fp16", 16, 6, 1),
     (16, "bf16", "bf16", 4, 8, 1),
     (16, "bf16", "bf16", 0, 12, 1),
-    (64, "bf16", "bf16", 1, 6, 1),
-    (64, "bf16", "bf16", 2, 6, 1),
+    (64, "bf16", "bf16", 16, 4, 1),
+    (32, "bf16", "bf16", 4, 6, 2),
 ]
+
+
+def test_routing_to_simt():
+    """Configurations the fused kernel does not take run on the SIMT kernel."""
+    bf = dict(gram="bf16", mv="bf16")
+    assert F.fpcg_path(64, 1, F.precision(**bf)) == F.PATH_SIMT          # L not in {0,4,8,16}
+    assert F.fpcg_path(64, 2, F.precision(**bf)) == F.PATH_SIMT
+    assert F.fpcg_path(128, 8, F.precision(**bf)) == F.PATH_SIMT         # K > 64
+    assert F.fpcg_path(8, 4, F.precision(**bf)) == F.PATH_SIMT           # K < 16
+    assert F.fpcg_path(64, 8, F.precision(**bf, resid="fp64")) == F.PATH_SIMT  # compensated residual
+    assert F.fpcg_path(64, 8, F.precision(gram="bf16", mv="e4m3")) == F.PATH_SIMT
+    assert F.fpcg_path(64, 8, F.precision(**bf)) == F.PATH_TENSOR_CORE
 
 
 @pytest.mark.parametrize("K,gram,mv,L,iters,refine", CASES)
@@ -91,11 +103,11 @@ def test_fused_headline_config_full_size_sampled():
     assert abs(e_gpu / e_ref - 1) < 0.05
 
 
-def test_fused_hist_alpha_ip_and_compensated_residual():
+def test_fused_hist_alpha_and_ip_rounding():
     d = wl.generate(wl.Spec(N=128, K=32, batch=700, rho=0.7, qam=16, snr_db=16.0, seed=77))
     for pk, L in ((dict(gram="bf16", mv="bf16", alpha_num=1, refine_steps=1), 8),
                   (dict(gram="bf16", mv="bf16", ip="bf16", refine_steps=1), 8),
-                  (dict(gram="fp16", mv="fp16", resid="fp64", refine_steps=2), 4)):
+                  (dict(gram="fp16", mv="fp16", refine_steps=2), 4)):
         res = gpu_detect(d, 6, pk, L=L, hist=True)
         ref = oracle_detect(d, 6, pk, L=L)
         _check(d, res, ref, tol=(5e-3 if pk.get("ip") == "bf16" else 2e-3))
