@@ -203,7 +203,8 @@ FPCG_API int fpcg_gram(const void* H, const void* y, const double* sigma2, int32
  * fpcg_path -- which kernel fpcg_detect / fpbjcg_detect (block_L = 0 for
  * FP-CG) would use for this configuration: FPCG_PATH_TENSOR_CORE (the fused
  * tcgen05 Gram + mma.sync CG kernel: gram and mv in {BF16, FP16}, w = resid
- * = FP32, K in {16, 32, 64}, L in {0, 4, 8, 16}) or FPCG_PATH_SIMT (one CTA per system, every
+ * = FP32, K in {16, 32, 64}, L in {0, 4, 8, 16}, N even; H and y must also be
+ * 16-byte aligned, which this query cannot see) or FPCG_PATH_SIMT (one CTA per system, every
  * other configuration); FPCG_EINVAL (negative) for an invalid configuration.
  * Setting the environment variable FPCG_FORCE_SIMT=1 makes every call take
  * the SIMT kernel (same results within rounding; for A/B comparisons).
@@ -211,7 +212,7 @@ FPCG_API int fpcg_gram(const void* H, const void* y, const double* sigma2, int32
  */
 #define FPCG_PATH_SIMT 0
 #define FPCG_PATH_TENSOR_CORE 1
-FPCG_API int fpcg_path(int32_t k, int32_t block_L, const fpcg_precision* prec);
+FPCG_API int fpcg_path(int32_t n_rx, int32_t k, int32_t block_L, const fpcg_precision* prec);
 
 /* Human-readable text for a return code (static storage). */
 FPCG_API const char* fpcg_strerror(int code);

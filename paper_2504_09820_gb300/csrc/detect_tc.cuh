@@ -37,7 +37,7 @@ __host__ __device__ inline size_t cg_smem_bytes(int K, int L) {
 
 // Offset of the first CG region after the stages, barriers and TMEM slot.
 __host__ __device__ inline size_t cg_region_offset() {
-  return (tcp::kStages * tcp::kStageBytes + sizeof(tcp::Bars) + 16 + 127) & ~size_t(127);
+  return (tcp::kPipeBytes + sizeof(tcp::Bars) + 16 + 127) & ~size_t(127);
 }
 
 inline size_t detect_tc_smem_bytes(int K, int L) {

@@ -5,7 +5,8 @@
 //
 //   warps 0-3    CG warpgroup 0: tiles 0, 2, 4, ... of this CTA (TMEM buffer 0)
 //   warps 4-7    CG warpgroup 1: tiles 1, 3, 5, ...             (TMEM buffer 1)
-//   warps 8-14   converters: H, y -> bf16/fp16 swizzled stages
+//   warps 8-13   converters: FP32 stages -> bf16/fp16 swizzled operand stages
+//   warp 14      TMA producer of the FP32 stages
 //   warp 15      TMEM allocation and the UMMA-issuing thread
 //
 // Gram + matched filter (Section II, eq. inversion) come out of the tcgen05
@@ -37,8 +38,9 @@ namespace {
 
 constexpr int kThreads = 16 * 32;
 constexpr int kMmaWarp = 15;
+constexpr int kProdWarp = 14;
 constexpr int kConv0 = 8;
-constexpr int kConv = 7;  // converter warps 8-14
+constexpr int kConv = 6;  // converter warps 8-13
 
 // Per-warpgroup shared memory (rows are the 64 rows of a tile: row = ps*K + k).
 struct CgSmem {
@@ -519,7 +521,7 @@ __device__ void cg_role(const DetectTcParams& P, tcp::Bars& B, volatile int* abo
 }
 
 struct Smem {
-  uint8_t* stages;
+  uint8_t* pipe;
   tcp::Bars* bars;
   uint32_t* tmem_slot;
   volatile int* abort;
@@ -527,14 +529,14 @@ struct Smem {
 };
 
 template <int K, bool BF, int LT>
-__global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(DetectTcParams P) {
+__global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_constant__ DetectTcParams P) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Smem S;
   {
     const uint32_t a = tc::smem_u32(smem_raw);
     uint8_t* base = smem_raw + ((1024u - (a & 1023u)) & 1023u);
-    S.stages = base;
-    S.bars = reinterpret_cast<tcp::Bars*>(base + tcp::kStages * tcp::kStageBytes);
+    S.pipe = base;
+    S.bars = reinterpret_cast<tcp::Bars*>(base + tcp::kPipeBytes);
     S.tmem_slot = reinterpret_cast<uint32_t*>(S.bars + 1);
     S.abort = reinterpret_cast<volatile int*>(S.tmem_slot + 1);
     uint8_t* cg = base + cg_region_offset();
@@ -544,17 +546,9 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(DetectTcParams P
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const tcp::Pipe& pp = P.pipe;
   for (int i = threadIdx.x; i < tcp::kStages * tcp::kStageBytes / 16; i += kThreads)
-    reinterpret_cast<uint4*>(S.stages)[i] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(tcp::stage16(S.pipe, 0))[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < tcp::kStages; ++s) {
-      tc::mbar_init(&S.bars->full[s], kConv);
-      tc::mbar_init(&S.bars->empty[s], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&S.bars->acc_full[b], 1);
-      tc::mbar_init(&S.bars->acc_empty[b], 1);
-    }
-    tc::mbar_init(&S.bars->done, 1);
+    tcp::init_bars(*S.bars, kConv);
     *S.abort = 0;
     tc::fence_mbar_init();
   }
@@ -567,10 +561,13 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(DetectTcParams P
   const int64_t tile0 = blockIdx.x, tstep = gridDim.x;
 
   if (warp == kMmaWarp) {
-    if (lane == 0) tcp::mma_role(pp, S.stages, *S.bars, S.abort, tmem, tile0, tstep);
+    if (lane == 0) tcp::mma_role(pp, S.pipe, *S.bars, S.abort, tmem, tile0, tstep);
+    __syncwarp();
+  } else if (warp == kProdWarp) {
+    if (lane == 0) tcp::producer_role(pp, S.pipe, *S.bars, S.abort, tile0, tstep);
     __syncwarp();
   } else if (warp >= kConv0) {
-    tcp::converter_role<kConv>(pp, S.stages, *S.bars, S.abort, tile0, tstep, warp - kConv0, lane);
+    tcp::converter_role<kConv>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, warp - kConv0, lane);
   } else {
     const int wg = warp >> 2;
     cg_role<K, BF, LT>(P, *S.bars, S.abort, tmem, S.cg[wg], wg, tile0, tstep);

@@ -91,7 +91,7 @@ int run(const void* H, const void* y, const double* sigma2, const int32_t* qam_o
     if (e != cudaSuccess) return cuda_fail(e);
   }
   if (batch == 0) return FPCG_OK;
-  const bool tc_ok = !Ain && uses_tc(k, block_L, prec);
+  const bool tc_ok = !Ain && uses_tc(k, block_L, prec) && fpcg::tma_pipe_ok(H, y, n_rx);
   if (tc_ok) {
     int sms = 0;
     rc = device_sms(&sms);
@@ -100,7 +100,8 @@ int run(const void* H, const void* y, const double* sigma2, const int32_t* qam_o
     if (rc) return rc;
     fpcg::DetectTcParams T;
     memset(&T, 0, sizeof(T));
-    T.pipe = fpcg::make_pipe((const float2*)H, (const float2*)y, n_rx, k, batch, prec->gram == FPCG_BF16);
+    if (!fpcg::make_pipe(&T.pipe, (const float2*)H, (const float2*)y, n_rx, k, batch, prec->gram == FPCG_BF16))
+      return FPCG_ENOTSUP;
     T.sigma2 = sigma2;
     T.qam = qam_order;
     T.iters = iters;
@@ -195,14 +196,16 @@ int fpcg_gram(const void* H, const void* y, const double* sigma2, int32_t n_rx, 
     if (e != cudaSuccess) return cuda_fail(e);
   }
   if (batch == 0) return FPCG_OK;
-  if ((gram == FPCG_BF16 || gram == FPCG_FP16) && fpcg::gram_tc_supported(k)) {
+  if ((gram == FPCG_BF16 || gram == FPCG_FP16) && fpcg::gram_tc_supported(k) && fpcg::tma_pipe_ok(H, y, n_rx) &&
+      !force_simt()) {
     int sms = 0;
     int rc = device_sms(&sms);
     if (rc) return rc;
     rc = check_device_smem(fpcg::gram_tc_smem_bytes());
     if (rc) return rc;
     fpcg::GramTcParams P;
-    P.pipe = fpcg::make_pipe((const float2*)H, (const float2*)y, n_rx, k, batch, gram == FPCG_BF16);
+    if (!fpcg::make_pipe(&P.pipe, (const float2*)H, (const float2*)y, n_rx, k, batch, gram == FPCG_BF16))
+      return FPCG_ENOTSUP;
     P.sigma2 = sigma2;
     P.A = (float2*)A;
     P.b = (float2*)b;
@@ -230,10 +233,11 @@ int fpcg_gram(const void* H, const void* y, const double* sigma2, int32_t n_rx, 
   return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
 }
 
-int fpcg_path(int32_t k, int32_t block_L, const fpcg_precision* prec) {
+int fpcg_path(int32_t n_rx, int32_t k, int32_t block_L, const fpcg_precision* prec) {
   if (check_prec(prec)) return -FPCG_EINVAL;
-  if (k < 1 || k > 128 || block_L < 0 || block_L > 32 || (block_L > 0 && k % block_L)) return -FPCG_EINVAL;
-  return uses_tc(k, block_L, prec) ? FPCG_PATH_TENSOR_CORE : FPCG_PATH_SIMT;
+  if (k < 1 || k > 128 || n_rx < k || block_L < 0 || block_L > 32 || (block_L > 0 && k % block_L))
+    return -FPCG_EINVAL;
+  return uses_tc(k, block_L, prec) && n_rx % 2 == 0 ? FPCG_PATH_TENSOR_CORE : FPCG_PATH_SIMT;
 }
 
 const char* fpcg_strerror(int code) {

@@ -3,8 +3,9 @@
 // rounding and fp32 accumulation (Section II, eq. inversion), written to
 // global memory.  Persistent kernel, one CTA per SM, warp-specialised:
 //   warp 0      TMEM allocation and the UMMA-issuing thread,
+//   warp 1      TMA producer,
 //   warps 4-7   drain warpgroup (TMEM -> combine -> A, b in global memory),
-//   warps 8-15  converters (H, y -> bf16/fp16 swizzled stages).
+//   warps 8-15  converters (FP32 stages -> bf16/fp16 swizzled operand stages).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -19,7 +20,7 @@ constexpr int kThreads = 512;
 constexpr int kConv = 8;  // converter warps 8-15
 
 struct Smem {
-  uint8_t* stages;
+  uint8_t* pipe;
   tcp::Bars* bars;
   uint32_t* tmem_slot;
   volatile int* abort;
@@ -29,31 +30,23 @@ __device__ inline Smem carve(uint8_t* raw) {
   Smem s;
   const uint32_t a = tc::smem_u32(raw);
   uint8_t* base = raw + ((1024u - (a & 1023u)) & 1023u);
-  s.stages = base;
-  s.bars = reinterpret_cast<tcp::Bars*>(base + tcp::kStages * tcp::kStageBytes);
+  s.pipe = base;
+  s.bars = reinterpret_cast<tcp::Bars*>(base + tcp::kPipeBytes);
   s.tmem_slot = reinterpret_cast<uint32_t*>(s.bars + 1);
   s.abort = reinterpret_cast<volatile int*>(s.tmem_slot + 1);
   return s;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcParams P) {
+__global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const __grid_constant__ GramTcParams P) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Smem S = carve(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const tcp::Pipe& pp = P.pipe;
 
   for (int i = threadIdx.x; i < tcp::kStages * tcp::kStageBytes / 16; i += kThreads)
-    reinterpret_cast<uint4*>(S.stages)[i] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(tcp::stage16(S.pipe, 0))[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < tcp::kStages; ++s) {
-      tc::mbar_init(&S.bars->full[s], kConv);
-      tc::mbar_init(&S.bars->empty[s], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&S.bars->acc_full[b], 1);
-      tc::mbar_init(&S.bars->acc_empty[b], 1);
-    }
-    tc::mbar_init(&S.bars->done, 1);
+    tcp::init_bars(*S.bars, kConv);
     *S.abort = 0;
     tc::fence_mbar_init();
   }
@@ -66,10 +59,13 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcParams P) {
   const int64_t tile0 = blockIdx.x, tstep = gridDim.x;
 
   if (warp == 0) {
-    if (lane == 0) tcp::mma_role(pp, S.stages, *S.bars, S.abort, tmem, tile0, tstep);
+    if (lane == 0) tcp::mma_role(pp, S.pipe, *S.bars, S.abort, tmem, tile0, tstep);
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) tcp::producer_role(pp, S.pipe, *S.bars, S.abort, tile0, tstep);
     __syncwarp();
   } else if (warp >= 8) {
-    tcp::converter_role<kConv>(pp, S.stages, *S.bars, S.abort, tile0, tstep, warp - 8, lane);
+    tcp::converter_role<kConv>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, warp - 8, lane);
   } else if (warp >= 4) {
     const int q = warp - 4;
     const int row = 32 * q + lane;
@@ -123,25 +119,10 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcParams P) {
 bool gram_tc_supported(int K) { return K == 8 || K == 16 || K == 32 || K == 64; }
 
 size_t gram_tc_smem_bytes() {
-  size_t s = 1024 + tcp::kStages * tcp::kStageBytes + sizeof(tcp::Bars) + 16;
+  size_t s = 1024 + tcp::kPipeBytes + sizeof(tcp::Bars) + 16;
   // at least half of the SM's shared memory, so one CTA (and one 512-column
   // TMEM allocation) per SM
   return s < 120 * 1024 ? 120 * 1024 : s;
-}
-
-tcp::Pipe make_pipe(const float2* H, const float2* y, int N, int K, int64_t batch, int bf16) {
-  tcp::Pipe p;
-  p.H = H;
-  p.y = y;
-  p.N = N;
-  p.K = K;
-  p.P = 64 / K;
-  p.nchunks = (N + tcp::kChunk - 1) / tcp::kChunk;
-  p.batch = batch;
-  p.ntiles = (batch + p.P - 1) / p.P;
-  p.bf16 = bf16;
-  p.vec4 = (N % 2 == 0) && ((uintptr_t)H % 16 == 0) && ((uintptr_t)y % 16 == 0);
-  return p;
 }
 
 cudaError_t launch_gram_tc(const GramTcParams& P, int num_sms, cudaStream_t stream) {

@@ -19,7 +19,11 @@ struct GramTcParams {
 
 bool gram_tc_supported(int K);
 size_t gram_tc_smem_bytes();
-tcp::Pipe make_pipe(const float2* H, const float2* y, int N, int K, int64_t batch, int bf16);
+// The TMA pipeline needs N even and 16-byte aligned H and y.
+bool tma_pipe_ok(const void* H, const void* y, int N);
+// Fill the pipeline description (tensor maps included); false if the driver
+// refused a tensor map.
+bool make_pipe(tcp::Pipe* p, const float2* H, const float2* y, int N, int K, int64_t batch, int bf16);
 cudaError_t launch_gram_tc(const GramTcParams& P, int num_sms, cudaStream_t stream);
 
 }  // namespace fpcg

@@ -15,11 +15,18 @@
 // of D are ignored.  Operands are bf16 or fp16 (the u_gram rounding), the
 // accumulator fp32.
 //
-// Stages: 64 antennas each, rows of 128 bytes in the 128B-swizzled K-major
+// Data movement.  A producer thread streams H and y with 2-D TMA loads
+// (cp.async.bulk.tensor, FP32 boxes of 32 antennas x 64 columns of the
+// [batch*K][2N] real view of H, and 32 antennas x P systems of y) into a ring
+// of FP32 stages, counted on `full32` by transaction bytes; out-of-range boxes
+// read as zeros.  Converter warps turn two FP32 stages (64 antennas) into one
+// bf16/fp16 operand stage: rows of 128 bytes in the 128B-swizzled K-major
 // layout, 144 rows (128 of X, 16 of Y) = 18 KiB.  Roles:
-//   converter warps: coalesced 16-byte loads of H and y, round to bf16/fp16,
-//                    store into the stage, fence.proxy.async, arrive `full`;
-//   MMA thread:      wait `full`, 4 UMMAs (K = 16 each), commit to `empty`;
+//   producer:        wait `empty32`, expect_tx, two TMA loads into `full32`;
+//   converter warps: wait `full32` (two) and `empty16`, read FP32, round,
+//                    store swizzled, fence.proxy.async, arrive `full16` and
+//                    release the FP32 stages (`empty32`);
+//   MMA thread:      wait `full16`, 4 UMMAs (K = 16 each), commit to `empty16`;
 //                    after a tile's last stage commit to `acc_full`;
 //   drain warps:     wait `acc_full`, tcgen05.ld, combine, consume, arrive
 //                    `acc_empty`.
@@ -27,6 +34,7 @@
 // leave their loops.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -36,23 +44,31 @@
 namespace fpcg {
 namespace tcp {
 
-constexpr int kStages = 4;
+constexpr int kStages32 = 4;                   // FP32 staging ring
+constexpr int kChunk32 = 32;                   // antennas per FP32 stage
+constexpr int kStage32HBytes = 64 * 64 * 4;    // 64 columns x 64 floats
+constexpr int kStage32Bytes = kStage32HBytes + 8 * 64 * 4;  // + y of up to 8 systems
+constexpr int kStages = 2;                     // bf16/fp16 operand stages
 constexpr int kStageRows = 144;
 constexpr int kStageBytes = kStageRows * 128;  // 18432, a multiple of 1024
-constexpr int kChunk = 64;                     // antennas per stage
+constexpr int kChunk = 64;                     // antennas per operand stage
 constexpr int kMmaN = 144;
 constexpr int kAccCols = 256;                  // TMEM columns per accumulator buffer
+constexpr int kPipeBytes = kStages32 * kStage32Bytes + kStages * kStageBytes;
 
 struct Pipe {
+  CUtensorMap tmH;   // FP32 view of H: dims {2N, batch*K}, box {64, 64}
+  CUtensorMap tmY;   // FP32 view of y: dims {2N, batch}, box {64, P}
   const float2* H;
   const float2* y;
-  int N, K, P, nchunks;
+  int N, K, P, nchunks;   // nchunks = operand stages per tile = ceil(N / 64)
   int64_t batch, ntiles;
   int bf16;
-  int vec4;  // 16-byte loads allowed (N even, 16-byte aligned bases)
 };
 
 struct Bars {
+  uint64_t full32[kStages32];
+  uint64_t empty32[kStages32];
   uint64_t full[kStages];
   uint64_t empty[kStages];
   uint64_t acc_full[2];
@@ -69,142 +85,103 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int bf16) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Load two consecutive complex samples v[n], v[n+1] of a length-N vector
-// (zero beyond N or when !valid).
-__device__ __forceinline__ float4 load2(const float2* v, int n, int N, bool valid, int vec4) {
-  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (!valid) return r;
-  if (vec4 && n + 1 < N) return __ldcs(reinterpret_cast<const float4*>(v + n));
-  if (n < N) {
-    float2 a = __ldcs(v + n);
-    r.x = a.x;
-    r.y = a.y;
-  }
-  if (n + 1 < N) {
-    float2 b = __ldcs(v + n + 1);
-    r.z = b.x;
-    r.w = b.y;
-  }
-  return r;
+__device__ __forceinline__ uint8_t* stage32(uint8_t* pipe_base, int s) { return pipe_base + s * kStage32Bytes; }
+__device__ __forceinline__ uint8_t* stage16(uint8_t* pipe_base, int t) {
+  return pipe_base + kStages32 * kStage32Bytes + t * kStageBytes;
 }
 
-// Converter warp `cw` of NC: its columns of the tile are cl = cw + NC m, and
-// it loads y of systems cw, cw + NC of the tile (P <= 8 <= 2 NC).
-template <int NC>
-struct ConvRegs {
-  static constexpr int NM = (64 + NC - 1) / NC;
-  float4 h[NM];
-  float4 y[2];
-};
-
-template <int NC>
-__device__ __forceinline__ void conv_load(const Pipe& p, int64_t tile, int c, int cw, int lane, ConvRegs<NC>& R) {
-  const int n = c * kChunk + 2 * lane;
-  const int64_t col0 = tile * (int64_t)(p.P * p.K);
-  const int64_t ncols = p.batch * (int64_t)p.K;
-#pragma unroll
-  for (int m = 0; m < ConvRegs<NC>::NM; ++m) {
-    const int cl = cw + NC * m;
-    const int64_t col = col0 + cl;
-    const bool ok = cl < p.P * p.K && col < ncols;
-    R.h[m] = load2(p.H + (ok ? col : 0) * (int64_t)p.N, n, p.N, ok, p.vec4);
-  }
-#pragma unroll
-  for (int m = 0; m < 2; ++m) {
-    const int ps = cw + NC * m;
-    const int64_t sys = tile * p.P + ps;
-    const bool oky = ps < p.P && sys < p.batch;
-    R.y[m] = load2(p.y + (oky ? sys : 0) * (int64_t)p.N, n, p.N, oky, p.vec4);
-  }
-}
-
-template <int NC>
-__device__ __forceinline__ void conv_store(const Pipe& p, uint8_t* stage, int cw, int lane, const ConvRegs<NC>& R) {
-  // k-positions 2*lane, 2*lane+1 of the 64-antenna chunk
-  const uint32_t kpos = 2u * lane;
-#pragma unroll
-  for (int m = 0; m < ConvRegs<NC>::NM; ++m) {
-    const int cl = cw + NC * m;
-    if (cl < p.P * p.K) {
-      const float4 v = R.h[m];
-      *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(2 * cl, kpos)) = pack2(v.x, v.z, p.bf16);
-      *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(2 * cl + 1, kpos)) = pack2(v.y, v.w, p.bf16);
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < 2; ++m) {
-    const int ps = cw + NC * m;
-    if (ps < p.P) {
-      const float4 v = R.y[m];
-      *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(128 + 2 * ps, kpos)) = pack2(v.x, v.z, p.bf16);
-      *reinterpret_cast<uint32_t*>(stage + tc::sw128_offset(129 + 2 * ps, kpos)) = pack2(v.y, v.w, p.bf16);
-    }
-  }
-}
-
-// Ask the bulk-copy engine to pull a tile's H and y into L2 ahead of the
-// converters' loads (16-byte granularity, clamped to the arrays).
+// Ask the bulk-copy engine to pull a tile's H and y into L2 ahead of the TMA
+// loads (16-byte granularity, clamped to the arrays).
 __device__ inline void prefetch_tile(const Pipe& p, int64_t tile) {
   if (tile >= p.ntiles) return;
   const int64_t col0 = tile * (int64_t)(p.P * p.K);
   const int64_t cols = min((int64_t)(p.P * p.K), p.batch * (int64_t)p.K - col0);
   const char* h = reinterpret_cast<const char*>(p.H + col0 * (int64_t)p.N);
   int64_t bytes = (cols * (int64_t)p.N * 8) & ~int64_t(15);
-  if ((reinterpret_cast<uintptr_t>(h) & 15) == 0)
-    for (int64_t o = 0; o < bytes; o += 32768)
-      tc::prefetch_l2(h + o, (uint32_t)min(bytes - o, (int64_t)32768));
+  for (int64_t o = 0; o < bytes; o += 32768) tc::prefetch_l2(h + o, (uint32_t)min(bytes - o, (int64_t)32768));
   const int64_t s0 = tile * (int64_t)p.P;
   const int64_t ns = min((int64_t)p.P, p.batch - s0);
   const char* yy = reinterpret_cast<const char*>(p.y + s0 * (int64_t)p.N);
   bytes = (ns * (int64_t)p.N * 8) & ~int64_t(15);
-  if ((reinterpret_cast<uintptr_t>(yy) & 15) == 0 && bytes > 0) tc::prefetch_l2(yy, (uint32_t)bytes);
+  if (bytes > 0) tc::prefetch_l2(yy, (uint32_t)bytes);
 }
 
-// Converter role: tiles this CTA owns are tile0, tile0 + tstep, ...
+// Producer role (one thread): tiles this CTA owns are tile0, tile0 + tstep, ...
+__device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B, volatile int* abort,
+                                     int64_t tile0, int64_t tstep) {
+  const uint32_t tx = kStage32HBytes + 64 * 4 * p.P;
+  uint32_t u = 0;
+  if (tile0 < p.ntiles) prefetch_tile(p, tile0 + tstep);
+  for (int64_t tile = tile0; tile < p.ntiles; tile += tstep) {
+    prefetch_tile(p, tile + 2 * tstep);
+    for (int c = 0; c < 2 * p.nchunks; ++c, ++u) {
+      const uint32_t s = u % kStages32, q = u / kStages32;
+      if (q > 0 && !tc::mbar_wait(&B.empty32[s], (q - 1) & 1u, abort)) {
+        *abort = 1;
+        return;
+      }
+      uint8_t* st = stage32(pipe_base, (int)s);
+      tc::mbar_expect_tx(&B.full32[s], tx);
+      tc::tma_load_2d(st, &p.tmH, 64 * c, (int)(tile * 64), &B.full32[s]);
+      tc::tma_load_2d(st + kStage32HBytes, &p.tmY, 64 * c, (int)(tile * p.P), &B.full32[s]);
+    }
+  }
+}
+
+// Converter warp `cw` of NC: columns cl = cw + NC m of the tile and y of
+// systems cw + NC m.  Lane l fills k-positions 2l, 2l+1 of the operand stage
+// (antennas 2l, 2l+1 of the 64), read from FP32 stage l/16 at antenna 2(l%16).
 template <int NC>
-__device__ inline void converter_role(const Pipe& p, uint8_t* stages, Bars& B, volatile int* abort,
+__device__ inline void converter_role(const Pipe& p, uint8_t* pipe_base, Bars& B, volatile int* abort,
                                       int64_t tile0, int64_t tstep, int cw, int lane) {
-  ConvRegs<NC> cur, nxt;
-  int64_t j = 0;
-  int c = 0;
-  int64_t tile = tile0;
-  if (tile >= p.ntiles) return;
-  const bool prefetcher = cw == 0 && lane == 0;
-  if (prefetcher) prefetch_tile(p, tile + tstep);
-  conv_load(p, tile, c, cw, lane, cur);
-  uint32_t u = 0;  // stage use counter
-  while (true) {
-    if (prefetcher && c == 0) prefetch_tile(p, tile + 2 * tstep);
-    // prefetch the next chunk's loads before waiting for the stage
-    int c2 = c + 1;
-    int64_t tile2 = tile, j2 = j;
-    if (c2 == p.nchunks) {
-      c2 = 0;
-      tile2 = tile + tstep;
-      ++j2;
+  constexpr int NM = (64 + NC - 1) / NC;
+  uint32_t u32 = 0, u16 = 0;
+  const int half = lane >> 4, ll = lane & 15;
+  const uint32_t kpos = 2u * lane;
+  for (int64_t tile = tile0; tile < p.ntiles; tile += tstep) {
+    for (int c = 0; c < p.nchunks; ++c, u32 += 2, ++u16) {
+      const uint32_t s0 = u32 % kStages32, q0 = u32 / kStages32;
+      const uint32_t s1 = (u32 + 1) % kStages32, q1 = (u32 + 1) / kStages32;
+      const uint32_t t = u16 % kStages, qt = u16 / kStages;
+      if (!tc::mbar_wait(&B.full32[s0], q0 & 1u, abort) || !tc::mbar_wait(&B.full32[s1], q1 & 1u, abort) ||
+          (qt > 0 && !tc::mbar_wait(&B.empty[t], (qt - 1) & 1u, abort))) {
+        *abort = 1;
+        return;
+      }
+      const float* src = reinterpret_cast<const float*>(stage32(pipe_base, (int)(half ? s1 : s0)));
+      uint8_t* dst = stage16(pipe_base, (int)t);
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        const int cl = cw + NC * m;
+        if (cl < p.P * p.K) {
+          const float4 v = *reinterpret_cast<const float4*>(src + cl * 64 + 4 * ll);
+          *reinterpret_cast<uint32_t*>(dst + tc::sw128_offset(2 * cl, kpos)) = pack2(v.x, v.z, p.bf16);
+          *reinterpret_cast<uint32_t*>(dst + tc::sw128_offset(2 * cl + 1, kpos)) = pack2(v.y, v.w, p.bf16);
+        }
+      }
+      const float* ysrc = src + kStage32HBytes / 4;
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        const int ps = cw + NC * m;
+        if (ps < p.P) {
+          const float4 v = *reinterpret_cast<const float4*>(ysrc + ps * 64 + 4 * ll);
+          *reinterpret_cast<uint32_t*>(dst + tc::sw128_offset(128 + 2 * ps, kpos)) = pack2(v.x, v.z, p.bf16);
+          *reinterpret_cast<uint32_t*>(dst + tc::sw128_offset(129 + 2 * ps, kpos)) = pack2(v.y, v.w, p.bf16);
+        }
+      }
+      tc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(&B.full[t]);
+        tc::mbar_arrive(&B.empty32[s0]);
+        tc::mbar_arrive(&B.empty32[s1]);
+      }
     }
-    const bool more = tile2 < p.ntiles;
-    if (more) conv_load(p, tile2, c2, cw, lane, nxt);
-    const uint32_t st = u % kStages, q = u / kStages;
-    if (q > 0 && !tc::mbar_wait(&B.empty[st], (q - 1) & 1u, abort)) {
-      *abort = 1;
-      return;
-    }
-    conv_store(p, stages + st * kStageBytes, cw, lane, cur);
-    tc::fence_proxy_async();
-    __syncwarp();
-    if (lane == 0) tc::mbar_arrive(&B.full[st]);
-    ++u;
-    if (!more) return;
-    cur = nxt;
-    c = c2;
-    tile = tile2;
-    j = j2;
   }
 }
 
 // MMA role (one thread).
-__device__ inline void mma_role(const Pipe& p, uint8_t* stages, Bars& B, volatile int* abort, uint32_t tmem,
+__device__ inline void mma_role(const Pipe& p, uint8_t* pipe_base, Bars& B, volatile int* abort, uint32_t tmem,
                                 int64_t tile0, int64_t tstep) {
   const uint32_t idesc = tc::idesc_f16(128, kMmaN, p.bf16 != 0);
   uint32_t u = 0;
@@ -224,7 +201,7 @@ __device__ inline void mma_role(const Pipe& p, uint8_t* stages, Bars& B, volatil
         break;
       }
       tc::tc_fence_after();
-      const uint32_t sa = tc::smem_u32(stages + st * kStageBytes);
+      const uint32_t sa = tc::smem_u32(stage16(pipe_base, (int)st));
       const uint64_t d0 = tc::sdesc_k_sw128(sa);
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
@@ -239,6 +216,23 @@ __device__ inline void mma_role(const Pipe& p, uint8_t* stages, Bars& B, volatil
   // make sure nothing is in flight before the TMEM is released
   tc::mma_commit(&B.done);
   tc::mbar_wait(&B.done, 0, abort, 2000000000LL);
+}
+
+// Initialise the pipeline's barriers (one thread).
+__device__ inline void init_bars(Bars& B, int nconv) {
+  for (int s = 0; s < kStages32; ++s) {
+    tc::mbar_init(&B.full32[s], 1);
+    tc::mbar_init(&B.empty32[s], nconv);
+  }
+  for (int s = 0; s < kStages; ++s) {
+    tc::mbar_init(&B.full[s], nconv);
+    tc::mbar_init(&B.empty[s], 1);
+  }
+  for (int b = 0; b < 2; ++b) {
+    tc::mbar_init(&B.acc_full[b], 1);
+    tc::mbar_init(&B.acc_empty[b], 1);
+  }
+  tc::mbar_init(&B.done, 1);
 }
 
 // Drain helper: for the calling thread (TMEM lane `row` of the tile) combine

@@ -79,7 +79,7 @@ def lib():
         L.fpcg_solve_gram.restype = ctypes.c_int
         L.fpcg_gram.argtypes = [_P, _P, _P, _I32, _I32, _I64, _I32, _P, _P, _P, _P]
         L.fpcg_gram.restype = ctypes.c_int
-        L.fpcg_path.argtypes = [_I32, _I32, ctypes.POINTER(Precision)]
+        L.fpcg_path.argtypes = [_I32, _I32, _I32, ctypes.POINTER(Precision)]
         L.fpcg_path.restype = ctypes.c_int
         L.fpcg_strerror.argtypes = [ctypes.c_int]
         L.fpcg_strerror.restype = ctypes.c_char_p
@@ -94,9 +94,9 @@ def lib():
 PATH_SIMT, PATH_TENSOR_CORE = 0, 1
 
 
-def fpcg_path(K, block_L, prec):
+def fpcg_path(N, K, block_L, prec):
     """Which kernel a detection call with these settings uses (no GPU needed)."""
-    rc = lib().fpcg_path(int(K), int(block_L or 0), ctypes.byref(prec))
+    rc = lib().fpcg_path(int(N), int(K), int(block_L or 0), ctypes.byref(prec))
     if rc < 0:
         raise FpcgError(-rc, "fpcg_path")
     return rc

@@ -56,13 +56,14 @@ CASES = [
 def test_routing_to_simt():
     """Configurations the fused kernel does not take run on the SIMT kernel."""
     bf = dict(gram="bf16", mv="bf16")
-    assert F.fpcg_path(64, 1, F.precision(**bf)) == F.PATH_SIMT          # L not in {0,4,8,16}
-    assert F.fpcg_path(64, 2, F.precision(**bf)) == F.PATH_SIMT
-    assert F.fpcg_path(128, 8, F.precision(**bf)) == F.PATH_SIMT         # K > 64
-    assert F.fpcg_path(8, 4, F.precision(**bf)) == F.PATH_SIMT           # K < 16
-    assert F.fpcg_path(64, 8, F.precision(**bf, resid="fp64")) == F.PATH_SIMT  # compensated residual
-    assert F.fpcg_path(64, 8, F.precision(gram="bf16", mv="e4m3")) == F.PATH_SIMT
-    assert F.fpcg_path(64, 8, F.precision(**bf)) == F.PATH_TENSOR_CORE
+    assert F.fpcg_path(256, 64, 1, F.precision(**bf)) == F.PATH_SIMT          # L not in {0,4,8,16}
+    assert F.fpcg_path(256, 64, 2, F.precision(**bf)) == F.PATH_SIMT
+    assert F.fpcg_path(256, 128, 8, F.precision(**bf)) == F.PATH_SIMT         # K > 64
+    assert F.fpcg_path(64, 8, 4, F.precision(**bf)) == F.PATH_SIMT           # K < 16
+    assert F.fpcg_path(256, 64, 8, F.precision(**bf, resid="fp64")) == F.PATH_SIMT  # compensated residual
+    assert F.fpcg_path(256, 64, 8, F.precision(gram="bf16", mv="e4m3")) == F.PATH_SIMT
+    assert F.fpcg_path(255, 64, 8, F.precision(**bf)) == F.PATH_SIMT          # odd N (no TMA)
+    assert F.fpcg_path(256, 64, 8, F.precision(**bf)) == F.PATH_TENSOR_CORE
 
 
 @pytest.mark.parametrize("K,gram,mv,L,iters,refine", CASES)
@@ -72,7 +73,7 @@ def test_fused_matches_oracle(K, gram, mv, L, iters, refine):
     batch = 152 * P * 2 + P // 2 + 1       # every CTA reuses both accumulators; ragged last tile
     d = wl.generate(wl.Spec(N=N, K=K, batch=batch, rho=0.5, qam=64, snr_db=14.0, seed=500 + K + L))
     pk = dict(gram=gram, mv=mv, refine_steps=refine)
-    assert F.fpcg_path(K, L, F.precision(**pk)) == F.PATH_TENSOR_CORE
+    assert F.fpcg_path(N, K, L, F.precision(**pk)) == F.PATH_TENSOR_CORE
     res = gpu_detect(d, iters, pk, L=(L or None))
     ref = oracle_detect(d, iters, pk, L=(L or None))
     _check(d, res, ref)
@@ -87,7 +88,7 @@ def test_fused_headline_config_full_size_sampled():
     spec = wl.c3_kron_256x64()
     d = wl.generate(spec)
     pk = dict(HEAD["prec"])
-    assert F.fpcg_path(64, HEAD["L"], F.precision(**pk)) == F.PATH_TENSOR_CORE
+    assert F.fpcg_path(256, 64, HEAD["L"], F.precision(**pk)) == F.PATH_TENSOR_CORE
     res = gpu_detect(d, HEAD["iters"], pk, L=HEAD["L"])
     rng = np.random.default_rng(0)
     sel = np.sort(rng.choice(spec.batch, 96, replace=False))
@@ -120,10 +121,10 @@ def test_fused_matches_simt_path(monkeypatch):
     path (forced with FPCG_FORCE_SIMT) on identical inputs."""
     d = wl.generate(wl.Spec(N=256, K=64, batch=600, rho=0.7, qam=64, snr_db=18.0, seed=99))
     pk = dict(gram="bf16", mv="bf16", refine_steps=1)
-    assert F.fpcg_path(64, 8, F.precision(**pk)) == F.PATH_TENSOR_CORE
+    assert F.fpcg_path(256, 64, 8, F.precision(**pk)) == F.PATH_TENSOR_CORE
     tc = gpu_detect(d, 6, pk, L=8)
     monkeypatch.setenv("FPCG_FORCE_SIMT", "1")
-    assert F.fpcg_path(64, 8, F.precision(**pk)) == F.PATH_SIMT
+    assert F.fpcg_path(256, 64, 8, F.precision(**pk)) == F.PATH_SIMT
     simt = gpu_detect(d, 6, pk, L=8)
     monkeypatch.delenv("FPCG_FORCE_SIMT")
     # each path is within 2e-3 of the oracle; they differ by at most the sum
