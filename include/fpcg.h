@@ -95,11 +95,12 @@ enum {
  *   alpha_num     FP-BJ-CG only: 0 = alpha's numerator r^H p as Algorithm 3
  *                 writes it, 1 = r^H z (textbook PCG); equal in exact arithmetic.
  *   fp8_block     e4m3 scale block in real components; must be 32.
- *   resid         precision of the residual b - A x of the refinement and of
- *                 rel_res: FP64 (fp64 units), or FP32 = fp32 products and a
- *                 compensated (double-fp32) sum, which is as accurate as fp64
- *                 for these inputs and far cheaper on GB300.  The fp64 mode
- *                 always uses FP64.
+ *   resid         the residual b - A x of the refinement and of rel_res:
+ *                 FPCG_FP32 = A is the matvec matrix (A rounded to u_MV) and
+ *                 the sums are fp32 (both kernels); FPCG_FP64 = A is the fp32
+ *                 Gram matrix and the sums are fp64-accurate (compensated
+ *                 double-fp32 products and sums, far cheaper than fp64 units
+ *                 on GB300; SIMT kernel).  The fp64 mode always uses fp64.
  */
 typedef struct fpcg_precision {
   int32_t gram;

@@ -284,7 +284,7 @@ def fp_cg(A_mv, b, iters, mv, ip="fp32", w="fp32", Md=None, alpha_num=0,
 # ---------------------------------------------------------------------------
 
 DEFAULT_PREC = {"gram": "fp32", "mv": "fp32", "ip": "fp32", "w": "fp32",
-                "refine_steps": 0, "refine_iters": None, "alpha_num": 0}
+                "refine_steps": 0, "refine_iters": None, "alpha_num": 0, "resid": "fp32"}
 
 
 def resid(A, x, b):
@@ -296,8 +296,13 @@ def detect(H, y, sigma2, qam_order, iters, prec=None, L=None, block=32):
     """Emulate one detection call; returns a dict of results.
 
     prec keys: gram, mv, ip, w in {"fp64","fp32","fp16","bf16"} (mv also
-    "e4m3"), refine_steps, refine_iters (default: iters), alpha_num.
+    "e4m3"), refine_steps, refine_iters (default: iters), alpha_num, resid.
     L: block-Jacobi block size (None = FP-CG, Algorithm 2).
+
+    resid selects the matrix of the refinement residual and of rel_res:
+    "fp32" -- the matrix the matvec uses (A rounded to u_MV), "fp64" -- the
+    Gram matrix A itself.  Either residual is formed exactly here (the GPU
+    sums it at fp32, or with fp64-class compensated sums for "fp64").
     """
     pr = dict(DEFAULT_PREC)
     pr.update(prec or {})
@@ -310,16 +315,17 @@ def detect(H, y, sigma2, qam_order, iters, prec=None, L=None, block=32):
         Md, fail = bj_inverse(A, L, w)
         status[fail] |= ST_BJ_FAIL
     A_mv = round_matvec_operand(A, pr["mv"], block)
+    A_res = A if (pr.get("resid", "fp32") == "fp64" or w == "fp64") else A_mv
     x, st, hist, _ = fp_cg(A_mv, b, iters, pr["mv"], pr["ip"], w, Md, pr["alpha_num"], block)
     status |= st
     ri = pr["refine_iters"] if pr["refine_iters"] is not None else iters
     for _ in range(int(pr["refine_steps"])):
-        rr = flc(resid(A, x, b), w)
+        rr = flc(resid(A_res, x, b), w)
         d, st2, _, _ = fp_cg(A_mv, rr, ri, pr["mv"], pr["ip"], w, Md, pr["alpha_num"], block)
         status |= st2 & ST_BREAKDOWN
         x = flc(x + d, w)
     nb = np.linalg.norm(_c128(b), axis=1)
-    nr = np.linalg.norm(resid(A, x, b), axis=1)
+    nr = np.linalg.norm(resid(A_res, x, b), axis=1)
     rel = np.where(nb > 0, nr / np.where(nb > 0, nb, 1.0), 0.0)
     status[~np.all(np.isfinite(x), axis=1)] |= ST_NONFINITE
     qam_order = np.broadcast_to(np.asarray(qam_order), (B,))

@@ -16,8 +16,9 @@
 //   3. FP-CG / FP-BJ-CG (Algorithms 2 and 3): A p with A and p rounded to
 //      u_MV (e4m3: per-block power-of-two scales) and fp32 sums; inner products
 //      summed at fp32 and rounded to u_IP; updates by FMA at u_W.
-//   4. Refinement: r = b - A x with a compensated (double-fp32) sum or fp64,
-//      a correction solve with step 3, x += d.
+//   4. Refinement: r = b - A x (A rounded to u_MV with fp32 sums, or the Gram
+//      matrix with compensated double-fp32 / fp64 sums), a correction solve
+//      with step 3, x += d.
 //   5. rel_res = ||b - A x|| / ||b||, the Gray-QAM decision, bit errors.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -521,19 +522,22 @@ __device__ int cg_phase(const SimtParams& P, const Smem<T>& S, const cplx<T>* rh
 }
 
 // ---------------------------------------------------------------------------
-// Step 4/5: residual out = b - A x.  Compensated fp32 or fp64 sums; returns
-// ||out||^2 and ||b||^2 (fp64) to every thread.
+// Step 4/5: residual out = b - A x; returns ||out||^2 and ||b||^2 (fp64) to
+// every thread.  resid = FP32: A is the matvec matrix (A rounded to u_MV) and
+// the sums are fp32.  resid = FP64 (and the fp64 mode): A is the Gram matrix
+// itself and the sums are fp64-accurate -- compensated double-fp32 in the fp32
+// modes (FMA TwoProd + TwoSum), plain fp64 in the fp64 mode.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int MV>
 __device__ void residual(const SimtParams& P, const Smem<T>& S, cplx<T>* out, double& nr2, double& nb2) {
-  const int K = P.K, AS = K + 1, tid = threadIdx.x;
+  const int K = P.K, AS = K + 1, tid = threadIdx.x, NB = (2 * K + 31) / 32;
   int tpr = 32;
   while (tpr > 1 && tpr * K > NT) tpr >>= 1;
   const int row = tid / tpr, part = tid % tpr;
   const bool row_ok = row < K;  // every lane of a warp takes part in the shuffles
   {
     const cplx<T>* Arow = S.A + (size_t)(row_ok ? row : 0) * AS;
-    if (sizeof(T) == 8 || P.resid_fp64) {
+    if (sizeof(T) == 8) {
       double sr = 0.0, si = 0.0;
       for (int l = part; row_ok && l < K; l += tpr) {
         const cplx<T> a = Arow[l], x = S.x[l];
@@ -547,6 +551,30 @@ __device__ void residual(const SimtParams& P, const Smem<T>& S, cplx<T>* out, do
       if (row_ok && part == 0) {
         const cplx<T> bb = S.b[row];
         out[row] = cplx<T>{(T)((double)bb.re - sr), (T)((double)bb.im - si)};
+      }
+    } else if (!P.resid_fp64) {
+      float sr = 0.f, si = 0.f;
+      for (int l = part; row_ok && l < K; l += tpr) {
+        cplx<T> a = Arow[l];
+        if (MV == BF16 || MV == F16) {
+          a.re = (T)round_to((float)a.re, MV);
+          a.im = (T)round_to((float)a.im, MV);
+        } else if (MV == E4M3) {
+          const float s = S.sA[row * NB + l / 16];
+          a.re = (T)(round_to((float)a.re / s, E4M3) * s);
+          a.im = (T)(round_to((float)a.im / s, E4M3) * s);
+        }
+        const cplx<T> x = S.x[l];
+        sr = fmaf((float)a.re, (float)x.re, fmaf(-(float)a.im, (float)x.im, sr));
+        si = fmaf((float)a.re, (float)x.im, fmaf((float)a.im, (float)x.re, si));
+      }
+      for (int o = tpr >> 1; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+      }
+      if (row_ok && part == 0) {
+        const cplx<T> bb = S.b[row];
+        out[row] = cplx<T>{(T)((float)bb.re - sr), (T)((float)bb.im - si)};
       }
     } else {
       // (hr, lr) = b_re - sum(a_re x_re - a_im x_im), (hi, li) likewise
@@ -616,7 +644,7 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
     for (int k = threadIdx.x; k < K; k += NT) S.w[k] = S.x[k];
     __syncthreads();
     double nr2, nb2;
-    residual(P, S, S.z, nr2, nb2);  // S.x still holds x_hat
+    residual<T, MV>(P, S, S.z, nr2, nb2);  // S.x still holds x_hat
     // the correction solve overwrites x, r, p, z, w, pq: move rhs and x_hat out
     // of the way into the staging buffer (free after the Gram phase)
     cplx<T>* xs = S.Hs;
@@ -638,7 +666,7 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
   }
 
   double nr2, nb2;
-  residual(P, S, S.z, nr2, nb2);
+  residual<T, MV>(P, S, S.z, nr2, nb2);
   if (threadIdx.x == 0 && P.rel_res) P.rel_res[sys] = nb2 > 0.0 ? sqrt(nr2 / nb2) : 0.0;
 
   // outputs

@@ -186,6 +186,15 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t
   return (row >> 3) * 1024u + r * 128u + (((chunk ^ r) & 7u) << 4) + ((k & 7u) << 1);
 }
 
+// Four 8x8 16-bit matrices from shared memory (lane l gives the address of
+// row l%8 of matrix l/8), in the register order of an m16n8k16 A fragment.
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], uint32_t saddr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(saddr)
+               : "memory");
+}
+
 // ---- warp-level MMA: D(16x8, f32) += A(16x16, bf16/fp16 row) * B(16x8, col) -----
 __device__ __forceinline__ void mma_m16n8k16_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                                   uint32_t b1) {

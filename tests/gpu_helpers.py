@@ -27,7 +27,7 @@ def gpu_detect(d, iters, prec_kw, L=None, hist=False, dev="cuda:0", g=None):
     return res
 
 
-ORACLE_KEYS = ("gram", "mv", "ip", "w", "refine_steps", "refine_iters", "alpha_num")
+ORACLE_KEYS = ("gram", "mv", "ip", "w", "refine_steps", "refine_iters", "alpha_num", "resid")
 
 
 def oracle_detect(d, iters, prec_kw, L=None, sel=None):
