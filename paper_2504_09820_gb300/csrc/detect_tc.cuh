@@ -14,6 +14,7 @@ struct DetectTcParams {
   const double* sigma2;
   const int32_t* qam;
   int iters, L, refine_steps, refine_iters, alpha_num, ip;
+  int nslots;  // systems in flight per CTA (tc_num_slots)
   float2* x_hat;
   uint8_t* sym;
   double* rel_res;
@@ -23,35 +24,51 @@ struct DetectTcParams {
   int32_t* status;
 };
 
-// Shared memory of one CG warpgroup (layout carved in detect_tc_impl.cuh):
-// A [64][K+1], b/W/X/R [64], M_d [64][L+1] (c64), packed p [64] (u32), flags.
-__host__ __device__ inline size_t cg_smem_bytes(int K, int L) {
-  size_t s = 0;
-  s += sizeof(float2) * 64 * (K + 1);
-  s += sizeof(float2) * 64 * 4;
-  s += sizeof(float2) * 64 * ((L > 0 ? L : 1) + 1);
-  s += sizeof(uint32_t) * 64;
-  s += sizeof(int) * 4;
+// One system slot in shared memory (carved in detect_tc_impl.cuh): A + sigma^2 I
+// in the matvec format as [Re A; Im A] (2K x K 16-bit), the fp32 diagonal
+// blocks M_d [K][L+1] (c64), b and the matvec result [K] (c64), the packed
+// B fragments (3K words).
+__host__ __device__ inline size_t tc_slot_bytes(int K, int L) {
+  size_t s = 4 * (size_t)K * K;
+  s += sizeof(float2) * K * ((L > 0 ? L : 1) + 1);
+  s += sizeof(float2) * K * 2;
+  s += sizeof(uint32_t) * 3 * K;
   return (s + 127) & ~size_t(127);
 }
 
-// Offset of the first CG region after the stages, barriers and TMEM slot.
-__host__ __device__ inline size_t cg_region_offset() {
-  return (tcp::kPipeBytes + sizeof(tcp::Bars) + 16 + 127) & ~size_t(127);
+constexpr int kTcCgWarps = 6;       // CG warps, one slot each (at most)
+constexpr int kTcStages32 = 4;      // FP32 TMA ring depth of the fused kernel
+constexpr size_t kTcSmemMax = 227 * 1024;
+
+// Offset of the first slot after the stages, barriers, TMEM address and abort flag.
+__host__ __device__ inline size_t tc_slots_offset() {
+  return (tcp::pipe_bytes(kTcStages32) + sizeof(tcp::Bars) + 2 * kTcCgWarps * sizeof(uint64_t) + 16 + 127) &
+         ~size_t(127);
+}
+
+// Systems in flight per CTA: as many slots as fit beside the pipeline.
+inline int tc_num_slots(int K, int L) {
+  const size_t avail = kTcSmemMax - 1024 - tc_slots_offset();
+  const size_t n = avail / tc_slot_bytes(K, L);
+  return n < (size_t)kTcCgWarps ? (int)n : kTcCgWarps;
 }
 
 inline size_t detect_tc_smem_bytes(int K, int L) {
-  const size_t s = 1024 + cg_region_offset() + 2 * cg_smem_bytes(K, L);
+  const size_t s = 1024 + tc_slots_offset() + tc_num_slots(K, L) * tc_slot_bytes(K, L);
   return s < 120 * 1024 ? 120 * 1024 : s;  // one CTA (one 512-column TMEM allocation) per SM
 }
 
 // K in {16, 32, 64}; L in {0 (FP-CG), 4, 8, 16}.
 inline bool detect_tc_supported(int K, int L) {
-  return (K == 16 || K == 32 || K == 64) && (L == 0 || L == 4 || L == 8 || L == 16);
+  return (K == 16 || K == 32 || K == 64) && (L == 0 || L == 4 || L == 8 || L == 16) && tc_num_slots(K, L) >= 2;
 }
 
 template <int K>
 cudaError_t launch_detect_tc_k(const DetectTcParams& P, int num_sms, int mv_bf16, cudaStream_t stream);
+// Each K is instantiated in its own translation unit (detect_tc_k{16,32,64}.cu).
+extern template cudaError_t launch_detect_tc_k<16>(const DetectTcParams&, int, int, cudaStream_t);
+extern template cudaError_t launch_detect_tc_k<32>(const DetectTcParams&, int, int, cudaStream_t);
+extern template cudaError_t launch_detect_tc_k<64>(const DetectTcParams&, int, int, cudaStream_t);
 
 inline cudaError_t launch_detect_tc(const DetectTcParams& P, int num_sms, int mv_bf16, cudaStream_t stream) {
   switch (P.pipe.K) {

@@ -44,7 +44,7 @@
 namespace fpcg {
 namespace tcp {
 
-constexpr int kStages32 = 4;                   // FP32 staging ring
+constexpr int kStages32 = 4;                   // FP32 staging ring (at most; a kernel may use fewer)
 constexpr int kChunk32 = 32;                   // antennas per FP32 stage
 constexpr int kStage32HBytes = 64 * 64 * 4;    // 64 columns x 64 floats
 constexpr int kStage32Bytes = kStage32HBytes + 8 * 64 * 4;  // + y of up to 8 systems
@@ -54,7 +54,9 @@ constexpr int kStageBytes = kStageRows * 128;  // 18432, a multiple of 1024
 constexpr int kChunk = 64;                     // antennas per operand stage
 constexpr int kMmaN = 144;
 constexpr int kAccCols = 256;                  // TMEM columns per accumulator buffer
-constexpr int kPipeBytes = kStages32 * kStage32Bytes + kStages * kStageBytes;
+// Operand stages first (1024-byte aligned for the 128B swizzle), then the ring.
+__host__ __device__ constexpr int pipe_bytes(int stages32) { return kStages * kStageBytes + stages32 * kStage32Bytes; }
+constexpr int kPipeBytes = pipe_bytes(kStages32);
 
 struct Pipe {
   CUtensorMap tmH;   // FP32 view of H: dims {2N, batch*K}, box {64, 64}
@@ -85,9 +87,11 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int bf16) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-__device__ __forceinline__ uint8_t* stage32(uint8_t* pipe_base, int s) { return pipe_base + s * kStage32Bytes; }
+__device__ __forceinline__ uint8_t* stage32(uint8_t* pipe_base, int s) {
+  return pipe_base + kStages * kStageBytes + s * kStage32Bytes;
+}
 __device__ __forceinline__ uint8_t* stage16(uint8_t* pipe_base, int t) {
-  return pipe_base + kStages32 * kStage32Bytes + t * kStageBytes;
+  return pipe_base + t * kStageBytes;
 }
 
 // Ask the bulk-copy engine to pull a tile's H and y into L2 ahead of the TMA
@@ -107,6 +111,8 @@ __device__ inline void prefetch_tile(const Pipe& p, int64_t tile) {
 }
 
 // Producer role (one thread): tiles this CTA owns are tile0, tile0 + tstep, ...
+// S32 = FP32 stages in the ring (2..kStages32).
+template <int S32 = kStages32>
 __device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B, volatile int* abort,
                                      int64_t tile0, int64_t tstep) {
   const uint32_t tx = kStage32HBytes + 64 * 4 * p.P;
@@ -115,7 +121,7 @@ __device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B,
   for (int64_t tile = tile0; tile < p.ntiles; tile += tstep) {
     prefetch_tile(p, tile + 2 * tstep);
     for (int c = 0; c < 2 * p.nchunks; ++c, ++u) {
-      const uint32_t s = u % kStages32, q = u / kStages32;
+      const uint32_t s = u % S32, q = u / S32;
       if (q > 0 && !tc::mbar_wait(&B.empty32[s], (q - 1) & 1u, abort)) {
         *abort = 1;
         return;
@@ -131,7 +137,7 @@ __device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B,
 // Converter warp `cw` of NC: columns cl = cw + NC m of the tile and y of
 // systems cw + NC m.  Lane l fills k-positions 2l, 2l+1 of the operand stage
 // (antennas 2l, 2l+1 of the 64), read from FP32 stage l/16 at antenna 2(l%16).
-template <int NC>
+template <int NC, int S32 = kStages32>
 __device__ inline void converter_role(const Pipe& p, uint8_t* pipe_base, Bars& B, volatile int* abort,
                                       int64_t tile0, int64_t tstep, int cw, int lane) {
   constexpr int NM = (64 + NC - 1) / NC;
@@ -140,8 +146,8 @@ __device__ inline void converter_role(const Pipe& p, uint8_t* pipe_base, Bars& B
   const uint32_t kpos = 2u * lane;
   for (int64_t tile = tile0; tile < p.ntiles; tile += tstep) {
     for (int c = 0; c < p.nchunks; ++c, u32 += 2, ++u16) {
-      const uint32_t s0 = u32 % kStages32, q0 = u32 / kStages32;
-      const uint32_t s1 = (u32 + 1) % kStages32, q1 = (u32 + 1) / kStages32;
+      const uint32_t s0 = u32 % S32, q0 = u32 / S32;
+      const uint32_t s1 = (u32 + 1) % S32, q1 = (u32 + 1) / S32;
       const uint32_t t = u16 % kStages, qt = u16 / kStages;
       if (!tc::mbar_wait(&B.full32[s0], q0 & 1u, abort) || !tc::mbar_wait(&B.full32[s1], q1 & 1u, abort) ||
           (qt > 0 && !tc::mbar_wait(&B.empty[t], (qt - 1) & 1u, abort))) {
@@ -219,8 +225,8 @@ __device__ inline void mma_role(const Pipe& p, uint8_t* pipe_base, Bars& B, vola
 }
 
 // Initialise the pipeline's barriers (one thread).
-__device__ inline void init_bars(Bars& B, int nconv) {
-  for (int s = 0; s < kStages32; ++s) {
+__device__ inline void init_bars(Bars& B, int nconv, int stages32 = kStages32) {
+  for (int s = 0; s < stages32; ++s) {
     tc::mbar_init(&B.full32[s], 1);
     tc::mbar_init(&B.empty32[s], nconv);
   }
