@@ -440,7 +440,7 @@ struct CgWarp {
     const float sc = m ? sqrtf((float)(2 * (M - 1) / 3)) : 0.f;  // 2(M-1)/3 is an integer here
     const int nb2 = m ? qam_bits_axis(m) : 0;
     if (vact()) {
-#pragma unroll 1
+#pragma unroll  // x, r, txv stay in registers only with static indices
       for (int e = 0; e < E; ++e) {
         const float2 bv = S.b[lane + 32 * e];
         nr += r[e].x * r[e].x + r[e].y * r[e].y;
@@ -561,17 +561,11 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
         }
       }
     }
-    {  // b from the y columns 128 + 2ps, 129 + 2ps
-      uint32_t v[16];
-      tc::tmem_ld16_async(tb + 128u, v);
+    {  // b from the y columns 128 + 2ps, 129 + 2ps (ps is the same on the whole warp)
+      uint32_t v[2];
+      tc::tmem_ld2_async(tb + 128u + 2u * (uint32_t)ps, v);
       tc::tmem_wait_ld();
-      float mine0 = 0.f, mine1 = 0.f;
-#pragma unroll
-      for (int m = 0; m < 16; m += 2)
-        if (m == 2 * (ps & 7)) {
-          mine0 = __uint_as_float(v[m]);
-          mine1 = __uint_as_float(v[m + 1]);
-        }
+      const float mine0 = __uint_as_float(v[0]), mine1 = __uint_as_float(v[1]);
       const float other = __shfl_xor_sync(0xffffffffu, mine1, 1);
       reinterpret_cast<float*>(sl.b + k)[odd] = valid ? (odd ? (other - mine0) : (mine0 + other)) : 0.f;
     }

@@ -286,16 +286,15 @@ __device__ __forceinline__ void drain_tile(const Pipe& p, uint32_t tmem_acc, int
       }
     }
   }
-  {
-    float v[16];
-    tc::tmem_ld16(lane_base + 128u, v);
-    float mine0 = 0.f, mine1 = 0.f;
-#pragma unroll
-    for (int m = 0; m < 16; m += 2)
-      if (m == 2 * (sys & 7)) {
-        mine0 = v[m];
-        mine1 = v[m + 1];
-      }
+  {  // y columns 128 + 2 sys, 129 + 2 sys; a warp covers one or two systems
+    const int s0 = (32 * q) / twoK;
+    const int s1 = s0 + 1 < 8 ? s0 + 1 : s0;
+    uint32_t v0[2], v1[2];
+    tc::tmem_ld2_async(lane_base + 128u + 2u * (uint32_t)s0, v0);
+    tc::tmem_ld2_async(lane_base + 128u + 2u * (uint32_t)s1, v1);
+    tc::tmem_wait_ld();
+    const float mine0 = __uint_as_float(sys == s0 ? v0[0] : v1[0]);
+    const float mine1 = __uint_as_float(sys == s0 ? v0[1] : v1[1]);
     const float other = __shfl_xor_sync(0xffffffffu, mine1, 1);
     if (sys < p.P) emit_b(odd ? (other - mine0) : (mine0 + other));
   }
