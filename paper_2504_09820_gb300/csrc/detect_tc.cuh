@@ -24,13 +24,20 @@ struct DetectTcParams {
   int32_t* status;
 };
 
+// Layout of the diagonal blocks M_d in a slot: block b at b * md_block_stride
+// (float2 units), row i of a block at i * md_row_stride.  Rows are padded to
+// an even length (16-byte aligned rows for vector loads) and blocks by 4 more
+// entries (successive blocks start on different banks).
+__host__ __device__ constexpr int md_row_stride(int L) { return L + 2; }
+__host__ __device__ constexpr int md_block_stride(int L) { return L * (L + 2) + 4; }
+
 // One system slot in shared memory (carved in detect_tc_impl.cuh): A + sigma^2 I
 // in the matvec format as [Re A; Im A] (2K x K 16-bit), the fp32 diagonal
-// blocks M_d [K][L+1] (c64), b and the matvec result [K] (c64), the packed
-// B fragments (3K words).
+// blocks M_d, b and the matvec result [K] (c64) and the packed B fragments
+// (3K words).
 __host__ __device__ inline size_t tc_slot_bytes(int K, int L) {
   size_t s = 4 * (size_t)K * K;
-  s += sizeof(float2) * K * ((L > 0 ? L : 1) + 1);
+  s += sizeof(float2) * (L > 0 ? (size_t)(K / L) * md_block_stride(L) : 2);
   s += sizeof(float2) * K * 2;
   s += sizeof(uint32_t) * 3 * K;
   return (s + 127) & ~size_t(127);
@@ -46,7 +53,7 @@ __host__ __device__ inline size_t tc_slots_offset() {
          ~size_t(127);
 }
 
-// Systems in flight per CTA: as many slots as fit beside the pipeline.
+// Systems in flight per CTA: as many slots as fit beside the pipeline, one per CG warp.
 inline int tc_num_slots(int K, int L) {
   const size_t avail = kTcSmemMax - 1024 - tc_slots_offset();
   const size_t n = avail / tc_slot_bytes(K, L);

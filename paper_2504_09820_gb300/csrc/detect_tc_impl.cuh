@@ -48,7 +48,7 @@ constexpr int kConv = kProdWarp - kConv0;
 // ---- one system slot in shared memory -----------------------------------------
 struct Slot {
   uint8_t* A16;     // [2K][K] 16-bit, row r at r*2K bytes, 16-byte chunk c at (c ^ swz(r))
-  float2* Md;       // [K][L+1] diagonal blocks of A (fp32), inverted in place
+  float2* Md;       // diagonal blocks of A (fp32), inverted in place (md_*_stride layout)
   float2* b;        // [K]
   float2* W;        // [K] matvec result, redistributed
   uint32_t* Pk;     // [3K] packed B fragments
@@ -60,7 +60,7 @@ __device__ inline Slot slot_carve(uint8_t* base, int K, int L) {
   s.A16 = p;
   p += 4 * K * K;
   s.Md = (float2*)p;
-  p += sizeof(float2) * K * ((L > 0 ? L : 1) + 1);
+  p += sizeof(float2) * (L > 0 ? (K / L) * md_block_stride(L) : 2);
   s.b = (float2*)p;
   p += sizeof(float2) * K;
   s.W = (float2*)p;
@@ -100,15 +100,16 @@ __device__ __forceinline__ void mma16(float (&d)[4], const uint32_t (&a)[4], uin
 }
 
 // In-place Gauss-Jordan inversion, no pivoting, of the K/L diagonal blocks
-// (Hermitian positive definite, L x L, row stride L+1) of M_d by one warp:
-// lane l owns columns c = l + 32e (e < NE, c < K) of their blocks.  Per pivot
-// pv, with d = 1 / M[pv][pv] and f = column pv of the block:
+// (Hermitian positive definite, L x L) of M_d by one warp: lane l owns columns
+// c = l + 32e (e < NE, c < K) of their blocks.  Per pivot pv, with
+// d = 1 / M[pv][pv] and f = column pv of the block:
 //   M[pv][j] <- M[pv][j] d,  M[i][j] <- M[i][j] - f_i M[pv][j] d   (j != pv)
 //   M[pv][pv] <- d,          M[i][pv] <- -f_i d                    (j == pv)
-// Returns nonzero (on every lane) if a pivot was not positive.
+// (one branch-free update for both cases).  Returns nonzero (on every lane) if
+// a pivot was not positive.
 template <int K, int LT, int NE>
 __device__ __forceinline__ int gj_blocks(float2* Md, int lane) {
-  constexpr int LD = LT + 1;
+  constexpr int LD = md_row_stride(LT), BS = md_block_stride(LT);
   float2* M[NE];
   int j[NE];
   bool on[NE];
@@ -116,7 +117,7 @@ __device__ __forceinline__ int gj_blocks(float2* Md, int lane) {
   for (int e = 0; e < NE; ++e) {
     const int c = lane + 32 * e;
     on[e] = c < K;
-    M[e] = Md + (on[e] ? (c / LT) * LT * LD : 0);
+    M[e] = Md + (on[e] ? (c / LT) * BS : 0);
     j[e] = c % LT;
   }
   int fail = 0;
@@ -137,25 +138,16 @@ __device__ __forceinline__ int gj_blocks(float2* Md, int lane) {
 #pragma unroll
     for (int e = 0; e < NE; ++e) {
       if (!on[e]) continue;
-      if (j[e] != pv) {
-        const float2 prow = cmul(mj[e], dinv[e]);
+      const bool own = j[e] == pv;
+      const float2 prow = cmul(mj[e], dinv[e]);
+      const float2 s = own ? dinv[e] : prow;
 #pragma unroll
-        for (int i = 0; i < LT; ++i) {  // row pv is rewritten below
-          float2 v = M[e][i * LD + j[e]];
-          const float2 fp = cmul(f[e][i], prow);
-          v.x -= fp.x;
-          v.y -= fp.y;
-          M[e][i * LD + j[e]] = v;
-        }
-        M[e][pv * LD + j[e]] = prow;
-      } else {
-#pragma unroll
-        for (int i = 0; i < LT; ++i) {
-          const float2 v = cmul(f[e][i], dinv[e]);
-          M[e][i * LD + pv] = make_float2(-v.x, -v.y);
-        }
-        M[e][pv * LD + pv] = dinv[e];
+      for (int i = 0; i < LT; ++i) {  // row pv is rewritten below
+        const float2 a = cmul(f[e][i], s);
+        const float2 v = M[e][i * LD + j[e]];
+        M[e][i * LD + j[e]] = own ? make_float2(-a.x, -a.y) : make_float2(v.x - a.x, v.y - a.y);
       }
+      M[e][pv * LD + j[e]] = s;
     }
     __syncwarp();
   }
@@ -177,7 +169,6 @@ struct CgWarp {
   static constexpr int KT = K / 16;          // k-tiles (16 users)
   static constexpr int MT = K / 16;          // m-tiles of Re A (and of Im A)
   static constexpr int E = K == 64 ? 2 : 1;  // vector rows per lane
-  static constexpr int LD = LT + 1;          // padded row of M_d
   static constexpr int NCOL = 6;             // B columns (re, im) x (hi, mid, lo)
   const DetectTcParams& P;
   Slot S;
@@ -263,7 +254,7 @@ struct CgWarp {
     }
     const uint32_t abase = tc::smem_u32(S.A16);
     const int lr = lane & 15, lc = lane >> 4;
-#pragma unroll 1
+#pragma unroll 1  // unrolled runs slower in the full kernel (code size)
     for (int mt = 0; mt < MT; ++mt) {
       float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
       float cr2[4] = {0.f, 0.f, 0.f, 0.f}, ci2[4] = {0.f, 0.f, 0.f, 0.f};
@@ -315,26 +306,35 @@ struct CgWarp {
     __syncwarp();
   }
 
-  // z = M_d r (z = r without a preconditioner): block rows are consecutive lanes.
+  // z = M_d r (z = r without a preconditioner): r is staged in W and each
+  // lane reads its block's L entries of it (broadcast) and its row of M_d.
   __device__ __forceinline__ void precond(const float2 (&r)[E], float2 (&z)[E]) {
+    if constexpr (LT == 0) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      if constexpr (LT == 0) {
-        z[e] = r[e];
-      } else {
-        const int first = lane & ~(LT - 1);
-        const float2* mrow = S.Md + (vact() ? lane + 32 * e : 0) * LD;
-        float2 acc = make_float2(0.f, 0.f);
+      for (int e = 0; e < E; ++e) z[e] = r[e];
+    } else {
+      constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
 #pragma unroll
-        for (int j = 0; j < LT; ++j) {
-          const float qx = __shfl_sync(0xffffffffu, r[e].x, first + j);
-          const float qy = __shfl_sync(0xffffffffu, r[e].y, first + j);
-          const float2 m = vact() ? mrow[j] : make_float2(0.f, 0.f);
-          acc.x = fmaf(m.x, qx, fmaf(-m.y, qy, acc.x));
-          acc.y = fmaf(m.x, qy, fmaf(m.y, qx, acc.y));
+      for (int e = 0; e < E; ++e)
+        if (vact()) S.W[lane + 32 * e] = r[e];
+      __syncwarp();
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = vact() ? lane + 32 * e : 0;
+        const float4* rb = reinterpret_cast<const float4*>(S.W + (k & ~(LT - 1)));
+        const float4* mr = reinterpret_cast<const float4*>(S.Md + (k / LT) * MBS + (k % LT) * MLD);
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < LT / 2; ++q) {  // entries 2q, 2q+1
+          const float4 m = mr[q], v = rb[q];
+          a0.x = fmaf(m.x, v.x, fmaf(-m.y, v.y, a0.x));
+          a0.y = fmaf(m.x, v.y, fmaf(m.y, v.x, a0.y));
+          a1.x = fmaf(m.z, v.z, fmaf(-m.w, v.w, a1.x));
+          a1.y = fmaf(m.z, v.w, fmaf(m.w, v.z, a1.y));
         }
-        z[e] = acc;
+        z[e] = vact() ? make_float2(a0.x + a1.x, a0.y + a1.y) : make_float2(0.f, 0.f);
       }
+      __syncwarp();
     }
   }
 
@@ -345,10 +345,12 @@ struct CgWarp {
   __device__ void detect(int64_t sys, bool valid) {
     int st = 0;
     if constexpr (LT > 0) {  // block-Jacobi setup (eq. pre_BJ); a failed block gives M_d = I
+      constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
       if (gj_blocks<K, LT, E>(S.Md, lane)) {
         st |= 8;
         for (int i = lane; i < K * LT; i += 32)
-          S.Md[(i / LT) * LD + i % LT] = make_float2((i / LT) % LT == i % LT ? 1.f : 0.f, 0.f);
+          S.Md[(i / LT / LT) * MBS + ((i / LT) % LT) * MLD + i % LT] =
+              make_float2((i / LT) % LT == i % LT ? 1.f : 0.f, 0.f);
         __syncwarp();
       }
     }
@@ -476,8 +478,8 @@ struct CgWarp {
 };
 
 struct Bars2 {
-  uint64_t slot_full[kTcCgWarps];
-  uint64_t slot_empty[kTcCgWarps];
+  uint64_t slot_full[kTcCgWarps];    // drain -> CG warp
+  uint64_t slot_empty[kTcCgWarps];   // CG warp -> drain
 };
 
 struct Smem {
@@ -499,7 +501,7 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
   const int row = 32 * q + lane;
   constexpr int twoK = 2 * K;
   constexpr int PP = 64 / K;
-  constexpr int LD = LT + 1;
+  constexpr int MLD = md_row_stride(LT > 0 ? LT : 1), MBS = md_block_stride(LT > 0 ? LT : 1);
   const int ns = P.nslots;
   const int ps = row / twoK, k = (row % twoK) >> 1, odd = row & 1;
   const int blk0 = ps * twoK;
@@ -525,7 +527,7 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
     const uint32_t tb = lane_base + b * (uint32_t)tcp::kAccCols;
     Slot sl = slot_carve(S.slots + ((j * PP + ps) % ns) * slot_bytes, K, LT);
     const int arow = odd ? K + k : k;           // row of [Re A; Im A]
-    const int kb0 = LT > 0 ? (k / LT) * LT : 0;  // first column of k's diagonal block
+    const int kb0 = (k / (LT > 0 ? LT : 1)) * LT;  // first column of k's diagonal block
 #pragma unroll 1
     for (int cg = blk0; cg < blk0 + twoK; cg += 32) {
       uint32_t v[2][16];
@@ -552,11 +554,12 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
         pkd.z = pk2<BF>(a[4], a[5]);
         pkd.w = pk2<BF>(a[6], a[7]);
         *reinterpret_cast<uint4*>(sl.A16 + a16_offset<K>(arow, l0 >> 3)) = pkd;
-        if (LT > 0) {
+        if constexpr (LT > 0) {
 #pragma unroll
           for (int m = 0; m < 8; ++m) {
             const int l = l0 + m;
-            if (l >= kb0 && l < kb0 + LT) reinterpret_cast<float*>(sl.Md + k * LD + (l - kb0))[odd] = a[m];
+            if (l >= kb0 && l < kb0 + LT)
+              reinterpret_cast<float*>(sl.Md + (k / LT) * MBS + (k % LT) * MLD + (l - kb0))[odd] = a[m];
           }
         }
       }
