@@ -215,6 +215,86 @@ FPCG_API int fpcg_gram(const void* H, const void* y, const double* sigma2, int32
 #define FPCG_PATH_TENSOR_CORE 1
 FPCG_API int fpcg_path(int32_t n_rx, int32_t k, int32_t block_L, const fpcg_precision* prec);
 
+/*
+ * ---- Uneven batches: a plan over systems of different (N, K) ----
+ *
+ * A plan groups the systems of one batch by (N, K) class.  Each class runs as
+ * one persistent launch of the kernel that fpcg_path names, or of the other
+ * kernel when fpcg_plan_autotune measured it faster on that class.  Both
+ * kernels compute the same algorithm (Algorithm 2, or 3 when block_L > 0) at
+ * the same precisions, so the choice changes results only within rounding.
+ * The class launches can be captured once into a CUDA graph and replayed.
+ *
+ * Layout ("plan order"): the systems are stored grouped by class, in the
+ * caller's order within each class.  fpcg_plan_layout gives, for position i of
+ * plan order:
+ *   order[i]  the caller's index of the system;
+ *   h_off[i]  offset in complex elements of its H (K columns of N, column-major)
+ *             in the packed H buffer;
+ *   y_off[i]  offset of its y (N) in the packed y buffer;
+ *   x_off[i]  offset of its x_hat (K) in the packed x_hat buffer, and of its K
+ *             labels in the sym_idx and tx_idx byte buffers;
+ *   totals    {elements of H, of y, of x_hat} to allocate.
+ * Every class starts on a 256-byte boundary of each buffer.  Per-system arrays
+ * (sigma2, qam_order, rel_res, status) are indexed by plan order.
+ *
+ * Ownership: the plan owns its host tables, the instantiated CUDA graph and a
+ * capture stream; fpcg_plan_destroy frees them.  All data buffers are the
+ * caller's device memory.  A plan is not thread-safe; runs of one plan are
+ * ordered on the stream they are issued to.
+ */
+typedef struct fpcg_plan fpcg_plan;
+
+typedef struct fpcg_batch_desc {
+  int64_t batch;            /* number of systems, >= 0 */
+  const int32_t* n_rx;      /* host [batch]: N of each system, K <= N <= 65536 */
+  const int32_t* k;         /* host [batch]: K of each system, 1 <= K <= 128 */
+  int32_t iters;            /* CG iterations per system, >= 0 */
+  int32_t block_L;          /* 0: FP-CG (Algorithm 2); > 0: FP-BJ-CG (Algorithm 3) with block size
+                               min(block_L, K), which must divide K */
+  fpcg_precision prec;      /* as for fpcg_detect */
+  int32_t flags;            /* FPCG_PLAN_GRAPH: capture the class launches into a CUDA graph on the
+                               first run and replay it while the run's pointers stay the same */
+} fpcg_batch_desc;
+
+#define FPCG_PLAN_GRAPH 1
+
+typedef struct fpcg_class_info {
+  int32_t n_rx, k, block_L; /* the class's N, K and block size (0: FP-CG) */
+  int32_t path;             /* FPCG_PATH_SIMT or FPCG_PATH_TENSOR_CORE */
+  int64_t first, count;     /* its systems: plan positions [first, first + count) */
+} fpcg_class_info;
+
+/* Builds a plan (host only, no GPU work).  FPCG_EINVAL for a bad descriptor,
+ * FPCG_ENOMEM if host memory runs out. */
+FPCG_API int fpcg_plan_create(const fpcg_batch_desc* desc, fpcg_plan** plan);
+
+/* Plan-order layout (see above); any output pointer may be NULL.  Host only. */
+FPCG_API int fpcg_plan_layout(const fpcg_plan* plan, int64_t* order, int64_t* h_off, int64_t* y_off,
+                              int64_t* x_off, int64_t totals[3]);
+
+/* Number of classes, and their description when info (n_classes entries) is non-NULL. */
+FPCG_API int fpcg_plan_classes(const fpcg_plan* plan, int32_t* n_classes, fpcg_class_info* info);
+
+/* Times, for every class that both kernels can run, each kernel on the given
+ * inputs (plan order; outputs are overwritten) and keeps the faster.  Issues
+ * work on `stream` and synchronises it.  Drops a captured graph. */
+FPCG_API int fpcg_plan_autotune(fpcg_plan* plan, const void* H, const void* y, const double* sigma2,
+                                const int32_t* qam_order, void* x_hat, uint8_t* sym_idx,
+                                double* rel_res, int32_t* status, void* stream);
+
+/* Detects the whole batch (plan order), asynchronously on `stream`.  Arguments
+ * as for fpcg_detect, with the packed buffers of fpcg_plan_layout; bit_errors
+ * (with tx_idx) is the total over all classes. */
+FPCG_API int fpcg_plan_run(fpcg_plan* plan, const void* H, const void* y, const double* sigma2,
+                           const int32_t* qam_order, void* x_hat, uint8_t* sym_idx, double* rel_res,
+                           const uint8_t* tx_idx, unsigned long long* bit_errors, int32_t* status,
+                           void* stream);
+
+/* Frees the plan (NULL is accepted).  Call it once the plan's work has
+ * finished (for instance after synchronising the stream of its last run). */
+FPCG_API int fpcg_plan_destroy(fpcg_plan* plan);
+
 /* Human-readable text for a return code (static storage). */
 FPCG_API const char* fpcg_strerror(int code);
 

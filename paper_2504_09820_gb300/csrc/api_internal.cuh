@@ -1,0 +1,32 @@
+// Internal entry points shared by the C ABI files of libfpcg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fpcg.h"
+
+namespace fpcg {
+
+// One uniform batch (every system with the same N, K): validation and
+// dispatch to a kernel.  path: -1 = as fpcg_path chooses, FPCG_PATH_SIMT or
+// FPCG_PATH_TENSOR_CORE (FPCG_ENOTSUP if the tensor-core kernel cannot run
+// it).  reset_bits: zero *bit_errors first (a plan zeroes it once for all of
+// its classes).
+int run_uniform(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+                const void* Ain, const void* bin, int32_t n_rx, int32_t k, int64_t batch, int32_t iters,
+                int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
+                double* rel_res, float* res_hist, const uint8_t* tx_idx,
+                unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits);
+
+// Whether the fused tensor-core kernel supports this configuration (alignment
+// of the data aside).
+bool tc_capable(int k, int block_L, const fpcg_precision* prec);
+
+// FPCG_OK, FPCG_EINVAL or FPCG_ENOTSUP for a precision descriptor.
+int check_precision(const fpcg_precision* p);
+
+// Records a CUDA error for fpcg_last_cuda_error and returns FPCG_ECUDA.
+int cuda_error(cudaError_t e);
+
+}  // namespace fpcg

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include "../../include/fpcg.h"
+#include "api_internal.cuh"
 #include "detect_simt.cuh"
 #include "gram_tc.cuh"
 #include "detect_tc.cuh"
@@ -54,10 +55,6 @@ bool force_simt() {
   return v && v[0] && v[0] != '0';
 }
 
-bool uses_tc(int k, int block_L, const fpcg_precision* prec) {
-  return !force_simt() && prec->w == FPCG_FP32 && prec->resid == FPCG_FP32 && (prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) &&
-         (prec->mv == FPCG_BF16 || prec->mv == FPCG_FP16) && fpcg::detect_tc_supported(k, block_L);
-}
 
 int device_sms(int* sms) {
   int dev = 0;
@@ -68,11 +65,15 @@ int device_sms(int* sms) {
   return FPCG_OK;
 }
 
-int run(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
-        const void* Ain, const void* bin, int32_t n_rx, int32_t k, int64_t batch, int32_t iters,
-        int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
-        double* rel_res, float* res_hist, const uint8_t* tx_idx,
-        unsigned long long* bit_errors, int32_t* status, void* stream) {
+}  // namespace
+
+namespace fpcg {
+
+int run_uniform(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+                const void* Ain, const void* bin, int32_t n_rx, int32_t k, int64_t batch, int32_t iters,
+                int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
+                double* rel_res, float* res_hist, const uint8_t* tx_idx,
+                unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits) {
   int rc = check_prec(prec);
   if (rc) return rc;
   if (k < 1 || k > 128 || batch < 0 || iters < 0) return FPCG_EINVAL;
@@ -86,12 +87,14 @@ int run(const void* H, const void* y, const double* sigma2, const int32_t* qam_o
   if (fp64 && k > 64) return FPCG_ENOTSUP;
   const int refine_iters = prec->refine_iters < 0 ? iters : prec->refine_iters;
   cudaStream_t s = (cudaStream_t)stream;
-  if (bit_errors) {
+  if (bit_errors && reset_bits) {
     cudaError_t e = cudaMemsetAsync(bit_errors, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   if (batch == 0) return FPCG_OK;
-  const bool tc_ok = !Ain && uses_tc(k, block_L, prec) && fpcg::tma_pipe_ok(H, y, n_rx);
+  const bool tc_possible = !Ain && tc_capable(k, block_L, prec) && fpcg::tma_pipe_ok(H, y, n_rx);
+  if (path == FPCG_PATH_TENSOR_CORE && !tc_possible) return FPCG_ENOTSUP;
+  const bool tc_ok = tc_possible && (path == FPCG_PATH_TENSOR_CORE || (path < 0 && !force_simt()));
   if (tc_ok) {
     int sms = 0;
     rc = device_sms(&sms);
@@ -151,6 +154,30 @@ int run(const void* H, const void* y, const double* sigma2, const int32_t* qam_o
   cudaError_t e = fpcg::launch_detect_simt(P, fp64, fp64 ? FPCG_FP64 : prec->mv, s);
   if (e != cudaSuccess) return cuda_fail(e);
   return FPCG_OK;
+}
+
+int cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+int check_precision(const fpcg_precision* p) { return check_prec(p); }
+
+bool tc_capable(int k, int block_L, const fpcg_precision* prec) {
+  return prec->w == FPCG_FP32 && prec->resid == FPCG_FP32 && (prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) &&
+         (prec->mv == FPCG_BF16 || prec->mv == FPCG_FP16) && fpcg::detect_tc_supported(k, block_L);
+}
+
+}  // namespace fpcg
+
+namespace {
+using fpcg::run_uniform;
+using fpcg::tc_capable;
+
+int run(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+        const void* Ain, const void* bin, int32_t n_rx, int32_t k, int64_t batch, int32_t iters,
+        int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
+        double* rel_res, float* res_hist, const uint8_t* tx_idx,
+        unsigned long long* bit_errors, int32_t* status, void* stream) {
+  return run_uniform(H, y, sigma2, qam_order, Ain, bin, n_rx, k, batch, iters, block_L, prec, x_hat, sym_idx,
+                     rel_res, res_hist, tx_idx, bit_errors, status, stream, -1, true);
 }
 
 }  // namespace
@@ -237,7 +264,8 @@ int fpcg_path(int32_t n_rx, int32_t k, int32_t block_L, const fpcg_precision* pr
   if (check_prec(prec)) return -FPCG_EINVAL;
   if (k < 1 || k > 128 || n_rx < k || block_L < 0 || block_L > 32 || (block_L > 0 && k % block_L))
     return -FPCG_EINVAL;
-  return uses_tc(k, block_L, prec) && n_rx % 2 == 0 ? FPCG_PATH_TENSOR_CORE : FPCG_PATH_SIMT;
+  return !force_simt() && fpcg::tc_capable(k, block_L, prec) && n_rx % 2 == 0 ? FPCG_PATH_TENSOR_CORE
+                                                                               : FPCG_PATH_SIMT;
 }
 
 const char* fpcg_strerror(int code) {

@@ -1,0 +1,265 @@
+// Uneven-batch plans (fpcg_plan_*): systems grouped by (N, K) class, the packed
+// plan-order layout, the per-class kernel choice (autotuned on request) and the
+// CUDA-graph capture of the class launches.  Host code only; the kernels are the
+// uniform ones, reached through run_uniform.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/fpcg.h"
+#include "api_internal.cuh"
+
+struct fpcg_plan {
+  struct Class {
+    int32_t n, k, L, path;         // path: -1 = default choice, else FPCG_PATH_*
+    int64_t first, count;          // plan positions
+    int64_t h0, y0, x0;            // first element of the class in H, y, x_hat
+  };
+  int32_t iters, flags;
+  fpcg_precision prec;
+  std::vector<Class> cls;
+  std::vector<int64_t> order, h_off, y_off, x_off;
+  int64_t tot[3] = {0, 0, 0};
+  cudaStream_t cap = nullptr;      // capture stream (graphs cannot be captured on the legacy stream)
+  cudaGraphExec_t exec = nullptr;  // instantiated graph of the class launches
+  const void* key[10] = {};        // the run arguments it was captured with
+};
+
+namespace {
+
+constexpr int64_t kAlign = 32;  // elements: 256 bytes of complex64
+
+int64_t align_up(int64_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+void drop_graph(fpcg_plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  p->exec = nullptr;
+}
+
+// Issues every class on `s`; bit_errors is zeroed once.
+int enqueue(fpcg_plan* p, const void* H, const void* y, const double* sigma2, const int32_t* qam,
+            void* x_hat, uint8_t* sym, double* rel_res, const uint8_t* tx, unsigned long long* bits,
+            int32_t* status, cudaStream_t s) {
+  if (bits) {
+    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return fpcg::cuda_error(e);
+  }
+  for (const auto& c : p->cls) {
+    const float2* Hc = static_cast<const float2*>(H) + c.h0;
+    const float2* yc = static_cast<const float2*>(y) + c.y0;
+    float2* xc = static_cast<float2*>(x_hat) + c.x0;
+    const int rc = fpcg::run_uniform(Hc, yc, sigma2 + c.first, qam ? qam + c.first : nullptr, nullptr, nullptr,
+                                     c.n, c.k, c.count, p->iters, c.L, &p->prec, xc, sym ? sym + c.x0 : nullptr,
+                                     rel_res ? rel_res + c.first : nullptr, nullptr, tx ? tx + c.x0 : nullptr, bits,
+                                     status ? status + c.first : nullptr, s, c.path, false);
+    if (rc) return rc;
+  }
+  return FPCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fpcg_plan_create(const fpcg_batch_desc* d, fpcg_plan** out) {
+  if (!d || !out) return FPCG_EINVAL;
+  *out = nullptr;
+  if (d->batch < 0 || d->iters < 0 || d->block_L < 0 || d->block_L > 32) return FPCG_EINVAL;
+  if (d->batch > 0 && (!d->n_rx || !d->k)) return FPCG_EINVAL;
+  if (fpcg::check_precision(&d->prec)) return FPCG_EINVAL;
+  for (int64_t i = 0; i < d->batch; ++i) {
+    const int32_t n = d->n_rx[i], k = d->k[i];
+    if (k < 1 || k > 128 || n < k || n > 65536) return FPCG_EINVAL;
+    if (d->block_L > 0) {
+      const int32_t L = std::min(d->block_L, k);
+      if (k % L) return FPCG_EINVAL;
+    }
+  }
+  fpcg_plan* p = new (std::nothrow) fpcg_plan;
+  if (!p) return FPCG_ENOMEM;
+  try {
+    p->iters = d->iters;
+    p->flags = d->flags;
+    p->prec = d->prec;
+    // classes sorted by (K, N); caller order kept inside a class
+    std::vector<int64_t> idx((size_t)d->batch);
+    for (int64_t i = 0; i < d->batch; ++i) idx[(size_t)i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+      return d->k[a] != d->k[b] ? d->k[a] < d->k[b] : d->n_rx[a] < d->n_rx[b];
+    });
+    p->order = idx;
+    p->h_off.resize((size_t)d->batch);
+    p->y_off.resize((size_t)d->batch);
+    p->x_off.resize((size_t)d->batch);
+    int64_t h = 0, yv = 0, x = 0;
+    for (int64_t pos = 0; pos < d->batch; ++pos) {
+      const int64_t i = idx[(size_t)pos];
+      const int32_t n = d->n_rx[i], k = d->k[i];
+      if (p->cls.empty() || p->cls.back().n != n || p->cls.back().k != k) {
+        fpcg_plan::Class c;
+        c.n = n;
+        c.k = k;
+        c.L = d->block_L > 0 ? std::min(d->block_L, k) : 0;
+        c.path = -1;
+        c.first = pos;
+        c.count = 0;
+        c.h0 = h = align_up(h);
+        c.y0 = yv = align_up(yv);
+        c.x0 = x = align_up(x);
+        p->cls.push_back(c);
+      }
+      p->cls.back().count++;
+      p->h_off[(size_t)pos] = h;
+      p->y_off[(size_t)pos] = yv;
+      p->x_off[(size_t)pos] = x;
+      h += (int64_t)n * k;
+      yv += n;
+      x += k;
+    }
+    p->tot[0] = align_up(h);
+    p->tot[1] = align_up(yv);
+    p->tot[2] = align_up(x);
+  } catch (const std::bad_alloc&) {
+    delete p;
+    return FPCG_ENOMEM;
+  }
+  *out = p;
+  return FPCG_OK;
+}
+
+int fpcg_plan_layout(const fpcg_plan* p, int64_t* order, int64_t* h_off, int64_t* y_off, int64_t* x_off,
+                     int64_t totals[3]) {
+  if (!p) return FPCG_EINVAL;
+  const size_t n = p->order.size();
+  if (order) std::copy(p->order.begin(), p->order.end(), order);
+  if (h_off) std::copy(p->h_off.begin(), p->h_off.end(), h_off);
+  if (y_off) std::copy(p->y_off.begin(), p->y_off.end(), y_off);
+  if (x_off) std::copy(p->x_off.begin(), p->x_off.end(), x_off);
+  if (totals) std::copy(p->tot, p->tot + 3, totals);
+  (void)n;
+  return FPCG_OK;
+}
+
+int fpcg_plan_classes(const fpcg_plan* p, int32_t* n_classes, fpcg_class_info* info) {
+  if (!p || !n_classes) return FPCG_EINVAL;
+  *n_classes = (int32_t)p->cls.size();
+  if (info) {
+    for (size_t c = 0; c < p->cls.size(); ++c) {
+      const auto& k = p->cls[c];
+      info[c].n_rx = k.n;
+      info[c].k = k.k;
+      info[c].block_L = k.L;
+      info[c].path = k.path >= 0 ? k.path : fpcg_path(k.n, k.k, k.L, &p->prec);
+      info[c].first = k.first;
+      info[c].count = k.count;
+    }
+  }
+  return FPCG_OK;
+}
+
+int fpcg_plan_autotune(fpcg_plan* p, const void* H, const void* y, const double* sigma2, const int32_t* qam,
+                       void* x_hat, uint8_t* sym, double* rel_res, int32_t* status, void* stream) {
+  if (!p || !H || !y || !sigma2 || !x_hat) return FPCG_EINVAL;
+  if (sym && !qam) return FPCG_EINVAL;
+  drop_graph(p);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fpcg::cuda_error(ce);
+  }
+  int rc = FPCG_OK;
+  for (auto& c : p->cls) {
+    if (!(fpcg::tc_capable(c.k, c.L, &p->prec) && c.n % 2 == 0)) {
+      c.path = FPCG_PATH_SIMT;
+      continue;
+    }
+    const float2* Hc = static_cast<const float2*>(H) + c.h0;
+    const float2* yc = static_cast<const float2*>(y) + c.y0;
+    float2* xc = static_cast<float2*>(x_hat) + c.x0;
+    float best = -1.f;
+    int best_path = FPCG_PATH_TENSOR_CORE;
+    for (int path : {FPCG_PATH_TENSOR_CORE, FPCG_PATH_SIMT}) {
+      float ms = 0.f;
+      for (int rep = 0; rep < 4 && rc == FPCG_OK; ++rep) {  // one warm-up, three timed
+        if (rep == 1) cudaEventRecord(e0, s);
+        rc = fpcg::run_uniform(Hc, yc, sigma2 + c.first, qam ? qam + c.first : nullptr, nullptr, nullptr, c.n, c.k,
+                               c.count, p->iters, c.L, &p->prec, xc, sym ? sym + c.x0 : nullptr,
+                               rel_res ? rel_res + c.first : nullptr, nullptr, nullptr, nullptr,
+                               status ? status + c.first : nullptr, s, path, false);
+      }
+      if (rc == FPCG_ENOTSUP && path == FPCG_PATH_TENSOR_CORE) {  // e.g. unaligned data
+        rc = FPCG_OK;
+        continue;
+      }
+      if (rc) break;
+      cudaEventRecord(e1, s);
+      ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) {
+        rc = fpcg::cuda_error(ce);
+        break;
+      }
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best < 0.f || ms < best) {
+        best = ms;
+        best_path = path;
+      }
+    }
+    if (rc) break;
+    c.path = best_path;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+int fpcg_plan_run(fpcg_plan* p, const void* H, const void* y, const double* sigma2, const int32_t* qam,
+                  void* x_hat, uint8_t* sym, double* rel_res, const uint8_t* tx, unsigned long long* bits,
+                  int32_t* status, void* stream) {
+  if (!p) return FPCG_EINVAL;
+  if (!p->cls.empty() && (!H || !y || !sigma2 || !x_hat)) return FPCG_EINVAL;
+  if ((sym || bits) && !qam) return FPCG_EINVAL;
+  if ((tx != nullptr) != (bits != nullptr)) return FPCG_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!(p->flags & FPCG_PLAN_GRAPH)) return enqueue(p, H, y, sigma2, qam, x_hat, sym, rel_res, tx, bits, status, s);
+  const void* key[10] = {H, y, sigma2, qam, x_hat, sym, rel_res, tx, bits, status};
+  if (p->exec && !std::equal(key, key + 10, p->key)) drop_graph(p);
+  if (!p->exec) {
+    cudaError_t e = cudaSuccess;
+    if (!p->cap) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fpcg::cuda_error(e);
+    e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fpcg::cuda_error(e);
+    const int rc = enqueue(p, H, y, sigma2, qam, x_hat, sym, rel_res, tx, bits, status, p->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(p->cap, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fpcg::cuda_error(e);
+    e = cudaGraphInstantiate(&p->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      p->exec = nullptr;
+      return fpcg::cuda_error(e);
+    }
+    std::copy(key, key + 10, p->key);
+  }
+  const cudaError_t e = cudaGraphLaunch(p->exec, s);
+  return e == cudaSuccess ? FPCG_OK : fpcg::cuda_error(e);
+}
+
+int fpcg_plan_destroy(fpcg_plan* p) {
+  if (!p) return FPCG_OK;
+  drop_graph(p);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  delete p;
+  return FPCG_OK;
+}
+
+}  // extern "C"

@@ -54,6 +54,19 @@ def precision(gram="fp32", mv="fp32", ip="fp32", w="fp32", refine_steps=0, refin
                      int(refine_iters), int(alpha_num), int(fp8_block), FORMAT[resid])
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int64), ("n_rx", ctypes.c_void_p), ("k", ctypes.c_void_p),
+                ("iters", ctypes.c_int32), ("block_L", ctypes.c_int32), ("prec", Precision),
+                ("flags", ctypes.c_int32)]
+
+
+class ClassInfo(ctypes.Structure):
+    _fields_ = [("n_rx", ctypes.c_int32), ("k", ctypes.c_int32), ("block_L", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("first", ctypes.c_int64), ("count", ctypes.c_int64)]
+
+
+PLAN_GRAPH = 1
+
 _lib = None
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -87,6 +100,18 @@ def lib():
         L.fpcg_last_cuda_error.restype = ctypes.c_char_p
         L.fpcg_version.argtypes = []
         L.fpcg_version.restype = ctypes.c_int
+        L.fpcg_plan_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(ctypes.c_void_p)]
+        L.fpcg_plan_create.restype = ctypes.c_int
+        L.fpcg_plan_layout.argtypes = [_P, _P, _P, _P, _P, _P]
+        L.fpcg_plan_layout.restype = ctypes.c_int
+        L.fpcg_plan_classes.argtypes = [_P, ctypes.POINTER(_I32), _P]
+        L.fpcg_plan_classes.restype = ctypes.c_int
+        L.fpcg_plan_autotune.argtypes = [_P] * 10
+        L.fpcg_plan_autotune.restype = ctypes.c_int
+        L.fpcg_plan_run.argtypes = [_P] * 12
+        L.fpcg_plan_run.restype = ctypes.c_int
+        L.fpcg_plan_destroy.argtypes = [_P]
+        L.fpcg_plan_destroy.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -219,3 +244,107 @@ def detect(H, y, sigma2, qam_order, iters, prec, L=None, tx_idx=None, hist=False
     else:
         fpbjcg_detect(H, y, sigma2, qam_order, iters, L, prec, out["x"], **kw)
     return out
+
+
+class Plan:
+    """An fpcg_plan over systems of different (N, K) (fpcg_plan_* in fpcg.h).
+
+    ``n_rx`` and ``k`` are per-system sequences in the caller's order.  The
+    layout (plan order, offsets, buffer sizes) is read back from the library;
+    ``run`` and ``autotune`` take packed device buffers in that layout.
+    """
+
+    def __init__(self, n_rx, k, iters, prec, block_L=0, graph=False):
+        import numpy as np
+        self._n = np.ascontiguousarray(n_rx, dtype=np.int32)
+        self._k = np.ascontiguousarray(k, dtype=np.int32)
+        if self._n.shape != self._k.shape or self._n.ndim != 1:
+            raise ValueError("n_rx and k must be 1-D and of equal length")
+        self.batch = int(self._n.size)
+        d = BatchDesc(self.batch, self._n.ctypes.data, self._k.ctypes.data, int(iters),
+                      int(block_L or 0), prec, PLAN_GRAPH if graph else 0)
+        h = ctypes.c_void_p()
+        _check(lib().fpcg_plan_create(ctypes.byref(d), ctypes.byref(h)), "fpcg_plan_create")
+        self._h = h
+        self.prec = prec
+        self.order = np.empty(self.batch, dtype=np.int64)
+        self.h_off = np.empty(self.batch, dtype=np.int64)
+        self.y_off = np.empty(self.batch, dtype=np.int64)
+        self.x_off = np.empty(self.batch, dtype=np.int64)
+        tot = np.empty(3, dtype=np.int64)
+        _check(lib().fpcg_plan_layout(self._h, self.order.ctypes.data, self.h_off.ctypes.data,
+                                      self.y_off.ctypes.data, self.x_off.ctypes.data, tot.ctypes.data),
+               "fpcg_plan_layout")
+        self.totals = tuple(int(v) for v in tot)
+
+    def pack(self, H, y, sigma2, qam_order, tx_idx=None, device="cuda"):
+        """Copy per-system host arrays (caller order: H[i] (K, N), y[i] (N,),
+        sigma2[i], qam_order[i], tx_idx[i] (K,)) into plan-order device buffers."""
+        import numpy as np
+        Hp = np.zeros(self.totals[0], dtype=np.complex64)
+        yp = np.zeros(self.totals[1], dtype=np.complex64)
+        txp = np.zeros(self.totals[2], dtype=np.uint8) if tx_idx is not None else None
+        s2 = np.empty(self.batch, dtype=np.float64)
+        q = np.empty(self.batch, dtype=np.int32)
+        for pos, i in enumerate(self.order):
+            h = np.asarray(H[i], dtype=np.complex64).ravel()
+            Hp[self.h_off[pos]:self.h_off[pos] + h.size] = h
+            v = np.asarray(y[i], dtype=np.complex64)
+            yp[self.y_off[pos]:self.y_off[pos] + v.size] = v
+            if txp is not None:
+                t = np.asarray(tx_idx[i], dtype=np.uint8)
+                txp[self.x_off[pos]:self.x_off[pos] + t.size] = t
+            s2[pos] = sigma2[i]
+            q[pos] = qam_order[i]
+        out = {"H": torch.from_numpy(Hp).to(device), "y": torch.from_numpy(yp).to(device),
+               "sigma2": torch.from_numpy(s2).to(device), "qam": torch.from_numpy(q).to(device)}
+        out["tx"] = torch.from_numpy(txp).to(device) if txp is not None else None
+        return out
+
+    def unpack(self, packed, k, per_system=None):
+        """Split a plan-order buffer into per-system arrays in caller order: x_hat
+        or labels (offsets x_off, k[i] entries each) when per_system is None,
+        else a per-system array (rel_res, status) indexed by plan position."""
+        import numpy as np
+        a = packed.cpu().numpy() if isinstance(packed, torch.Tensor) else np.asarray(packed)
+        out = [None] * self.batch
+        for pos, i in enumerate(self.order):
+            out[i] = a[pos] if per_system else a[self.x_off[pos]:self.x_off[pos] + int(k[i])]
+        return out
+
+    def classes(self):
+        n = _I32()
+        _check(lib().fpcg_plan_classes(self._h, ctypes.byref(n), None), "fpcg_plan_classes")
+        info = (ClassInfo * n.value)()
+        _check(lib().fpcg_plan_classes(self._h, ctypes.byref(n), info), "fpcg_plan_classes")
+        return [dict(n_rx=c.n_rx, k=c.k, block_L=c.block_L, path=c.path, first=c.first, count=c.count)
+                for c in info]
+
+    def _bufs(self, H, y, sigma2, qam_order, x_hat, sym_idx, rel_res, status):
+        return [_ptr(H, torch.complex64, "H"), _ptr(y, torch.complex64, "y"),
+                _ptr(sigma2, torch.float64, "sigma2"), _ptr(qam_order, torch.int32, "qam_order"),
+                _ptr(x_hat, _xdtype(self.prec), "x_hat"), _ptr(sym_idx, torch.uint8, "sym_idx"),
+                _ptr(rel_res, torch.float64, "rel_res")], _ptr(status, torch.int32, "status")
+
+    def autotune(self, H, y, sigma2, qam_order, x_hat, sym_idx=None, rel_res=None, status=None,
+                 stream=None):
+        a, st = self._bufs(H, y, sigma2, qam_order, x_hat, sym_idx, rel_res, status)
+        _check(lib().fpcg_plan_autotune(self._h, *a, st, _stream(stream)), "fpcg_plan_autotune")
+
+    def run(self, H, y, sigma2, qam_order, x_hat, sym_idx=None, rel_res=None, tx_idx=None,
+            bit_errors=None, status=None, stream=None):
+        a, st = self._bufs(H, y, sigma2, qam_order, x_hat, sym_idx, rel_res, status)
+        _check(lib().fpcg_plan_run(self._h, *a, _ptr(tx_idx, torch.uint8, "tx_idx"),
+                                   _ptr(bit_errors, torch.int64, "bit_errors"), st, _stream(stream)),
+               "fpcg_plan_run")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fpcg_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

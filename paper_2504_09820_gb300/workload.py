@@ -149,3 +149,55 @@ def c2_kron_128x32(batch=8192, snr_db=10.0, seed=1002):
 def c3_kron_256x64(batch=16384, seed=1003):
     """N=256, K=64, Kronecker rho=0.7 both ends, 64-QAM, SNR 18 dB."""
     return Spec(N=256, K=64, batch=batch, rho=0.7, qam=64, snr_db=18.0, seed=seed)
+
+
+@dataclass
+class MixedSpec:
+    """An uneven batch: every system draws its K, the ratio N/K (N capped), rho
+    and the QAM order uniformly from the given sets."""
+    batch: int
+    ks: tuple = (8, 16, 32, 64, 128)
+    ratios: tuple = (2, 4, 8)
+    n_cap: int = 512
+    rhos: tuple = (0.0, 0.3, 0.7)
+    qams: tuple = (16, 64, 256)
+    snr_db: float = 18.0
+    seed: int = 1004
+
+
+def mixed_params(spec):
+    """Per-system (N, K, rho, QAM order) of an uneven batch, in system order."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([spec.seed, 0x6d6978])))
+    k = np.asarray(spec.ks, dtype=np.int32)[rng.integers(0, len(spec.ks), spec.batch)]
+    r = np.asarray(spec.ratios, dtype=np.int32)[rng.integers(0, len(spec.ratios), spec.batch)]
+    n = np.minimum(k * r, spec.n_cap).astype(np.int32)
+    rho = np.asarray(spec.rhos, dtype=np.float64)[rng.integers(0, len(spec.rhos), spec.batch)]
+    qam = np.asarray(spec.qams, dtype=np.int32)[rng.integers(0, len(spec.qams), spec.batch)]
+    return n, k, rho, qam
+
+
+def generate_mixed(spec):
+    """Draw an uneven batch.  Systems with equal (N, K, rho, QAM order) are drawn
+    together as one uniform batch (its own seed stream), then put back in
+    system order.  Returns per-system lists H[i] (K, N) complex64, y[i] (N,),
+    tx[i] (K,) uint8, x[i] (K,) complex128, and arrays n, k, rho, qam, sigma2."""
+    n, k, rho, qam = mixed_params(spec)
+    H = [None] * spec.batch
+    y = [None] * spec.batch
+    tx = [None] * spec.batch
+    x = [None] * spec.batch
+    keys = sorted(set(zip(n.tolist(), k.tolist(), rho.tolist(), qam.tolist())))
+    for g, (gn, gk, grho, gq) in enumerate(keys):
+        idx = np.nonzero((n == gn) & (k == gk) & (rho == grho) & (qam == gq))[0]
+        d = generate(Spec(N=gn, K=gk, batch=len(idx), rho=grho, qam=gq, snr_db=spec.snr_db,
+                          seed=spec.seed * 1000 + g))
+        for j, i in enumerate(idx):
+            H[i], y[i], tx[i], x[i] = d["H"][j], d["y"][j], d["tx"][j], d["x"][j]
+    return {"H": H, "y": y, "tx": tx, "x": x, "n": n, "k": k, "rho": rho, "qam": qam,
+            "sigma2": np.full(spec.batch, float(snr_to_sigma2(spec.snr_db)))}
+
+
+def mixed_kron(batch=12000, seed=1004):
+    """Uneven batch: K in {8,16,32,64,128}, N = K x {2,4,8} capped at 512, rho in
+    {0, 0.3, 0.7}, 16/64/256-QAM, SNR 18 dB."""
+    return MixedSpec(batch=batch, seed=seed)
