@@ -13,6 +13,7 @@ Under torchrun every rank detects its own batch (weak scaling); rank 0 prints
 one JSON line.
 """
 import argparse
+import math
 import json
 import os
 import statistics
@@ -173,6 +174,77 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mixed(args):
+    """Uneven batch through a plan: every system draws K in {8,...,128}, N = K x
+    {2, 4, 8} (at most 512), rho and the QAM order; one CUDA graph of one
+    persistent launch per (N, K) class, kernels chosen by the autotuner."""
+    import torch
+    from paper_2504_09820_gb300 import fpcg as F
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    F.lib()
+    spec = wl.mixed_kron(batch=args.batch or 12000)
+    d = wl.generate_mixed(spec)
+    prec = F.precision(**HEAD["prec"])
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for graph in (True, False):
+        plan = F.Plan(d["n"], d["k"], HEAD["iters"], prec, block_L=HEAD["L"], graph=graph)
+        g = plan.pack(d["H"], d["y"], d["sigma2"], d["qam"], d["tx"], device=dev)
+        o = {"x": torch.zeros(plan.totals[2], dtype=torch.complex64, device=dev),
+             "sym": torch.zeros(plan.totals[2], dtype=torch.uint8, device=dev),
+             "rel": torch.empty(plan.batch, dtype=torch.float64, device=dev),
+             "st": torch.empty(plan.batch, dtype=torch.int32, device=dev),
+             "be": torch.zeros(1, dtype=torch.int64, device=dev)}
+        t0 = time.perf_counter()
+        plan.autotune(g["H"], g["y"], g["sigma2"], g["qam"], o["x"], o["sym"], o["rel"], o["st"], stream=stream)
+        t_tune = time.perf_counter() - t0
+
+        def call():
+            plan.run(g["H"], g["y"], g["sigma2"], g["qam"], o["x"], o["sym"], o["rel"], g["tx"], o["be"], o["st"],
+                     stream=stream)
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(dev) as clk:
+            a.record(stream)
+            for _ in range(args.steps):
+                call()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+        res[graph] = {"t": a.elapsed_time(b) / 1e3 / args.steps, "tune_s": t_tune, "clocks": clk.summary(),
+                      "classes": plan.classes(), "bits": int(o["be"][0]), "status_max": int(o["st"].max())}
+        del g, o
+        plan.close()
+    r = res[True]
+    B = spec.batch
+    algo = float(sum(bytes_per_detection(int(n), int(k)) for n, k in zip(d["n"], d["k"])))
+    pk = peaks()
+    achieved = algo / r["t"] / 1e9
+    nbits = float(sum(int(k) * int(round(math.log2(q))) for k, q in zip(d["k"], d["qam"])))
+    paths = {}
+    for c in r["classes"]:
+        key = "tensor_core" if c["path"] == F.PATH_TENSOR_CORE else "simt"
+        paths[key] = paths.get(key, 0) + c["count"]
+    print(json.dumps({
+        "metric": "detections/s, uneven batch (one CUDA graph, one launch per (N, K) class)",
+        "value": B / r["t"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * r["t"], "higher_is_better": True, "dtype": "bf16-in/f32-acc", "data": "synthetic",
+        "config": {"workload": f"uneven batch of {B}: K in {spec.ks}, N = K x {spec.ratios} capped at "
+                               f"{spec.n_cap}, rho in {spec.rhos}, QAM in {spec.qams}, {spec.snr_db} dB",
+                   "method": HEAD["name"], "block_L": f"min({HEAD['L']}, K)", "iters": HEAD["iters"],
+                   "precision": HEAD["prec"], "classes": len(r["classes"]), "systems_per_path": paths,
+                   "l2": "inputs larger than L2; no flush needed"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"],
+                     "algorithmic_bytes_per_launch": algo},
+        "without_graph_ms": 1e3 * res[False]["t"], "autotune_s": r["tune_s"],
+        "ber_total": r["bits"] / nbits, "status_max": r["status_max"], "clocks": r["clocks"],
+        "class_table": [{k: c[k] for k in ("n_rx", "k", "block_L", "path", "count")} for c in r["classes"]],
+    }), flush=True)
+
+
 def config_dict(spec):
     return {"workload": f"kronecker rho={spec.rho} N={spec.N} K={spec.K} batch={spec.batch} "
                         f"{spec.qam}-QAM {spec.snr_db:g} dB",
@@ -192,11 +264,16 @@ def main():
     ap.add_argument("--batch", type=int, default=None, help="override the batch (profiling runs)")
     ap.add_argument("--only-head", action="store_true",
                     help="time only the headline detector (profiling runs; no comparator, BER, e2e)")
+    ap.add_argument("--workload", default="kron256x64", choices=["kron256x64", "mixed"],
+                    help="mixed: the uneven batch through a plan (its own JSON line)")
     ap.add_argument("--breakdown", action="store_true",
                     help="also time the Gram alone and the detector without CG iterations")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "mixed":
+        run_mixed(args)
         return
 
     import torch
@@ -301,21 +378,32 @@ def main():
     c_total, _ = timed(comp, max(2, args.steps // 2), 1)
     comp_det_s = world * B * max(2, args.steps // 2) / c_total
 
-    # BER of both paths vs the fp64 direct LMMSE solve on a sample
+    # BER of both paths vs fp64 LMMSE on a sample.  The LMMSE estimate is the
+    # library's own fp64 path: CG in fp64 for 2K iterations (exact after K in
+    # exact arithmetic), sliced by the same slicer; bit errors counted on the GPU.
     ber = None
     if rank == 0:
-        from oracle import detect as D
-        from oracle import qam as Q
-        ns = 1024
-        xs = D.lmmse(d["H"][:ns], d["y"][:ns], d["sigma2"][:ns])
-        nbits = ns * K * Q.bits_per_symbol(spec.qam)
-        e_ref = Q.bit_errors(Q.slice_symbols(xs, spec.qam, "fp64"), d["tx"][:ns])
-        e_head = Q.bit_errors(o_head["sym"][:ns].cpu().numpy(), d["tx"][:ns])
-        e_comp = Q.bit_errors(o_comp["sym"][:ns].cpu().numpy(), d["tx"][:ns])
+        ns = min(1024, B)
+        bps = int(round(math.log2(spec.qam)))
+        ref = {k: g[k][:ns].contiguous() for k in g}
+        o_ref = {"x": torch.empty((ns, K), dtype=torch.complex128, device=dev),
+                 "sym": torch.empty((ns, K), dtype=torch.uint8, device=dev),
+                 "be": torch.zeros(1, dtype=torch.int64, device=dev)}
+        F.fpcg_detect(ref["H"], ref["y"], ref["sigma2"], ref["qam"], 2 * K, F.precision(w="fp64"), o_ref["x"],
+                      sym_idx=o_ref["sym"], tx_idx=ref["tx"], bit_errors=o_ref["be"], stream=stream)
+        popc = torch.tensor([bin(v).count("1") for v in range(256)], dtype=torch.int64, device=dev)
+
+        def errors(sym):
+            return int(popc[(sym[:ns] ^ ref["tx"]).long()].sum())
+        torch.cuda.synchronize(dev)
+        e_ref = int(o_ref["be"][0])
+        e_head, e_comp = errors(o_head["sym"]), errors(o_comp["sym"])
+        nbits = ns * K * bps
         ber = {"sample_systems": ns, "lmmse_fp64": e_ref / nbits, "head": e_head / nbits,
                "comparator": e_comp / nbits, "head_rel_to_lmmse": e_head / e_ref - 1,
                "comparator_rel_to_lmmse": e_comp / e_ref - 1,
-               "head_full_batch": int(o_head["be"][0]) / (B * K * Q.bits_per_symbol(spec.qam))}
+               "lmmse_reference": f"fp64 CG, {2 * K} iterations (SIMT kernel)",
+               "head_full_batch": int(o_head["be"][0]) / (B * K * bps)}
 
     # end to end through the public API from pinned host buffers
     hst = {k: g[k].cpu().pin_memory() for k in g}

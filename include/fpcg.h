@@ -75,6 +75,8 @@ enum {
 #define FPCG_ST_TIMEOUT  32  /* a pipeline wait of the tensor-core kernel gave up: outputs
                                 of this system are not valid (never expected; reported
                                 instead of hanging the GPU) */
+#define FPCG_ST_BAD_INDEX 64 /* fpcg_detect_shared: rb_index[s] outside [0, n_rb): nothing solved,
+                                x_hat and labels 0 */
 
 /*
  * Precision of each step (the roles u_MV, u_IP, u_W of Algorithms 2/3).
@@ -214,6 +216,32 @@ FPCG_API int fpcg_gram(const void* H, const void* y, const double* sigma2, int32
 #define FPCG_PATH_SIMT 0
 #define FPCG_PATH_TENSOR_CORE 1
 FPCG_API int fpcg_path(int32_t n_rx, int32_t k, int32_t block_L, const fpcg_precision* prec);
+
+/*
+ * fpcg_detect_shared -- many right-hand sides per channel (Section II's model
+ * with one H for a group of received vectors, e.g. the 12 subcarriers x 14
+ * symbols of a resource block).  Each group's Gram matrix is formed once, by
+ * fpcg_gram, and kept; every received vector y_s is then detected against the
+ * Gram of its group g = rb_index[s]: its own matched filter b_s = fl(H_g)^H
+ * fl(y_s) (eq. inversion, rounded to prec->gram like the Gram), then Algorithm
+ * 2 (block_L = 0) or Algorithm 3 (block_L > 0), refinement, slicing, as in
+ * fpcg_detect.  One CTA per received vector (the SIMT kernel).
+ *   A          [n_rb][K][K] complex64 (complex128 in FP64 mode): A_g + sigma_g^2 I,
+ *              as fpcg_gram writes it with the same gram format
+ *   H          [n_rb][K][N] complex64: the groups' channels (the layout of fpcg_detect)
+ *   y          [n_rhs][N] complex64
+ *   rb_index   [n_rhs] int32, group of each received vector; one outside [0, n_rb)
+ *              gives FPCG_ST_BAD_INDEX for that vector
+ *   qam_order, x_hat, sym_idx, rel_res, tx_idx, bit_errors, status: per received
+ *              vector, as in fpcg_detect (batch = n_rhs)
+ * All device pointers, caller-owned.  Returns FPCG_EINVAL / FPCG_ENOTSUP as
+ * fpcg_detect does (K <= 128; K <= 64 in FP64 mode).
+ */
+FPCG_API int fpcg_detect_shared(const void* A, const void* H, const void* y, const int32_t* rb_index,
+                                const int32_t* qam_order, int32_t n_rx, int32_t k, int64_t n_rb,
+                                int64_t n_rhs, int32_t iters, int32_t block_L, const fpcg_precision* prec,
+                                void* x_hat, uint8_t* sym_idx, double* rel_res, const uint8_t* tx_idx,
+                                unsigned long long* bit_errors, int32_t* status, void* stream);
 
 /*
  * ---- Uneven batches: a plan over systems of different (N, K) ----

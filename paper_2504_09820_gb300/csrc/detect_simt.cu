@@ -270,6 +270,40 @@ __device__ void load_gram(const SimtParams& P, const Smem<T>& S, int64_t sys) {
   __syncthreads();
 }
 
+// Shared-Gram mode: A (with sigma^2 I) of the system's group from Ain, and its
+// own matched filter b = fl(H)^H fl(y) (eq. inversion) from the group's H and
+// the system's y, rounded like the Gram.  One warp per row k of b, lanes over
+// the antennas, shuffle reduction.  Returns false for an index out of range.
+template <typename T>
+__device__ bool load_shared(const SimtParams& P, const Smem<T>& S, int64_t sys) {
+  const int K = P.K, N = P.N, AS = K + 1;
+  const int64_t g = P.a_map[sys];
+  if (g < 0 || g >= P.n_shared) return false;
+  const cplx<T>* Ag = (const cplx<T>*)P.Ain + (size_t)g * K * K;
+  for (int idx = threadIdx.x; idx < K * K; idx += NT) S.A[(idx / K) * AS + idx % K] = Ag[idx];
+  const float2* Hg = P.H + (size_t)g * K * N;
+  const float2* yg = P.y + (size_t)sys * N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = warp; k < K; k += NT / 32) {
+    T re = T(0), im = T(0);
+    for (int n = lane; n < N; n += 32) {
+      const float2 h = Hg[(size_t)k * N + n], yy = yg[n];
+      const T hr = round_gram<T>(h.x, P.gram), hi = round_gram<T>(h.y, P.gram);
+      const T yr = round_gram<T>(yy.x, P.gram), yi = round_gram<T>(yy.y, P.gram);
+      re = fma(hr, yr, fma(hi, yi, re));  // conj(h_k) y
+      im = fma(hr, yi, fma(-hi, yr, im));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) S.b[k] = cplx<T>{re, im};
+  }
+  __syncthreads();
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // Step 2: block-Jacobi inverse, in-place Gauss-Jordan per diagonal block.
 // Returns nonzero (in every thread) if some pivot was not positive.
@@ -620,8 +654,24 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
   const int K = P.K;
   int st = 0;
 
-  if (P.Ain) load_gram(P, S, sys);
-  else gram_phase(P, S, sys);
+  if (P.Ain && P.a_map) {
+    if (!load_shared(P, S, sys)) {  // index out of range: x = 0, labels 0, status
+      cplx<T>* xo = (cplx<T>*)P.x_hat + (size_t)sys * K;
+      for (int k = threadIdx.x; k < K; k += NT) {
+        xo[k] = cplx<T>{T(0), T(0)};
+        if (P.sym) P.sym[(size_t)sys * K + k] = 0;
+      }
+      if (threadIdx.x == 0) {
+        if (P.rel_res) P.rel_res[sys] = 0.0;
+        if (P.status) P.status[sys] = 64;  // FPCG_ST_BAD_INDEX
+      }
+      return;
+    }
+  } else if (P.Ain) {
+    load_gram(P, S, sys);
+  } else {
+    gram_phase(P, S, sys);
+  }
   if (P.A_out) {  // gram-only mode (fpcg_gram)
     cplx<T>* Ao = (cplx<T>*)P.A_out + (size_t)sys * K * K;
     cplx<T>* bo = (cplx<T>*)P.b_out + (size_t)sys * K;

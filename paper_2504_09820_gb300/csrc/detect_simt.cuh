@@ -14,6 +14,8 @@ struct SimtParams {
   const int32_t* qam;       // [batch], may be null when sym and bit_errors are null
   const void* Ain;          // [batch][K][K] given Gram (fpcg_solve_gram) or null
   const void* bin;          // [batch][K] given right-hand side
+  const int32_t* a_map;     // shared-Gram mode (with Ain, H, y): system i uses A and H number a_map[i]
+  int64_t n_shared;         //   number of shared Gram matrices (bound of a_map)
   int N, K, iters, L, refine_steps, refine_iters, alpha_num, gram, ip, resid_fp64;
   int64_t batch;
   void* x_hat;

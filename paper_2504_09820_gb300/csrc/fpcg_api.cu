@@ -203,6 +203,57 @@ int fpbjcg_detect(const void* H, const void* y, const double* sigma2, const int3
              x_hat, sym_idx, rel_res, res_hist, tx_idx, bit_errors, status, stream);
 }
 
+int fpcg_detect_shared(const void* A, const void* H, const void* y, const int32_t* rb_index,
+                       const int32_t* qam_order, int32_t n_rx, int32_t k, int64_t n_rb, int64_t n_rhs,
+                       int32_t iters, int32_t block_L, const fpcg_precision* prec, void* x_hat,
+                       uint8_t* sym_idx, double* rel_res, const uint8_t* tx_idx,
+                       unsigned long long* bit_errors, int32_t* status, void* stream) {
+  int rc = check_prec(prec);
+  if (rc) return rc;
+  if (!A || !H || !y || !rb_index || !x_hat) return FPCG_EINVAL;
+  if (k < 1 || k > 128 || n_rx < k || n_rx > 65536 || n_rb < 0 || n_rhs < 0 || iters < 0) return FPCG_EINVAL;
+  if (block_L < 0 || block_L > 32 || (block_L > 0 && k % block_L)) return FPCG_EINVAL;
+  if ((sym_idx || bit_errors) && !qam_order) return FPCG_EINVAL;
+  if ((tx_idx != nullptr) != (bit_errors != nullptr)) return FPCG_EINVAL;
+  const int fp64 = prec->w == FPCG_FP64;
+  if (fp64 && k > 64) return FPCG_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (bit_errors) {
+    cudaError_t e = cudaMemsetAsync(bit_errors, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (n_rhs == 0) return FPCG_OK;
+  rc = check_device_smem(fpcg::simt_smem_bytes(fp64, k, block_L, prec->mv));
+  if (rc) return rc;
+  fpcg::SimtParams P;
+  memset(&P, 0, sizeof(P));
+  P.H = (const float2*)H;
+  P.y = (const float2*)y;
+  P.qam = qam_order;
+  P.Ain = A;
+  P.a_map = rb_index;
+  P.n_shared = n_rb;
+  P.N = n_rx;
+  P.K = k;
+  P.iters = iters;
+  P.L = block_L;
+  P.refine_steps = prec->refine_steps;
+  P.refine_iters = prec->refine_iters < 0 ? iters : prec->refine_iters;
+  P.alpha_num = prec->alpha_num;
+  P.gram = prec->gram;
+  P.ip = prec->ip;
+  P.resid_fp64 = prec->resid == FPCG_FP64;
+  P.batch = n_rhs;
+  P.x_hat = x_hat;
+  P.sym = sym_idx;
+  P.rel_res = rel_res;
+  P.tx = tx_idx;
+  P.bit_errors = bit_errors;
+  P.status = status;
+  cudaError_t e = fpcg::launch_detect_simt(P, fp64, fp64 ? FPCG_FP64 : prec->mv, s);
+  return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+}
+
 int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t batch, int32_t iters,
                     int32_t block_L, const fpcg_precision* prec, void* x_hat, double* rel_res,
                     float* res_hist, int32_t* status, void* stream) {

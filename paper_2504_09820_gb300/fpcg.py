@@ -23,7 +23,7 @@ FP64, FP32, FP16, BF16, FP8E4M3 = 0, 1, 2, 3, 4
 FORMAT = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16, "e4m3": FP8E4M3, "fp8": FP8E4M3}
 
 # status bits (FPCG_ST_*)
-ST_BREAKDOWN, ST_RHO_ZERO, ST_NONFINITE, ST_BJ_FAIL, ST_BAD_QAM, ST_TIMEOUT = 1, 2, 4, 8, 16, 32
+ST_BREAKDOWN, ST_RHO_ZERO, ST_NONFINITE, ST_BJ_FAIL, ST_BAD_QAM, ST_TIMEOUT, ST_BAD_INDEX = 1, 2, 4, 8, 16, 32, 64
 
 # return codes
 OK, EINVAL, ENOTSUP, ECUDA, ENOMEM = 0, 1, 2, 3, 4
@@ -100,6 +100,9 @@ def lib():
         L.fpcg_last_cuda_error.restype = ctypes.c_char_p
         L.fpcg_version.argtypes = []
         L.fpcg_version.restype = ctypes.c_int
+        L.fpcg_detect_shared.argtypes = [_P, _P, _P, _P, _P, _I32, _I32, _I64, _I64, _I32, _I32,
+                                         ctypes.POINTER(Precision), _P, _P, _P, _P, _P, _P, _P]
+        L.fpcg_detect_shared.restype = ctypes.c_int
         L.fpcg_plan_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(ctypes.c_void_p)]
         L.fpcg_plan_create.restype = ctypes.c_int
         L.fpcg_plan_layout.argtypes = [_P, _P, _P, _P, _P, _P]
@@ -219,6 +222,23 @@ def fpcg_gram(H, y, sigma2, gram, A, b, status=None, stream=None):
                            _ptr(sigma2, torch.float64, "sigma2"), int(N), int(K), int(batch),
                            FORMAT[gram], _ptr(A, dt, "A"), _ptr(b, dt, "b"),
                            _ptr(status, torch.int32, "status"), _stream(stream)), "fpcg_gram")
+
+
+def fpcg_detect_shared(A, H, y, rb_index, qam_order, iters, block_L, prec, x_hat, sym_idx=None,
+                       rel_res=None, tx_idx=None, bit_errors=None, status=None, stream=None):
+    """Marshal a call to fpcg_detect_shared: A [n_rb][K][K] from fpcg_gram, H
+    [n_rb][K][N], y [n_rhs][N], rb_index [n_rhs] (group of each y)."""
+    n_rb, K, N = H.shape
+    n_rhs = y.shape[0]
+    dt = _xdtype(prec)
+    _check(lib().fpcg_detect_shared(_ptr(A, dt, "A"), _ptr(H, torch.complex64, "H"),
+                                    _ptr(y, torch.complex64, "y"), _ptr(rb_index, torch.int32, "rb_index"),
+                                    _ptr(qam_order, torch.int32, "qam_order"), int(N), int(K), int(n_rb),
+                                    int(n_rhs), int(iters), int(block_L or 0), ctypes.byref(prec),
+                                    _ptr(x_hat, dt, "x_hat"), _ptr(sym_idx, torch.uint8, "sym_idx"),
+                                    _ptr(rel_res, torch.float64, "rel_res"), _ptr(tx_idx, torch.uint8, "tx_idx"),
+                                    _ptr(bit_errors, torch.int64, "bit_errors"), _ptr(status, torch.int32, "status"),
+                                    _stream(stream)), "fpcg_detect_shared")
 
 
 def detect(H, y, sigma2, qam_order, iters, prec, L=None, tx_idx=None, hist=False, stream=None):

@@ -201,3 +201,42 @@ def mixed_kron(batch=12000, seed=1004):
     """Uneven batch: K in {8,16,32,64,128}, N = K x {2,4,8} capped at 512, rho in
     {0, 0.3, 0.7}, 16/64/256-QAM, SNR 18 dB."""
     return MixedSpec(batch=batch, seed=seed)
+
+
+@dataclass
+class RBSpec:
+    """Resource blocks sharing a channel: n_rb channels H (N x K), each seen by
+    res_per_rb received vectors (subcarriers x symbols) with their own symbols
+    and noise."""
+    N: int
+    K: int
+    n_rb: int
+    res_per_rb: int = 168
+    rho: float = 0.5
+    qam: int = 64
+    snr_db: float = 15.0
+    seed: int = 1005
+
+
+def generate_rb(spec):
+    """Draw the channels (one per resource block) and the received vectors.
+    Returns H (n_rb, K, N) complex64, y (n_rb*res_per_rb, N) complex64,
+    rb_index (n_rb*res_per_rb,) int32 (received vector s belongs to block
+    s // res_per_rb), tx (n, K) uint8, x (n, K) complex128, sigma2 (n_rb,)
+    float64 (one per block) and qam (n,) int32."""
+    ch = generate(Spec(N=spec.N, K=spec.K, batch=spec.n_rb, rho=spec.rho, qam=spec.qam,
+                       snr_db=spec.snr_db, seed=spec.seed))
+    H = ch["H"]                                      # (n_rb, K, N)
+    n = spec.n_rb * spec.res_per_rb
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([spec.seed, 0x7262])))
+    tx = rng.integers(0, spec.qam, size=(n, spec.K)).astype(np.uint8)
+    x = qam_modulate(tx, spec.qam)
+    rb = (np.arange(n) // spec.res_per_rb).astype(np.int32)
+    Hn = H.transpose(0, 2, 1).astype(np.complex128)  # (n_rb, N, K)
+    yc = np.einsum("snk,sk->sn", Hn[rb], x)
+    sigma2 = float(snr_to_sigma2(spec.snr_db))
+    sn = np.sqrt(sigma2 / 2.0)
+    yc = yc + (rng.standard_normal((n, spec.N)) + 1j * rng.standard_normal((n, spec.N))) * sn
+    return {"H": H, "y": yc.astype(np.complex64), "rb_index": rb, "tx": tx, "x": x,
+            "sigma2": np.full(spec.n_rb, sigma2), "qam": np.full(n, spec.qam, dtype=np.int32),
+            "N": spec.N, "K": spec.K}

@@ -1,0 +1,89 @@
+"""fpcg_detect_shared: one Gram per resource block (fpcg_gram), many received
+vectors per block, against the oracle run on each vector with its block's H."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import qam as Q
+from paper_2504_09820_gb300 import fpcg as F
+from paper_2504_09820_gb300 import workload as wl
+
+from gpu_helpers import oracle_detect, rel_err
+
+pytestmark = pytest.mark.gpu
+
+PREC = dict(gram="bf16", mv="fp16", refine_steps=1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    F.lib()
+
+
+def _shared(d, iters, L, prec_kw, rb=None):
+    n_rb, K, N = d["H"].shape
+    dev = "cuda"
+    H = torch.from_numpy(d["H"]).to(dev)
+    prec = F.precision(**prec_kw)
+    xdt = torch.complex128 if prec_kw.get("w") == "fp64" else torch.complex64
+    A = torch.empty((n_rb, K, K), dtype=xdt, device=dev)
+    b = torch.empty((n_rb, K), dtype=xdt, device=dev)
+    F.fpcg_gram(H, torch.zeros((n_rb, N), dtype=torch.complex64, device=dev),
+                torch.from_numpy(d["sigma2"]).to(dev), prec_kw["gram"], A, b)
+    y = torch.from_numpy(d["y"]).to(dev)
+    n = y.shape[0]
+    rbi = torch.from_numpy(d["rb_index"] if rb is None else rb).to(dev)
+    out = {"x": torch.empty((n, K), dtype=xdt, device=dev), "sym": torch.empty((n, K), dtype=torch.uint8, device=dev),
+           "rel": torch.empty(n, dtype=torch.float64, device=dev), "st": torch.empty(n, dtype=torch.int32, device=dev),
+           "be": torch.zeros(1, dtype=torch.int64, device=dev)}
+    F.fpcg_detect_shared(A, H, y, rbi, torch.from_numpy(d["qam"]).to(dev), iters, L, prec, out["x"],
+                         sym_idx=out["sym"], rel_res=out["rel"], tx_idx=torch.from_numpy(d["tx"]).to(dev),
+                         bit_errors=out["be"], status=out["st"])
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _per_vector(d):
+    """The same problems as independent systems: each y with its block's H."""
+    rb = d["rb_index"]
+    return {"H": d["H"][rb], "y": d["y"], "sigma2": d["sigma2"][rb], "qam": d["qam"], "tx": d["tx"]}
+
+
+@pytest.mark.parametrize("N,K", [(64, 8), (128, 32), (256, 64), (512, 128)])
+def test_shared_matches_oracle(N, K):
+    d = wl.generate_rb(wl.RBSpec(N=N, K=K, n_rb=5, res_per_rb=24, seed=40 + K))
+    L = min(8, K)
+    res = _shared(d, 6, L, PREC)
+    ref = oracle_detect(_per_vector(d), 6, PREC, L=L)
+    e = rel_err(res["x"], ref["x"])
+    assert np.quantile(e, 0.99) < 2e-3 and e.max() < 1e-2, (np.quantile(e, 0.99), e.max())
+    assert np.array_equal(Q.slice_symbols(res["x"], 64, "fp32"), res["sym"])
+    assert int(res["be"][0]) == Q.bit_errors(res["sym"], d["tx"])
+    allowed = F.ST_RHO_ZERO | (F.ST_BREAKDOWN if L == K else 0)
+    assert np.all(res["st"] & ~allowed == 0)
+
+
+def test_shared_fp64_equals_exact_solve():
+    """fp64 CG, 2K iterations (in fp64 at kappa ~ 20, K steps leave ~1e-6; 2K reach
+    rounding level) against the direct solve of each vector's own system."""
+    from oracle import detect as D
+    d = wl.generate_rb(wl.RBSpec(N=64, K=16, n_rb=3, res_per_rb=12, seed=3))
+    res = _shared(d, 32, 0, dict(w="fp64", gram="fp64", mv="fp64", ip="fp64"))
+    pv = _per_vector(d)
+    A, b = D.gram_mf(pv["H"], pv["y"], pv["sigma2"])
+    assert rel_err(res["x"], D.cholesky_solve(A, b)).max() < 1e-10
+
+
+def test_shared_bad_index():
+    d = wl.generate_rb(wl.RBSpec(N=64, K=16, n_rb=3, res_per_rb=4, seed=5))
+    rb = d["rb_index"].copy()
+    rb[2] = 3          # outside [0, n_rb)
+    rb[5] = -1
+    res = _shared(d, 6, 4, PREC, rb=rb)
+    assert res["st"][2] == F.ST_BAD_INDEX and res["st"][5] == F.ST_BAD_INDEX
+    assert np.all(res["x"][[2, 5]] == 0)
+    ok = np.ones(len(rb), bool)
+    ok[[2, 5]] = False
+    assert np.all(res["st"][ok] & ~F.ST_RHO_ZERO == 0)
