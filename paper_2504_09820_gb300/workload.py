@@ -232,8 +232,8 @@ def generate_rb(spec):
     tx = rng.integers(0, spec.qam, size=(n, spec.K)).astype(np.uint8)
     x = qam_modulate(tx, spec.qam)
     rb = (np.arange(n) // spec.res_per_rb).astype(np.int32)
-    Hn = H.transpose(0, 2, 1).astype(np.complex128)  # (n_rb, N, K)
-    yc = np.einsum("snk,sk->sn", Hn[rb], x)
+    xb = x.reshape(spec.n_rb, spec.res_per_rb, spec.K)
+    yc = np.matmul(xb, H.astype(np.complex128)).reshape(n, spec.N)   # y_s = H_rb x_s, block by block
     sigma2 = float(snr_to_sigma2(spec.snr_db))
     sn = np.sqrt(sigma2 / 2.0)
     yc = yc + (rng.standard_normal((n, spec.N)) + 1j * rng.standard_normal((n, spec.N))) * sn
