@@ -180,7 +180,10 @@ FPCG_API int fpbjcg_detect(const void* H, const void* y, const double* sigma2, c
  *   b      [batch][K] same element type
  *   block_L  0 = FP-CG (Algorithm 2), else FP-BJ-CG (Algorithm 3) with this L
  * prec->gram is ignored; everything else as fpcg_detect.  rel_res, res_hist
- * and status are nullable.
+ * and status are nullable.  Runs on the tensor-core solver (one warp per
+ * system, A rounded to the matvec format in shared memory) when fpcg_path
+ * would pick the tensor-core kernel for (K, block_L, prec) and A, b are
+ * 16-byte aligned, else on the SIMT kernel.
  */
 FPCG_API int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t batch, int32_t iters,
                     int32_t block_L, const fpcg_precision* prec,
@@ -242,6 +245,25 @@ FPCG_API int fpcg_detect_shared(const void* A, const void* H, const void* y, con
                                 int64_t n_rhs, int32_t iters, int32_t block_L, const fpcg_precision* prec,
                                 void* x_hat, uint8_t* sym_idx, double* rel_res, const uint8_t* tx_idx,
                                 unsigned long long* bit_errors, int32_t* status, void* stream);
+
+/*
+ * fpcg_detect_grouped -- fpcg_detect_shared for received vectors stored grouped
+ * by channel: the vectors of group g are y[group_start[g] .. group_start[g+1]).
+ * Same computation and arguments otherwise (A from fpcg_gram, H per group,
+ * outputs per received vector), with
+ *   group_start  device [n_groups + 1] int64, non-decreasing, group_start[0] = 0,
+ *                group_start[n_groups] = n_rhs (not checked on the device)
+ * Runs on the tensor-core solver when K in {16, 32, 64, 128}, block_L in {0,
+ * 4, 8, 16}, mv in {BF16, FP16}, w = resid = FP32 and A is 16-byte aligned:
+ * the eight warps of a CTA share one group's A (rounded to the matvec format)
+ * and inverted diagonal blocks, and each warp detects one received vector at a
+ * time.  Otherwise the SIMT kernel (one CTA per received vector).
+ */
+FPCG_API int fpcg_detect_grouped(const void* A, const void* H, const void* y, const int64_t* group_start,
+                                 const int32_t* qam_order, int32_t n_rx, int32_t k, int64_t n_groups,
+                                 int64_t n_rhs, int32_t iters, int32_t block_L, const fpcg_precision* prec,
+                                 void* x_hat, uint8_t* sym_idx, double* rel_res, const uint8_t* tx_idx,
+                                 unsigned long long* bit_errors, int32_t* status, void* stream);
 
 /*
  * ---- Uneven batches: a plan over systems of different (N, K) ----

@@ -1,0 +1,469 @@
+// The CG warp: one warp detects one system from a shared-memory slot holding
+// A + sigma^2 I in the matvec format, the fp32 diagonal blocks M_d and b.
+// Used by the fused tensor-core detector (slots filled from the Gram
+// accumulator) and by the solver for given Gram matrices (slots filled from
+// global memory).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "detect_tc.cuh"
+#include "tc.cuh"
+#include "tc_pipeline.cuh"
+
+namespace fpcg {
+namespace {
+
+// ---- one system slot in shared memory -----------------------------------------
+struct Slot {
+  uint8_t* A16;     // [2K][K] 16-bit, row r at r*2K bytes, 16-byte chunk c at (c ^ swz(r))
+  float2* Md;       // diagonal blocks of A (fp32), inverted in place (md_*_stride layout)
+  float2* b;        // [K]
+  float2* W;        // [K] matvec result, redistributed
+  uint32_t* Pk;     // [3K] packed B fragments
+};
+
+__device__ inline Slot slot_carve(uint8_t* base, int K, int L) {
+  Slot s;
+  uint8_t* p = base;
+  s.A16 = p;
+  p += 4 * K * K;
+  s.Md = (float2*)p;
+  p += sizeof(float2) * (L > 0 ? (K / L) * md_block_stride(L) : 2);
+  s.b = (float2*)p;
+  p += sizeof(float2) * K;
+  s.W = (float2*)p;
+  p += sizeof(float2) * K;
+  s.Pk = (uint32_t*)p;
+  return s;
+}
+
+// 16-byte chunk swizzle of row r of a [2K][K] 16-bit matrix (K/8 chunks per
+// row): eight consecutive rows at one chunk hit eight different 16-byte bank
+// groups of a 128-byte window.
+template <int K>
+__device__ __forceinline__ uint32_t a16_offset(int r, int chunk) {
+  constexpr int CPR = K / 8;                           // chunks per row: 16, 8, 4, 2
+  constexpr int SH = CPR >= 8 ? 0 : CPR == 4 ? 1 : 2;  // rows per swizzle step
+  constexpr int MASK = (CPR >= 8 ? 8 : CPR) - 1;        // within one 128-byte bank window
+  return (uint32_t)(r * (2 * K) + ((chunk ^ ((r >> SH) & MASK)) << 4));
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <bool BF>
+__device__ __forceinline__ uint32_t pk2(float a, float b) {
+  return tcp::pack2(a, b, BF ? 1 : 0);
+}
+
+template <bool BF>
+__device__ __forceinline__ float round16(float v) {
+  if (BF) return __bfloat162float(__float2bfloat16_rn(v));
+  return __half2float(__float2half_rn(v));
+}
+
+template <bool BF>
+__device__ __forceinline__ void mma16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  if (BF) tc::mma_m16n8k16_bf16(d, a, b0, b1);
+  else tc::mma_m16n8k16_f16(d, a, b0, b1);
+}
+
+// In-place Gauss-Jordan inversion, no pivoting, of the K/L diagonal blocks
+// (Hermitian positive definite, L x L) of M_d by one warp: lane l owns columns
+// c = c0 + l + 32e (e < NE, c < K) of their blocks.  Per pivot pv, with
+// d = 1 / M[pv][pv] and f = column pv of the block:
+//   M[pv][j] <- M[pv][j] d,  M[i][j] <- M[i][j] - f_i M[pv][j] d   (j != pv)
+//   M[pv][pv] <- d,          M[i][pv] <- -f_i d                    (j == pv)
+// (one branch-free update for both cases).  Returns nonzero (on every lane) if
+// a pivot was not positive.
+template <int K, int LT, int NE>
+__device__ __forceinline__ int gj_blocks(float2* Md, int lane, int c0 = 0) {
+  constexpr int LD = md_row_stride(LT), BS = md_block_stride(LT);
+  float2* M[NE];
+  int j[NE];
+  bool on[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int c = c0 + lane + 32 * e;
+    on[e] = c < K;
+    M[e] = Md + (on[e] ? (c / LT) * BS : 0);
+    j[e] = c % LT;
+  }
+  int fail = 0;
+#pragma unroll 1
+  for (int pv = 0; pv < LT; ++pv) {
+    float2 dinv[NE], mj[NE], f[NE][LT];
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      const float2 piv = M[e][pv * LD + pv];
+      if (on[e] && !(piv.x > 0.f && isfinite(piv.x))) fail = 1;
+      const float rd = 1.f / (piv.x * piv.x + piv.y * piv.y);
+      dinv[e] = make_float2(piv.x * rd, -piv.y * rd);
+#pragma unroll
+      for (int i = 0; i < LT; ++i) f[e][i] = M[e][i * LD + pv];
+      mj[e] = M[e][pv * LD + j[e]];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      if (!on[e]) continue;
+      const bool own = j[e] == pv;
+      const float2 prow = cmul(mj[e], dinv[e]);
+      const float2 s = own ? dinv[e] : prow;
+#pragma unroll
+      for (int i = 0; i < LT; ++i) {  // row pv is rewritten below
+        const float2 a = cmul(f[e][i], s);
+        const float2 v = M[e][i * LD + j[e]];
+        M[e][i * LD + j[e]] = own ? make_float2(-a.x, -a.y) : make_float2(v.x - a.x, v.y - a.y);
+      }
+      M[e][pv * LD + j[e]] = s;
+    }
+    __syncwarp();
+  }
+  return __any_sync(0xffffffffu, fail);
+}
+
+// Rounding of an inner product to u_IP when it is not fp32 (out of line: the
+// format switch is rare and would otherwise be inlined at every call).
+__device__ __noinline__ float round_ip(float v, int fmt) { return round_to(v, fmt); }
+
+// ---- the CG warp -------------------------------------------------------------------
+// Code size matters here: the CG warps share each SM sub-partition's
+// instruction cache with the drain, converter, producer and MMA warps, and code
+// that runs once per system is fetched cold.  So every step exists once in the
+// code: the solves of all passes and the refinement residuals run in one loop,
+// whose trips are either A p (a CG iteration) or b - A x (a residual).
+template <int K, bool BF, int LT>
+struct CgWarp {
+  static constexpr int KT = K / 16;          // k-tiles (16 users)
+  static constexpr int MT = K / 16;          // m-tiles of Re A (and of Im A)
+  static constexpr int E = K >= 32 ? K / 32 : 1;  // vector rows per lane
+  static constexpr int NCOL = 6;             // B columns (re, im) x (hi, mid, lo)
+  const DetectTcParams& P;
+  Slot S;
+  int lane, g, t;
+  int ipf, alpha_num, iters, refine_steps, refine_iters;  // parameters kept in registers
+
+  __device__ CgWarp(const DetectTcParams& P_, Slot S_, int lane_) : P(P_), S(S_), lane(lane_) {
+    g = lane >> 2;
+    t = lane & 3;
+    ipf = P_.ip;
+    alpha_num = P_.alpha_num;
+    iters = P_.iters;
+    refine_steps = P_.refine_steps;
+    refine_iters = P_.refine_iters;
+  }
+
+  __device__ __forceinline__ bool vact() const { return lane < K; }
+  __device__ __forceinline__ float rip(float v) { return ipf == F32 ? v : round_ip(v, ipf); }
+
+  // Re sum conj(a) b and Re sum conj(c) d over the warp's rows.
+  __device__ __forceinline__ void dot2(const float2 (&a)[E], const float2 (&b)[E], const float2 (&c)[E],
+                                       const float2 (&d)[E], float& s1, float& s2) {
+    s1 = 0.f;
+    s2 = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      s1 += a[e].x * b[e].x + a[e].y * b[e].y;
+      s2 += c[e].x * d[e].x + c[e].y * d[e].y;
+    }
+    if (!vact()) s1 = s2 = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+  }
+
+  // Store vector v (rows lane + 32e) as m16n8k16 B fragments: word
+  // ((kt*NCOL + col)*4 + tt)*2 + h holds rows 16kt + 8h + 2tt, +1 of column
+  // col.  Columns (re, im) of v rounded to the 16-bit format, then of the two
+  // remainders when `split` (three pieces carry all 24 bits of an fp32 value;
+  // zeros otherwise).
+  __device__ __forceinline__ void pack(const float2 (&v)[E], bool split) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const float nx = __shfl_down_sync(0xffffffffu, v[e].x, 1);
+      const float ny = __shfl_down_sync(0xffffffffu, v[e].y, 1);
+      const int rl = lane + 32 * e;
+      if (vact() && (rl & 1) == 0) {
+        const int kt = rl >> 4, j = rl & 15, tt = (j & 7) >> 1, h = j >> 3;
+        uint32_t* w = S.Pk + (kt * NCOL * 4 + tt) * 2 + h;
+        float a[4] = {v[e].x, nx, v[e].y, ny};
+#pragma unroll
+        for (int s3 = 0; s3 < 3; ++s3) {
+          float hh[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            hh[u] = round16<BF>(a[u]);
+            a[u] = split ? a[u] - hh[u] : 0.f;  // exact remainder of the rounding
+          }
+          w[(2 * s3) * 8] = pk2<BF>(hh[0], hh[1]);
+          w[(2 * s3 + 1) * 8] = pk2<BF>(hh[2], hh[3]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+
+  // W = A v (res = false) or W = b - A v (res = true: the three column pairs
+  // of v are summed), one m-tile (16 rows of Re A and of Im A) at a time; lane
+  // (g, t) holds C rows g, g+8 and columns 2t, 2t+1.  Then w = W in the vector
+  // layout.
+  __device__ __forceinline__ void apply(bool res, float2 (&w)[E]) {
+    uint32_t b0[KT], b1[KT];
+#pragma unroll
+    for (int kt = 0; kt < KT; ++kt) {
+      b0[kt] = b1[kt] = 0u;
+      if (g < NCOL) {
+        const uint2 pw = *reinterpret_cast<const uint2*>(S.Pk + ((kt * NCOL + g) * 4 + t) * 2);
+        b0[kt] = pw.x;
+        b1[kt] = pw.y;
+      }
+    }
+    const uint32_t abase = tc::smem_u32(S.A16);
+    const int lr = lane & 15, lc = lane >> 4;
+#pragma unroll 1  // unrolled runs slower in the full kernel (code size)
+    for (int mt = 0; mt < MT; ++mt) {
+      float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
+      float cr2[4] = {0.f, 0.f, 0.f, 0.f}, ci2[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) {  // two accumulator chains per part (even / odd kt)
+        uint32_t ar[4], ai[4];
+        tc::ldmatrix_x4(ar, abase + a16_offset<K>(16 * mt + lr, 2 * kt + lc));
+        tc::ldmatrix_x4(ai, abase + a16_offset<K>(K + 16 * mt + lr, 2 * kt + lc));
+        if (kt & 1) {
+          mma16<BF>(cr2, ar, b0[kt], b1[kt]);
+          mma16<BF>(ci2, ai, b0[kt], b1[kt]);
+        } else {
+          mma16<BF>(cr, ar, b0[kt], b1[kt]);
+          mma16<BF>(ci, ai, b0[kt], b1[kt]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        cr[q] += cr2[q];
+        ci[q] += ci2[q];
+      }
+      if (res) {  // add the mid (t = 1) and lo (t = 2) column products into t = 0
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float r1 = __shfl_down_sync(0xffffffffu, cr[q], 1);
+          const float r2 = __shfl_down_sync(0xffffffffu, cr[q], 2);
+          const float i1 = __shfl_down_sync(0xffffffffu, ci[q], 1);
+          const float i2 = __shfl_down_sync(0xffffffffu, ci[q], 2);
+          cr[q] += r1 + r2;
+          ci[q] += i1 + i2;
+        }
+      }
+      if (t == 0) {
+        // rows 16mt+g / +8: (Re A vr - Im A vi) + i (Re A vi + Im A vr)
+        float2 w0 = make_float2(cr[0] - ci[1], cr[1] + ci[0]);
+        float2 w8 = make_float2(cr[2] - ci[3], cr[3] + ci[2]);
+        if (res) {
+          const float2 bb0 = S.b[16 * mt + g], bb8 = S.b[16 * mt + g + 8];
+          w0 = make_float2(bb0.x - w0.x, bb0.y - w0.y);
+          w8 = make_float2(bb8.x - w8.x, bb8.y - w8.y);
+        }
+        S.W[16 * mt + g] = w0;
+        S.W[16 * mt + g + 8] = w8;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; ++e) w[e] = vact() ? S.W[lane + 32 * e] : make_float2(0.f, 0.f);
+    __syncwarp();
+  }
+
+  // z = M_d r (z = r without a preconditioner): r is staged in W and each
+  // lane reads its block's L entries of it (broadcast) and its row of M_d.
+  __device__ __forceinline__ void precond(const float2 (&r)[E], float2 (&z)[E]) {
+    if constexpr (LT == 0) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) z[e] = r[e];
+    } else {
+      constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (vact()) S.W[lane + 32 * e] = r[e];
+      __syncwarp();
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = vact() ? lane + 32 * e : 0;
+        const float4* rb = reinterpret_cast<const float4*>(S.W + (k & ~(LT - 1)));
+        const float4* mr = reinterpret_cast<const float4*>(S.Md + (k / LT) * MBS + (k % LT) * MLD);
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < LT / 2; ++q) {  // entries 2q, 2q+1
+          const float4 m = mr[q], v = rb[q];
+          a0.x = fmaf(m.x, v.x, fmaf(-m.y, v.y, a0.x));
+          a0.y = fmaf(m.x, v.y, fmaf(m.y, v.x, a0.y));
+          a1.x = fmaf(m.z, v.z, fmaf(-m.w, v.w, a1.x));
+          a1.y = fmaf(m.z, v.w, fmaf(m.w, v.z, a1.y));
+        }
+        z[e] = vact() ? make_float2(a0.x + a1.x, a0.y + a1.y) : make_float2(0.f, 0.f);
+      }
+      __syncwarp();
+    }
+  }
+
+  // The whole detection of one system from its slot.  Pass 0 runs Algorithm 2
+  // (LT == 0) or 3 on b from x0 = 0; each refinement pass runs it again on the
+  // residual b - A x and adds the correction; the last trip is the final
+  // residual.
+  // Block-Jacobi setup (eq. pre_BJ) on the slot's M_d: FPCG_ST_BJ_FAIL (8) and
+  // M_d = I if a diagonal block was not positive definite, else 0.
+  __device__ int bj_setup() {
+    if constexpr (LT > 0) {
+      constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
+      int fail;
+      if constexpr (E <= 2) {
+        fail = gj_blocks<K, LT, E>(S.Md, lane);
+      } else {  // columns in rounds of 64 (a block never straddles two)
+        fail = 0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < K; c0 += 64) fail |= gj_blocks<K, LT, 2>(S.Md, lane, c0);
+      }
+      if (fail) {
+        for (int i = lane; i < K * LT; i += 32)
+          S.Md[(i / LT / LT) * MBS + ((i / LT) % LT) * MLD + i % LT] =
+              make_float2((i / LT) % LT == i % LT ? 1.f : 0.f, 0.f);
+        __syncwarp();
+        return 8;
+      }
+    }
+    return 0;
+  }
+
+  // st0: status bits already known for this system (from bj_setup).
+  __device__ void detect(int64_t sys, bool valid, int st0) {
+    int st = st0;
+    // per-system inputs of the output stage, loaded now (their latency hides under the solve)
+    const int64_t base = sys * (int64_t)K;
+    const bool want_sym = valid && (P.sym || P.bit_errors);
+    const int M = want_sym ? P.qam[sys] : 0;
+    int txv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) txv[e] = (want_sym && P.tx && vact()) ? P.tx[base + lane + 32 * e] : 0;
+    float* hist = (P.res_hist && valid) ? P.res_hist + sys * (int64_t)(iters + 1) : nullptr;
+
+    float2 x[E], d[E], r[E], p[E], z[E], w[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      x[e] = d[e] = p[e] = make_float2(0.f, 0.f);
+      r[e] = vact() ? S.b[lane + 32 * e] : make_float2(0.f, 0.f);
+    }
+    int pass = 0, it = 0, iters_p = iters, mask = ~0;
+    float rho = 0.f, rho_prev = 1.f, rr = 0.f;
+    bool fresh = true;  // r is a new right-hand side: start a pass
+#pragma unroll 1
+    while (true) {
+      if (!fresh) {
+        const bool rt = it >= iters_p;  // this trip: residual, else a CG iteration
+        if (rt) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) x[e] = make_float2(x[e].x + d[e].x, x[e].y + d[e].y);
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) w[e] = rt ? x[e] : p[e];
+        pack(w, rt);
+        apply(rt, w);
+        if (rt) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) r[e] = w[e];  // r = b - A x
+          if (pass >= refine_steps) break;
+          ++pass;
+          iters_p = refine_iters;
+          it = 0;
+          mask = 1;  // a refinement pass reports breakdown only
+          hist = nullptr;
+#pragma unroll
+          for (int e = 0; e < E; ++e) d[e] = make_float2(0.f, 0.f);
+          fresh = true;
+        } else {
+          float phi, rp;
+          dot2(p, w, r, p, phi, rp);
+          phi = rip(phi);
+          rho_prev = (LT > 0 && alpha_num == 0) ? rip(rp) : rho;
+          int bad = 0;
+          if (rho_prev == 0.f) bad = 2;
+          else if (!(phi > 0.f) || !isfinite(phi) || !isfinite(rho_prev)) bad = 1;
+          if (bad) {  // the pass stops here; the history repeats its last value
+            st |= bad & mask;
+            if (hist && lane == 0)
+              for (int k = it + 1; k <= iters_p; ++k) hist[k] = hist[it];
+            it = iters_p;
+            continue;
+          }
+          const float alpha = rho_prev / phi;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            d[e] = make_float2(fmaf(alpha, p[e].x, d[e].x), fmaf(alpha, p[e].y, d[e].y));
+            r[e] = make_float2(fmaf(-alpha, w[e].x, r[e].x), fmaf(-alpha, w[e].y, r[e].y));
+          }
+          ++it;
+        }
+      }
+      // z = M_d r, rho = r^H z, and the next direction
+      precond(r, z);
+      float rz;
+      dot2(r, z, r, r, rz, rr);
+      const float rho_new = rip(rz);
+      const float beta = fresh ? 0.f : rho_new / rho_prev;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        p[e] = fresh ? z[e] : make_float2(fmaf(beta, p[e].x, z[e].x), fmaf(beta, p[e].y, z[e].y));
+      rho = rho_new;
+      if (hist && lane == 0) hist[it] = sqrtf(rr);
+      fresh = false;
+    }
+
+    if (!valid) return;
+    float nr = 0.f, nb = 0.f;
+    int nonfinite = 0;
+    unsigned errs = 0;
+    const int m = qam_sqrt(M);
+    const float sc = m ? sqrtf((float)(2 * (M - 1) / 3)) : 0.f;  // 2(M-1)/3 is an integer here
+    const int nb2 = m ? qam_bits_axis(m) : 0;
+    if (vact()) {
+#pragma unroll  // x, r, txv stay in registers only with static indices
+      for (int e = 0; e < E; ++e) {
+        const float2 bv = S.b[lane + 32 * e];
+        nr += r[e].x * r[e].x + r[e].y * r[e].y;
+        nb += bv.x * bv.x + bv.y * bv.y;
+        const int k = lane + 32 * e;
+        if (!(isfinite(x[e].x) && isfinite(x[e].y))) nonfinite = 1;
+        P.x_hat[base + k] = x[e];
+        if (want_sym) {
+          int lab = 0;
+          if (m) lab = (gray(axis_level<float>(x[e].x, m, sc)) << nb2) | gray(axis_level<float>(x[e].y, m, sc));
+          if (P.sym) P.sym[base + k] = (uint8_t)lab;
+          if (P.tx && m) errs += __popc((unsigned)(lab ^ txv[e]));
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nr += __shfl_xor_sync(0xffffffffu, nr, o);
+      nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    }
+    nonfinite = __any_sync(0xffffffffu, nonfinite);
+    if (P.bit_errors && P.tx) {
+      errs = __reduce_add_sync(0xffffffffu, errs);
+      if (lane == 0 && errs) atomicAdd(P.bit_errors, (unsigned long long)errs);
+    }
+    if (lane == 0) {
+      if (P.rel_res) P.rel_res[sys] = nb > 0.f ? (double)sqrtf(nr / nb) : 0.0;
+      if (nonfinite) st |= 4;
+      if (want_sym && m == 0) st |= 16;
+      if (P.status) P.status[sys] = st;
+    }
+  }
+};
+
+}  // namespace
+}  // namespace fpcg

@@ -277,7 +277,18 @@ __device__ void load_gram(const SimtParams& P, const Smem<T>& S, int64_t sys) {
 template <typename T>
 __device__ bool load_shared(const SimtParams& P, const Smem<T>& S, int64_t sys) {
   const int K = P.K, N = P.N, AS = K + 1;
-  const int64_t g = P.a_map[sys];
+  int64_t g;
+  if (P.a_map) {
+    g = P.a_map[sys];
+  } else {  // largest g with group_start[g] <= sys
+    int64_t lo = 0, hi = P.n_shared;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) / 2;
+      if (P.group_start[mid] <= sys) lo = mid;
+      else hi = mid;
+    }
+    g = lo;
+  }
   if (g < 0 || g >= P.n_shared) return false;
   const cplx<T>* Ag = (const cplx<T>*)P.Ain + (size_t)g * K * K;
   for (int idx = threadIdx.x; idx < K * K; idx += NT) S.A[(idx / K) * AS + idx % K] = Ag[idx];
@@ -654,7 +665,7 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
   const int K = P.K;
   int st = 0;
 
-  if (P.Ain && P.a_map) {
+  if (P.Ain && (P.a_map || P.group_start)) {
     if (!load_shared(P, S, sys)) {  // index out of range: x = 0, labels 0, status
       cplx<T>* xo = (cplx<T>*)P.x_hat + (size_t)sys * K;
       for (int k = threadIdx.x; k < K; k += NT) {

@@ -15,6 +15,7 @@ struct SimtParams {
   const void* Ain;          // [batch][K][K] given Gram (fpcg_solve_gram) or null
   const void* bin;          // [batch][K] given right-hand side
   const int32_t* a_map;     // shared-Gram mode (with Ain, H, y): system i uses A and H number a_map[i]
+  const int64_t* group_start;  //   or, grouped: the systems of group g are [group_start[g], group_start[g+1])
   int64_t n_shared;         //   number of shared Gram matrices (bound of a_map)
   int N, K, iters, L, refine_steps, refine_iters, alpha_num, gram, ip, resid_fp64;
   int64_t batch;

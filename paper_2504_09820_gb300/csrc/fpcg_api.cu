@@ -9,6 +9,7 @@
 #include "detect_simt.cuh"
 #include "gram_tc.cuh"
 #include "detect_tc.cuh"
+#include "solve_tc.cuh"
 
 namespace {
 
@@ -65,6 +66,28 @@ int device_sms(int* sms) {
   return FPCG_OK;
 }
 
+// The CG warp's settings and outputs (shared by the fused detector and the solver).
+void cg_params(fpcg::DetectTcParams& T, const int32_t* qam_order, int32_t iters, int32_t block_L,
+               const fpcg_precision* prec, int refine_iters, void* x_hat, uint8_t* sym_idx, double* rel_res,
+               float* res_hist, const uint8_t* tx_idx, unsigned long long* bit_errors, int32_t* status) {
+  T.qam = qam_order;
+  T.iters = iters;
+  T.L = block_L;
+  T.refine_steps = prec->refine_steps;
+  T.refine_iters = refine_iters;
+  T.alpha_num = prec->alpha_num;
+  T.ip = prec->ip;
+  T.x_hat = (float2*)x_hat;
+  T.sym = sym_idx;
+  T.rel_res = rel_res;
+  T.res_hist = res_hist;
+  T.tx = tx_idx;
+  T.bit_errors = bit_errors;
+  T.status = status;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 }  // namespace
 
 namespace fpcg {
@@ -92,9 +115,30 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
     if (e != cudaSuccess) return cuda_fail(e);
   }
   if (batch == 0) return FPCG_OK;
-  const bool tc_possible = !Ain && tc_capable(k, block_L, prec) && fpcg::tma_pipe_ok(H, y, n_rx);
+  const bool tc_possible = tc_capable(k, block_L, prec) &&
+                           (Ain ? aligned16(Ain) && aligned16(bin) : fpcg::tma_pipe_ok(H, y, n_rx));
   if (path == FPCG_PATH_TENSOR_CORE && !tc_possible) return FPCG_ENOTSUP;
   const bool tc_ok = tc_possible && (path == FPCG_PATH_TENSOR_CORE || (path < 0 && !force_simt()));
+  if (tc_ok && Ain) {  // given Gram matrices: the tensor-core solver
+    int sms = 0;
+    rc = device_sms(&sms);
+    if (rc) return rc;
+    rc = check_device_smem(fpcg::solve_tc_smem_bytes(k, block_L));
+    if (rc) return rc;
+    fpcg::SolveTcParams T;
+    memset(&T, 0, sizeof(T));
+    cg_params(T.D, qam_order, iters, block_L, prec, refine_iters, x_hat, sym_idx, rel_res, res_hist, tx_idx,
+              bit_errors, status);
+    T.A = (const float2*)Ain;
+    T.b = (const float2*)bin;
+    T.n = batch;
+    T.n_groups = batch;
+    T.N = k;
+    T.K = k;
+    T.gram = prec->gram;
+    cudaError_t e = fpcg::launch_solve_tc(T, sms, prec->mv == FPCG_BF16, s);
+    return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+  }
   if (tc_ok) {
     int sms = 0;
     rc = device_sms(&sms);
@@ -106,20 +150,8 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
     if (!fpcg::make_pipe(&T.pipe, (const float2*)H, (const float2*)y, n_rx, k, batch, prec->gram == FPCG_BF16))
       return FPCG_ENOTSUP;
     T.sigma2 = sigma2;
-    T.qam = qam_order;
-    T.iters = iters;
-    T.L = block_L;
-    T.refine_steps = prec->refine_steps;
-    T.refine_iters = refine_iters;
-    T.alpha_num = prec->alpha_num;
-    T.ip = prec->ip;
-    T.x_hat = (float2*)x_hat;
-    T.sym = sym_idx;
-    T.rel_res = rel_res;
-    T.res_hist = res_hist;
-    T.tx = tx_idx;
-    T.bit_errors = bit_errors;
-    T.status = status;
+    cg_params(T, qam_order, iters, block_L, prec, refine_iters, x_hat, sym_idx, rel_res, res_hist, tx_idx,
+              bit_errors, status);
     cudaError_t e = fpcg::launch_detect_tc(T, sms, prec->mv == FPCG_BF16, s);
     return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
   }
@@ -239,6 +271,82 @@ int fpcg_detect_shared(const void* A, const void* H, const void* y, const int32_
   P.L = block_L;
   P.refine_steps = prec->refine_steps;
   P.refine_iters = prec->refine_iters < 0 ? iters : prec->refine_iters;
+  P.alpha_num = prec->alpha_num;
+  P.gram = prec->gram;
+  P.ip = prec->ip;
+  P.resid_fp64 = prec->resid == FPCG_FP64;
+  P.batch = n_rhs;
+  P.x_hat = x_hat;
+  P.sym = sym_idx;
+  P.rel_res = rel_res;
+  P.tx = tx_idx;
+  P.bit_errors = bit_errors;
+  P.status = status;
+  cudaError_t e = fpcg::launch_detect_simt(P, fp64, fp64 ? FPCG_FP64 : prec->mv, s);
+  return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+}
+
+int fpcg_detect_grouped(const void* A, const void* H, const void* y, const int64_t* group_start,
+                        const int32_t* qam_order, int32_t n_rx, int32_t k, int64_t n_groups, int64_t n_rhs,
+                        int32_t iters, int32_t block_L, const fpcg_precision* prec, void* x_hat,
+                        uint8_t* sym_idx, double* rel_res, const uint8_t* tx_idx,
+                        unsigned long long* bit_errors, int32_t* status, void* stream) {
+  int rc = check_prec(prec);
+  if (rc) return rc;
+  if (!A || !H || !y || !group_start || !x_hat) return FPCG_EINVAL;
+  if (k < 1 || k > 128 || n_rx < k || n_rx > 65536 || n_groups < 1 || n_rhs < 0 || iters < 0) return FPCG_EINVAL;
+  if (block_L < 0 || block_L > 32 || (block_L > 0 && k % block_L)) return FPCG_EINVAL;
+  if ((sym_idx || bit_errors) && !qam_order) return FPCG_EINVAL;
+  if ((tx_idx != nullptr) != (bit_errors != nullptr)) return FPCG_EINVAL;
+  const int fp64 = prec->w == FPCG_FP64;
+  if (fp64 && k > 64) return FPCG_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (bit_errors) {
+    cudaError_t e = cudaMemsetAsync(bit_errors, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (n_rhs == 0) return FPCG_OK;
+  const int refine_iters = prec->refine_iters < 0 ? iters : prec->refine_iters;
+  const bool tc_prec = prec->w == FPCG_FP32 && prec->resid == FPCG_FP32 &&
+                       (prec->mv == FPCG_BF16 || prec->mv == FPCG_FP16);
+  if (!force_simt() && tc_prec && fpcg::solve_grouped_supported(k, block_L) && aligned16(A)) {
+    int sms = 0;
+    rc = device_sms(&sms);
+    if (rc) return rc;
+    rc = check_device_smem(fpcg::solve_grouped_smem_bytes(k, block_L));
+    if (rc) return rc;
+    fpcg::SolveTcParams T;
+    memset(&T, 0, sizeof(T));
+    cg_params(T.D, qam_order, iters, block_L, prec, refine_iters, x_hat, sym_idx, rel_res, nullptr, tx_idx,
+              bit_errors, status);
+    T.A = (const float2*)A;
+    T.H = (const float2*)H;
+    T.y = (const float2*)y;
+    T.group_start = group_start;
+    T.n = n_rhs;
+    T.n_groups = n_groups;
+    T.N = n_rx;
+    T.K = k;
+    T.gram = prec->gram;
+    cudaError_t e = fpcg::launch_solve_grouped(T, sms, prec->mv == FPCG_BF16, s);
+    return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+  }
+  rc = check_device_smem(fpcg::simt_smem_bytes(fp64, k, block_L, prec->mv));
+  if (rc) return rc;
+  fpcg::SimtParams P;
+  memset(&P, 0, sizeof(P));
+  P.H = (const float2*)H;
+  P.y = (const float2*)y;
+  P.qam = qam_order;
+  P.Ain = A;
+  P.group_start = group_start;
+  P.n_shared = n_groups;
+  P.N = n_rx;
+  P.K = k;
+  P.iters = iters;
+  P.L = block_L;
+  P.refine_steps = prec->refine_steps;
+  P.refine_iters = refine_iters;
   P.alpha_num = prec->alpha_num;
   P.gram = prec->gram;
   P.ip = prec->ip;

@@ -1,0 +1,299 @@
+#pragma once
+// Tensor-core solver for given Gram matrices (kernel templates; instantiated
+// per K by solve_tc_k{16,32,64}.cu).  The CG of the fused detector without its
+// Gram pipeline: A + sigma^2 I comes from global memory (fpcg_gram's output, or
+// the caller's), every warp of a persistent CTA is an independent CG worker
+// with its own shared-memory slot, and systems that share a Gram matrix share
+// the slot's 16-bit A and inverted diagonal blocks.
+//
+// A warp takes a contiguous range of systems.  When the group changes it
+// rounds the group's fp32 A to the matvec format into the slot ([Re A; Im A],
+// swizzled), copies the diagonal blocks and inverts them (eq. pre_BJ).  The
+// right-hand side is either given or the system's matched filter
+// b = fl(H_g)^H fl(y_s) (eq. inversion; lanes over antennas, four rows of b at
+// a time, warp reductions).  Then CgWarp::detect: Algorithm 2 or 3,
+// refinement, slicing, outputs.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cg_warp.cuh"
+#include "common.cuh"
+#include "solve_tc.cuh"
+
+namespace fpcg {
+namespace {
+
+// Round the group's A into the slot: 16-bit [Re A; Im A] chunks of 8 columns,
+// and the fp32 diagonal blocks.
+template <int K, bool BF, int LT>
+__device__ void fill_slot_A(const float2* Ag, const Slot& S, int lane) {
+  constexpr int CPR = K / 8;
+  for (int idx = lane; idx < K * CPR; idx += 32) {
+    const int k = idx / CPR, c = idx % CPR;
+    const float4* src = reinterpret_cast<const float4*>(Ag + (size_t)k * K + 8 * c);
+    float2 a[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = __ldg(src + q);
+      a[2 * q] = make_float2(v.x, v.y);
+      a[2 * q + 1] = make_float2(v.z, v.w);
+    }
+    uint4 re, im;
+    re.x = pk2<BF>(a[0].x, a[1].x);
+    re.y = pk2<BF>(a[2].x, a[3].x);
+    re.z = pk2<BF>(a[4].x, a[5].x);
+    re.w = pk2<BF>(a[6].x, a[7].x);
+    im.x = pk2<BF>(a[0].y, a[1].y);
+    im.y = pk2<BF>(a[2].y, a[3].y);
+    im.z = pk2<BF>(a[4].y, a[5].y);
+    im.w = pk2<BF>(a[6].y, a[7].y);
+    *reinterpret_cast<uint4*>(S.A16 + a16_offset<K>(k, c)) = re;
+    *reinterpret_cast<uint4*>(S.A16 + a16_offset<K>(K + k, c)) = im;
+    if constexpr (LT > 0) {
+      constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
+      const int kb0 = (k / LT) * LT;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int l = 8 * c + m;
+        if (l >= kb0 && l < kb0 + LT) S.Md[(k / LT) * MBS + (k % LT) * MLD + (l - kb0)] = a[m];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// b = fl(H)^H fl(y) for one system into S.b (rounding of the Gram step).
+template <int K>
+__device__ void matched_filter(const float2* Hg, const float2* ys, int N, int gram, const Slot& S, int lane) {
+  for (int k0 = 0; k0 < K; k0 += 4) {
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int n = lane; n < N; n += 32) {
+      const float2 yy = ys[n];
+      const float yr = round_to(yy.x, gram), yi = round_to(yy.y, gram);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 h = Hg[(size_t)(k0 + q) * N + n];
+        const float hr = round_to(h.x, gram), hi = round_to(h.y, gram);
+        re[q] = fmaf(hr, yr, fmaf(hi, yi, re[q]));  // conj(h_k) y
+        im[q] = fmaf(hr, yi, fmaf(-hi, yr, im[q]));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        re[q] += __shfl_xor_sync(0xffffffffu, re[q], o);
+        im[q] += __shfl_xor_sync(0xffffffffu, im[q], o);
+      }
+    if (lane < 4) {
+      float r = re[0], i = im[0];
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+        if (lane == q) {
+          r = re[q];
+          i = im[q];
+        }
+      S.b[k0 + lane] = make_float2(r, i);
+    }
+  }
+  __syncwarp();
+}
+
+template <int K, bool BF, int LT>
+__global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_tc_kernel(const __grid_constant__ SolveTcParams P) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+  const Slot S = slot_carve(base + warp * tc_slot_bytes(K, LT), K, LT);
+  CgWarp<K, BF, LT> W(P.D, S, lane);
+  const int64_t tw = (int64_t)gridDim.x * kSolveWarps, gw = (int64_t)blockIdx.x * kSolveWarps + warp;
+  const int64_t chunk = (P.n + tw - 1) / tw;
+  const int64_t s0 = gw * chunk, s1 = min(P.n, s0 + chunk);
+  if (s0 >= s1) return;
+  // group of the first system: binary search in group_start
+  int64_t g = s0, g_end = s0 + 1;
+  if (P.group_start) {
+    int64_t lo = 0, hi = P.n_groups;  // largest g with start[g] <= s0
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) / 2;
+      if (P.group_start[mid] <= s0) lo = mid;
+      else hi = mid;
+    }
+    g = lo;
+    g_end = P.group_start[g + 1];
+  }
+  int64_t cur = -1;
+  int st_bj = 0;
+  for (int64_t s = s0; s < s1; ++s) {
+    if (P.group_start) {
+      while (s >= g_end && g + 1 < P.n_groups) {
+        ++g;
+        g_end = P.group_start[g + 1];
+      }
+    } else {
+      g = s;
+    }
+    if (g != cur) {
+      fill_slot_A<K, BF, LT>(P.A + (size_t)g * K * K, S, lane);
+      st_bj = W.bj_setup();
+      cur = g;
+    }
+    if (P.b) {
+      if (lane < K / 2) reinterpret_cast<float4*>(S.b)[lane] = __ldg(reinterpret_cast<const float4*>(P.b + (size_t)s * K) + lane);
+      __syncwarp();
+    } else {
+      matched_filter<K>(P.H + (size_t)g * K * P.N, P.y + (size_t)s * P.N, P.N, P.gram, S, lane);
+    }
+    W.detect(s, true, st_bj);
+    __syncwarp();
+  }
+}
+
+// Grouped mode: CTA c takes groups c, c + gridDim.x, ...; for each, all its
+// threads round the group's A into the shared slot, warps 0..K/32-1 invert the
+// diagonal blocks (one block column per lane), and the warps take the group's
+// received vectors round-robin: matched filter into their own b, then detect.
+template <int K, bool BF, int LT>
+__global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_grouped_kernel(const __grid_constant__ SolveTcParams P) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  constexpr int CPR = K / 8;
+  constexpr int NT = kSolveWarps * 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+  Slot S;
+  S.A16 = base;
+  S.Md = reinterpret_cast<float2*>(base + 4 * K * K);
+  uint8_t* scratch = base + 4 * K * K + md_bytes(K, LT);
+  uint8_t* mine = scratch + (size_t)warp * (16 * K + 12 * K);
+  S.b = reinterpret_cast<float2*>(mine);
+  S.W = reinterpret_cast<float2*>(mine + 8 * K);
+  S.Pk = reinterpret_cast<uint32_t*>(mine + 16 * K);
+  volatile int* flag = reinterpret_cast<volatile int*>(scratch + (size_t)kSolveWarps * (16 * K + 12 * K));
+  CgWarp<K, BF, LT> W(P.D, S, lane);
+  for (int64_t g = blockIdx.x; g < P.n_groups; g += gridDim.x) {
+    const int64_t s0 = P.group_start[g], s1 = P.group_start[g + 1];
+    if (s1 <= s0) continue;
+    __syncthreads();  // the previous group's vectors are done with the slot
+    const float2* Ag = P.A + (size_t)g * K * K;
+    for (int idx = threadIdx.x; idx < K * CPR; idx += NT) {  // A -> [Re A; Im A] 16-bit, diagonal blocks fp32
+      const int k = idx / CPR, c = idx % CPR;
+      const float4* src = reinterpret_cast<const float4*>(Ag + (size_t)k * K + 8 * c);
+      float2 a[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 v = __ldg(src + q);
+        a[2 * q] = make_float2(v.x, v.y);
+        a[2 * q + 1] = make_float2(v.z, v.w);
+      }
+      uint4 re, im;
+      re.x = pk2<BF>(a[0].x, a[1].x);
+      re.y = pk2<BF>(a[2].x, a[3].x);
+      re.z = pk2<BF>(a[4].x, a[5].x);
+      re.w = pk2<BF>(a[6].x, a[7].x);
+      im.x = pk2<BF>(a[0].y, a[1].y);
+      im.y = pk2<BF>(a[2].y, a[3].y);
+      im.z = pk2<BF>(a[4].y, a[5].y);
+      im.w = pk2<BF>(a[6].y, a[7].y);
+      *reinterpret_cast<uint4*>(S.A16 + a16_offset<K>(k, c)) = re;
+      *reinterpret_cast<uint4*>(S.A16 + a16_offset<K>(K + k, c)) = im;
+      if constexpr (LT > 0) {
+        constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
+        const int kb0 = (k / LT) * LT;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int l = 8 * c + m;
+          if (l >= kb0 && l < kb0 + LT) S.Md[(k / LT) * MBS + (k % LT) * MLD + (l - kb0)] = a[m];
+        }
+      }
+    }
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    int st0 = 0;
+    if constexpr (LT > 0) {  // block-Jacobi setup (eq. pre_BJ), 32 block columns per warp
+      constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
+      if (warp * 32 < K && gj_blocks<K, LT, 1>(S.Md, lane, warp * 32)) *flag = 1;
+      __syncthreads();
+      if (*flag) {  // a failed block: M_d = I for the group
+        for (int i = threadIdx.x; i < K * LT; i += NT)
+          S.Md[(i / LT / LT) * MBS + ((i / LT) % LT) * MLD + i % LT] =
+              make_float2((i / LT) % LT == i % LT ? 1.f : 0.f, 0.f);
+        st0 = 8;
+      }
+      __syncthreads();
+    }
+    for (int64_t s = s0 + warp; s < s1; s += kSolveWarps) {
+      matched_filter<K>(P.H + (size_t)g * K * P.N, P.y + (size_t)s * P.N, P.N, P.gram, S, lane);
+      W.detect(s, true, st0);
+      __syncwarp();
+    }
+  }
+}
+
+template <int K, bool BF, int LT>
+cudaError_t launch_g(const SolveTcParams& P, int num_sms, cudaStream_t stream) {
+  const size_t smem = solve_grouped_smem_bytes(K, LT);
+  cudaError_t e =
+      cudaFuncSetAttribute(solve_grouped_kernel<K, BF, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_grouped_kernel<K, BF, LT>, kSolveWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)num_sms * per_sm;
+  if (grid > P.n_groups) grid = P.n_groups;
+  if (grid <= 0) return cudaSuccess;
+  solve_grouped_kernel<K, BF, LT><<<(unsigned)grid, kSolveWarps * 32, smem, stream>>>(P);
+  return cudaGetLastError();
+}
+
+template <int K, bool BF, int LT>
+cudaError_t launch_s(const SolveTcParams& P, int num_sms, cudaStream_t stream) {
+  const size_t smem = solve_tc_smem_bytes(K, LT);
+  cudaError_t e =
+      cudaFuncSetAttribute(solve_tc_kernel<K, BF, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_tc_kernel<K, BF, LT>, kSolveWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)num_sms * per_sm;
+  const int64_t need = (P.n + kSolveWarps - 1) / kSolveWarps;
+  if (grid > need) grid = need;
+  if (grid <= 0) return cudaSuccess;
+  solve_tc_kernel<K, BF, LT><<<(unsigned)grid, kSolveWarps * 32, smem, stream>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <int K>
+cudaError_t launch_solve_grouped_k(const SolveTcParams& P, int num_sms, int mv_bf16, cudaStream_t stream) {
+  switch (P.D.L * 2 + (mv_bf16 ? 1 : 0)) {
+    case 0: return launch_g<K, false, 0>(P, num_sms, stream);
+    case 1: return launch_g<K, true, 0>(P, num_sms, stream);
+    case 8: return launch_g<K, false, 4>(P, num_sms, stream);
+    case 9: return launch_g<K, true, 4>(P, num_sms, stream);
+    case 16: return launch_g<K, false, 8>(P, num_sms, stream);
+    case 17: return launch_g<K, true, 8>(P, num_sms, stream);
+    case 32: return launch_g<K, false, 16>(P, num_sms, stream);
+    case 33: return launch_g<K, true, 16>(P, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int K>
+cudaError_t launch_solve_tc_k(const SolveTcParams& P, int num_sms, int mv_bf16, cudaStream_t stream) {
+  switch (P.D.L * 2 + (mv_bf16 ? 1 : 0)) {
+    case 0: return launch_s<K, false, 0>(P, num_sms, stream);
+    case 1: return launch_s<K, true, 0>(P, num_sms, stream);
+    case 8: return launch_s<K, false, 4>(P, num_sms, stream);
+    case 9: return launch_s<K, true, 4>(P, num_sms, stream);
+    case 16: return launch_s<K, false, 8>(P, num_sms, stream);
+    case 17: return launch_s<K, true, 8>(P, num_sms, stream);
+    case 32: return launch_s<K, false, 16>(P, num_sms, stream);
+    case 33: return launch_s<K, true, 16>(P, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fpcg

@@ -103,6 +103,9 @@ def lib():
         L.fpcg_detect_shared.argtypes = [_P, _P, _P, _P, _P, _I32, _I32, _I64, _I64, _I32, _I32,
                                          ctypes.POINTER(Precision), _P, _P, _P, _P, _P, _P, _P]
         L.fpcg_detect_shared.restype = ctypes.c_int
+        L.fpcg_detect_grouped.argtypes = [_P, _P, _P, _P, _P, _I32, _I32, _I64, _I64, _I32, _I32,
+                                          ctypes.POINTER(Precision), _P, _P, _P, _P, _P, _P, _P]
+        L.fpcg_detect_grouped.restype = ctypes.c_int
         L.fpcg_plan_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(ctypes.c_void_p)]
         L.fpcg_plan_create.restype = ctypes.c_int
         L.fpcg_plan_layout.argtypes = [_P, _P, _P, _P, _P, _P]
@@ -239,6 +242,23 @@ def fpcg_detect_shared(A, H, y, rb_index, qam_order, iters, block_L, prec, x_hat
                                     _ptr(rel_res, torch.float64, "rel_res"), _ptr(tx_idx, torch.uint8, "tx_idx"),
                                     _ptr(bit_errors, torch.int64, "bit_errors"), _ptr(status, torch.int32, "status"),
                                     _stream(stream)), "fpcg_detect_shared")
+
+
+def fpcg_detect_grouped(A, H, y, group_start, qam_order, iters, block_L, prec, x_hat, sym_idx=None,
+                        rel_res=None, tx_idx=None, bit_errors=None, status=None, stream=None):
+    """Marshal a call to fpcg_detect_grouped: A [n_groups][K][K] from fpcg_gram, H
+    [n_groups][K][N], y [n_rhs][N] grouped, group_start [n_groups + 1] int64 (device)."""
+    n_groups, K, N = H.shape
+    n_rhs = y.shape[0]
+    dt = _xdtype(prec)
+    _check(lib().fpcg_detect_grouped(_ptr(A, dt, "A"), _ptr(H, torch.complex64, "H"),
+                                     _ptr(y, torch.complex64, "y"), _ptr(group_start, torch.int64, "group_start"),
+                                     _ptr(qam_order, torch.int32, "qam_order"), int(N), int(K), int(n_groups),
+                                     int(n_rhs), int(iters), int(block_L or 0), ctypes.byref(prec),
+                                     _ptr(x_hat, dt, "x_hat"), _ptr(sym_idx, torch.uint8, "sym_idx"),
+                                     _ptr(rel_res, torch.float64, "rel_res"), _ptr(tx_idx, torch.uint8, "tx_idx"),
+                                     _ptr(bit_errors, torch.int64, "bit_errors"), _ptr(status, torch.int32, "status"),
+                                     _stream(stream)), "fpcg_detect_grouped")
 
 
 def detect(H, y, sigma2, qam_order, iters, prec, L=None, tx_idx=None, hist=False, stream=None):

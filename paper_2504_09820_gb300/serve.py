@@ -5,8 +5,8 @@ A request is one slot of one user group: 14 OFDM symbols x S subcarriers seen
 through one channel per 12-subcarrier resource block, so the 168 received
 vectors of a block share a Gram matrix.  On the device a request runs
   copies in -> fpcg_gram (one A + sigma^2 I per block, kept for the whole slot)
-  -> fpcg_detect_shared (every received vector against its block's A)
-  -> copies out
+  -> fpcg_detect_grouped (every received vector against its block's A; the
+     vectors are stored block by block) -> copies out
 on a stream of its own.  Requests that arrive while others run are admitted
 as soon as a stream and enough of the memory budget are free (continuous
 batching: their work overlaps on the GPU); the rest wait in arrival order.
@@ -78,6 +78,7 @@ class Request:
     H: torch.Tensor             # [n_rb][K][N] complex64
     y: torch.Tensor             # [n_re][N] complex64, resource-block-major
     rb: torch.Tensor            # [n_re] int32
+    start: torch.Tensor         # [n_rb + 1] int64: received vectors of block g are [start[g], start[g+1])
     sigma2: torch.Tensor        # [n_rb] float64
     qam: torch.Tensor           # [n_re] int32
     tx: torch.Tensor = None     # [n_re][K] uint8 (optional: bit errors)
@@ -100,7 +101,7 @@ class Request:
 def request_layout(n_rb, n_re, N, K):
     """(name, dtype, shape) of every device buffer of a request, in order."""
     return [("H", torch.complex64, (n_rb, K, N)), ("y", torch.complex64, (n_re, N)),
-            ("rb", torch.int32, (n_re,)), ("sigma2", torch.float64, (n_rb,)),
+            ("rb", torch.int32, (n_re,)), ("start", torch.int64, (n_rb + 1,)), ("sigma2", torch.float64, (n_rb,)),
             ("qam", torch.int32, (n_re,)), ("tx", torch.uint8, (n_re, K)),
             ("A", torch.complex64, (n_rb, K, K)), ("b", torch.complex64, (n_rb, K)),
             ("x", torch.complex64, (n_re, K)), ("sym", torch.uint8, (n_re, K)),
@@ -144,18 +145,18 @@ class Server:
     def _issue(self, req, stream, off):
         v = self._views(off, req)
         with torch.cuda.stream(stream):
-            for k in ("H", "y", "rb", "sigma2", "qam"):
+            for k in ("H", "y", "rb", "start", "sigma2", "qam"):
                 v[k].copy_(getattr(req, k), non_blocking=True)
             if req.tx is not None:
                 v["tx"].copy_(req.tx, non_blocking=True)
             zy = self.zero_y[:req.n_rb * req.N].view(req.n_rb, req.N)
             F.fpcg_gram(v["H"], zy, v["sigma2"], self.prec_kw["gram"], v["A"], v["b"], stream=stream)
             L = min(self.block_L, req.K) if self.block_L else 0
-            F.fpcg_detect_shared(v["A"], v["H"], v["y"], v["rb"], v["qam"], self.iters, L, self.prec, v["x"],
-                                 sym_idx=v["sym"], rel_res=v["rel"],
-                                 tx_idx=v["tx"] if req.tx is not None else None,
-                                 bit_errors=v["bits"] if req.tx is not None else None,
-                                 status=v["st"], stream=stream)
+            F.fpcg_detect_grouped(v["A"], v["H"], v["y"], v["start"], v["qam"], self.iters, L, self.prec, v["x"],
+                                  sym_idx=v["sym"], rel_res=v["rel"],
+                                  tx_idx=v["tx"] if req.tx is not None else None,
+                                  bit_errors=v["bits"] if req.tx is not None else None,
+                                  status=v["st"], stream=stream)
             for k in ("x", "sym", "rel", "st", "bits"):
                 req.out[k].copy_(v[k], non_blocking=True)
             ev = torch.cuda.Event()
@@ -228,8 +229,10 @@ def slot_request(rid, pinned, S, arrival):
     14 S received vectors of a pinned full-size slot (views, no copies)."""
     n_rb = math.ceil(S / SUBCARRIERS_PER_RB)
     n_re = SYMBOLS_PER_SLOT * S
+    per = SYMBOLS_PER_SLOT * SUBCARRIERS_PER_RB
+    start = torch.from_numpy(np.minimum(np.arange(n_rb + 1, dtype=np.int64) * per, n_re)).pin_memory()
     return Request(rid=rid, N=pinned["N"], K=pinned["K"], S=S, arrival=arrival, H=pinned["H"][:n_rb],
-                   y=pinned["y"][:n_re], rb=pinned["rb"][:n_re], sigma2=pinned["sigma2"][:n_rb],
+                   y=pinned["y"][:n_re], rb=pinned["rb"][:n_re], start=start, sigma2=pinned["sigma2"][:n_rb],
                    qam=pinned["qam"][:n_re], tx=pinned["tx"][:n_re])
 
 

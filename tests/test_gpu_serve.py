@@ -1,6 +1,6 @@
 """Serving loop on the GPU: requests admitted by memory budget and run
 concurrently give, for each request, the same results as that request alone and
-as direct fpcg_gram + fpcg_detect_shared calls on its data."""
+as direct fpcg_gram + fpcg_detect_grouped calls on its data."""
 import numpy as np
 import pytest
 import torch
@@ -50,7 +50,7 @@ def test_alone_equals_in_mix_and_direct(slots):
     assert srv.arena.used == 0 and srv.arena.free_list == [(0, srv.arena.size)]
 
     # direct library calls on the same data
-    d = {k: getattr(probe, k).cuda() for k in ("H", "y", "rb", "sigma2", "qam", "tx")}
+    d = {k: getattr(probe, k).cuda() for k in ("H", "y", "rb", "start", "sigma2", "qam", "tx")}
     A = torch.empty((probe.n_rb, 64, 64), dtype=torch.complex64, device="cuda")
     b = torch.empty((probe.n_rb, 64), dtype=torch.complex64, device="cuda")
     F.fpcg_gram(d["H"], torch.zeros((probe.n_rb, 256), dtype=torch.complex64, device="cuda"), d["sigma2"],
@@ -58,8 +58,8 @@ def test_alone_equals_in_mix_and_direct(slots):
     x = torch.empty((probe.n_re, 64), dtype=torch.complex64, device="cuda")
     sym = torch.empty((probe.n_re, 64), dtype=torch.uint8, device="cuda")
     bits = torch.zeros(1, dtype=torch.int64, device="cuda")
-    F.fpcg_detect_shared(A, d["H"], d["y"], d["rb"], d["qam"], 6, 8, F.precision(**srv.prec_kw), x, sym_idx=sym,
-                         tx_idx=d["tx"], bit_errors=bits)
+    F.fpcg_detect_grouped(A, d["H"], d["y"], d["start"], d["qam"], 6, 8, F.precision(**srv.prec_kw), x,
+                          sym_idx=sym, tx_idx=d["tx"], bit_errors=bits)
     torch.cuda.synchronize()
     assert torch.equal(x.cpu(), alone["x"]) and torch.equal(sym.cpu(), alone["sym"])
     assert int(bits[0]) == int(alone["bits"][0])

@@ -87,3 +87,69 @@ def test_shared_bad_index():
     ok = np.ones(len(rb), bool)
     ok[[2, 5]] = False
     assert np.all(res["st"][ok] & ~F.ST_RHO_ZERO == 0)
+
+
+def _grouped(d, iters, L, prec_kw):
+    """Same problems through fpcg_detect_grouped (the vectors are block-major)."""
+    n_rb, K, N = d["H"].shape
+    H = torch.from_numpy(d["H"]).cuda()
+    A = torch.empty((n_rb, K, K), dtype=torch.complex64, device="cuda")
+    b = torch.empty((n_rb, K), dtype=torch.complex64, device="cuda")
+    F.fpcg_gram(H, torch.zeros((n_rb, N), dtype=torch.complex64, device="cuda"),
+                torch.from_numpy(d["sigma2"]).cuda(), prec_kw["gram"], A, b)
+    rb = d["rb_index"]
+    start = np.searchsorted(rb, np.arange(n_rb + 1)).astype(np.int64)
+    y = torch.from_numpy(d["y"]).cuda()
+    n = y.shape[0]
+    out = {"x": torch.empty((n, K), dtype=torch.complex64, device="cuda"),
+           "sym": torch.empty((n, K), dtype=torch.uint8, device="cuda"),
+           "rel": torch.empty(n, dtype=torch.float64, device="cuda"),
+           "st": torch.empty(n, dtype=torch.int32, device="cuda"),
+           "be": torch.zeros(1, dtype=torch.int64, device="cuda")}
+    F.fpcg_detect_grouped(A, H, y, torch.from_numpy(start).cuda(), torch.from_numpy(d["qam"]).cuda(), iters, L,
+                          F.precision(**prec_kw), out["x"], sym_idx=out["sym"], rel_res=out["rel"],
+                          tx_idx=torch.from_numpy(d["tx"]).cuda(), bit_errors=out["be"], status=out["st"])
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("N,K,L", [(64, 16, 4), (128, 32, 8), (256, 64, 8), (256, 64, 0), (256, 64, 16),
+                                   (64, 8, 8), (512, 128, 8), (256, 128, 16), (512, 128, 0)])
+def test_grouped_matches_oracle(N, K, L, monkeypatch):
+    """Tensor-core grouped solver (K in {16, 32, 64, 128}) or the SIMT kernel (K = 8),
+    against the oracle, and against the SIMT kernel (forced) on the same inputs."""
+    d = wl.generate_rb(wl.RBSpec(N=N, K=K, n_rb=7, res_per_rb=40, seed=90 + K + L))
+    pk = dict(PREC, mv="bf16") if L == 16 else PREC
+    res = _grouped(d, 6, L, pk)
+    ref = oracle_detect(_per_vector(d), 6, pk, L=(L or None))
+    e = rel_err(res["x"], ref["x"])
+    assert np.quantile(e, 0.99) < 2e-3 and e.max() < 1e-2, (np.quantile(e, 0.99), e.max())
+    assert np.array_equal(Q.slice_symbols(res["x"], 64, "fp32"), res["sym"])
+    assert int(res["be"][0]) == Q.bit_errors(res["sym"], d["tx"])
+    allowed = F.ST_RHO_ZERO | (F.ST_BREAKDOWN if L == K else 0)
+    assert np.all(res["st"] & ~allowed == 0)
+    monkeypatch.setenv("FPCG_FORCE_SIMT", "1")
+    simt = _grouped(d, 6, L, pk)
+    e2 = rel_err(res["x"], simt["x"])
+    assert np.quantile(e2, 0.99) < 4e-3 and e2.max() < 2e-2
+
+
+def test_solve_gram_tensor_core_vs_simt(monkeypatch):
+    """fpcg_solve_gram on the tensor-core solver against the SIMT kernel."""
+    d = wl.generate(wl.Spec(N=256, K=64, batch=300, rho=0.7, qam=64, snr_db=18.0, seed=12))
+    H = torch.from_numpy(d["H"]).cuda()
+    A = torch.empty((300, 64, 64), dtype=torch.complex64, device="cuda")
+    b = torch.empty((300, 64), dtype=torch.complex64, device="cuda")
+    F.fpcg_gram(H, torch.from_numpy(d["y"]).cuda(), torch.from_numpy(d["sigma2"]).cuda(), "bf16", A, b)
+    prec = F.precision(gram="bf16", mv="fp16", refine_steps=1)
+    outs = []
+    for force in ("0", "1"):
+        monkeypatch.setenv("FPCG_FORCE_SIMT", force)
+        x = torch.empty((300, 64), dtype=torch.complex64, device="cuda")
+        st = torch.empty(300, dtype=torch.int32, device="cuda")
+        F.fpcg_solve_gram(A, b, 6, 8, prec, x, status=st)
+        torch.cuda.synchronize()
+        outs.append((x.cpu().numpy(), st.cpu().numpy()))
+    e = rel_err(outs[0][0], outs[1][0])
+    assert np.quantile(e, 0.99) < 4e-3 and e.max() < 2e-2
+    assert np.all(outs[0][1] & ~F.ST_RHO_ZERO == 0)
