@@ -345,6 +345,30 @@ FPCG_API int fpcg_plan_run(fpcg_plan* plan, const void* H, const void* y, const 
  * finished (for instance after synchronising the stream of its last run). */
 FPCG_API int fpcg_plan_destroy(fpcg_plan* plan);
 
+/*
+ * ---- Precision selection (Section IV-B, eq. heuristic and eq. heuristic_bj) ----
+ *
+ * fpcg_choose_precision -- the lowest-precision Table I format (BF16, FP16,
+ * FP32, FP64 in that order) whose unit roundoff u satisfies the paper's
+ * heuristic u_MV < 1 / (K^(3/2) sqrt(kappa)).  For FP-CG kappa is that of A;
+ * for FP-BJ-CG that of the block-Jacobi preconditioned matrix.  Returns the
+ * FPCG_* format code, or -FPCG_EINVAL for k < 1 or kappa < 1 (or not
+ * finite).  *u_bound (nullable) receives the bound.  Host only.
+ */
+FPCG_API int fpcg_choose_precision(int32_t k, double kappa, double* u_bound);
+
+/*
+ * fpcg_kappa_cg -- estimate of kappa from the first m CG step sizes alpha_0 ..
+ * alpha_{m-1} and beta_0 .. beta_{m-2} of Algorithm 2 or 3 (exact-arithmetic
+ * relation between CG and Lanczos): the tridiagonal T_m with diagonal 1/alpha_j
+ * + beta_{j-1}/alpha_{j-1} (beta_{-1} = 0) and off-diagonal sqrt(beta_j)/alpha_j
+ * has the Ritz values of A (of the preconditioned matrix for Algorithm 3).
+ * kappa_hat = largest / smallest eigenvalue of T_m, found by bisection on
+ * Sturm sequences; kappa_hat <= kappa, equal after K steps in exact arithmetic.
+ * FPCG_EINVAL for m < 1, alpha_j <= 0 or beta_j < 0.  Host only.
+ */
+FPCG_API int fpcg_kappa_cg(const double* alpha, const double* beta, int32_t m, double* kappa_hat);
+
 /* Human-readable text for a return code (static storage). */
 FPCG_API const char* fpcg_strerror(int code);
 

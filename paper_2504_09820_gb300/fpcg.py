@@ -106,6 +106,10 @@ def lib():
         L.fpcg_detect_grouped.argtypes = [_P, _P, _P, _P, _P, _I32, _I32, _I64, _I64, _I32, _I32,
                                           ctypes.POINTER(Precision), _P, _P, _P, _P, _P, _P, _P]
         L.fpcg_detect_grouped.restype = ctypes.c_int
+        L.fpcg_choose_precision.argtypes = [_I32, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+        L.fpcg_choose_precision.restype = ctypes.c_int
+        L.fpcg_kappa_cg.argtypes = [_P, _P, _I32, ctypes.POINTER(ctypes.c_double)]
+        L.fpcg_kappa_cg.restype = ctypes.c_int
         L.fpcg_plan_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(ctypes.c_void_p)]
         L.fpcg_plan_create.restype = ctypes.c_int
         L.fpcg_plan_layout.argtypes = [_P, _P, _P, _P, _P, _P]
@@ -131,6 +135,29 @@ def fpcg_path(N, K, block_L, prec):
     if rc < 0:
         raise FpcgError(-rc, "fpcg_path")
     return rc
+
+
+FORMAT_NAME = {v: k for k, v in FORMAT.items() if k != "fp8"}
+
+
+def fpcg_choose_precision(K, kappa):
+    """(format name, u bound) of the heuristic of Section IV-B (host only)."""
+    u = ctypes.c_double()
+    rc = lib().fpcg_choose_precision(int(K), float(kappa), ctypes.byref(u))
+    if rc < 0:
+        raise FpcgError(-rc, "fpcg_choose_precision")
+    return FORMAT_NAME[rc], u.value
+
+
+def fpcg_kappa_cg(alpha, beta):
+    """kappa estimate from CG step sizes alpha[0..m-1], beta[0..m-2] (host only)."""
+    import numpy as np
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    out = ctypes.c_double()
+    _check(lib().fpcg_kappa_cg(a.ctypes.data, b.ctypes.data if b.size else None, int(a.size), ctypes.byref(out)),
+           "fpcg_kappa_cg")
+    return out.value
 
 
 def fpcg_strerror(code):
