@@ -225,7 +225,7 @@ def run_mixed(args):
     nbits = float(sum(int(k) * int(round(math.log2(q))) for k, q in zip(d["k"], d["qam"])))
     paths = {}
     for c in r["classes"]:
-        key = "tensor_core" if c["path"] == F.PATH_TENSOR_CORE else "simt"
+        key = {F.PATH_TENSOR_CORE: "tensor_core", F.PATH_TWO_PASS: "two_pass"}.get(c["path"], "simt")
         paths[key] = paths.get(key, 0) + c["count"]
     print(json.dumps({
         "metric": "detections/s, uneven batch (one CUDA graph, one launch per (N, K) class)",

@@ -194,8 +194,10 @@ FPCG_API int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t ba
  * fpcg_gram -- form the Gram matrix and matched filter only (Section II,
  * eq. inversion): A = fl(H)^H fl(H) + sigma2[s] I and b = fl(H)^H fl(y) for
  * every system, fl = rounding of H and y to `gram` (FPCG_BF16 or FPCG_FP16:
- * fp32 accumulation on the tensor cores for K in {8,16,32,64}, in fp32 FMAs
- * otherwise; FPCG_FP32: fp32; FPCG_FP64: fp64).  The Hermitian A is written in
+ * exact products and fp32 accumulation on the tensor cores -- the tcgen05
+ * pipeline for K in {8,16,32,64} with N even and 16-byte aligned H and y,
+ * mma.sync for the other K in {16,32,64,128} -- and in fp32 FMAs otherwise;
+ * FPCG_FP32: fp32; FPCG_FP64: fp64).  The Hermitian A is written in
  * full.  Useful when one A serves many received vectors.
  *   A       [batch][K][K] row-major, c64 (c128 for FPCG_FP64)
  *   b       [batch][K] same element type
@@ -218,6 +220,9 @@ FPCG_API int fpcg_gram(const void* H, const void* y, const double* sigma2, int32
  */
 #define FPCG_PATH_SIMT 0
 #define FPCG_PATH_TENSOR_CORE 1
+/* (plans only) Gram matrices by mma.sync into plan workspace, then the tensor-core
+ * solver; for classes the fused kernel does not take (K = 128) */
+#define FPCG_PATH_TWO_PASS 2
 FPCG_API int fpcg_path(int32_t n_rx, int32_t k, int32_t block_L, const fpcg_precision* prec);
 
 /*
@@ -288,10 +293,13 @@ FPCG_API int fpcg_detect_grouped(const void* A, const void* H, const void* y, co
  * Every class starts on a 256-byte boundary of each buffer.  Per-system arrays
  * (sigma2, qam_order, rel_res, status) are indexed by plan order.
  *
- * Ownership: the plan owns its host tables, the instantiated CUDA graph and a
- * capture stream; fpcg_plan_destroy frees them.  All data buffers are the
- * caller's device memory.  A plan is not thread-safe; runs of one plan are
- * ordered on the stream they are issued to.
+ * Ownership: the plan owns its host tables, the instantiated CUDA graph, a
+ * capture stream and, when some class runs in two passes (FPCG_PATH_TWO_PASS:
+ * the Gram matrices of the class first, then the solves), device workspace for
+ * those Gram matrices (allocated by the first autotune or run);
+ * fpcg_plan_destroy frees them.  All data buffers are the caller's device
+ * memory.  A plan is not thread-safe; runs of one plan are ordered on the
+ * stream they are issued to.
  */
 typedef struct fpcg_plan fpcg_plan;
 
@@ -311,7 +319,7 @@ typedef struct fpcg_batch_desc {
 
 typedef struct fpcg_class_info {
   int32_t n_rx, k, block_L; /* the class's N, K and block size (0: FP-CG) */
-  int32_t path;             /* FPCG_PATH_SIMT or FPCG_PATH_TENSOR_CORE */
+  int32_t path;             /* FPCG_PATH_SIMT, FPCG_PATH_TENSOR_CORE or FPCG_PATH_TWO_PASS */
   int64_t first, count;     /* its systems: plan positions [first, first + count) */
 } fpcg_class_info;
 

@@ -23,6 +23,9 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
 // of the data aside).
 bool tc_capable(int k, int block_L, const fpcg_precision* prec);
 
+// Whether a class can run as Gram (mma.sync) + tensor-core solver.
+bool two_pass_capable(int k, int block_L, const fpcg_precision* prec);
+
 // FPCG_OK, FPCG_EINVAL or FPCG_ENOTSUP for a precision descriptor.
 int check_precision(const fpcg_precision* p);
 

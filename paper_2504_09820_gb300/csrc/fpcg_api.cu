@@ -7,6 +7,7 @@
 #include "../../include/fpcg.h"
 #include "api_internal.cuh"
 #include "detect_simt.cuh"
+#include "gram_mma.cuh"
 #include "gram_tc.cuh"
 #include "detect_tc.cuh"
 #include "solve_tc.cuh"
@@ -88,6 +89,11 @@ void cg_params(fpcg::DetectTcParams& T, const int32_t* qam_order, int32_t iters,
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
+// Precisions the CG warp runs: 16-bit matvec, fp32 vectors, residual with the matvec matrix.
+bool tc_prec_ok(const fpcg_precision* p) {
+  return p->w == FPCG_FP32 && p->resid == FPCG_FP32 && (p->mv == FPCG_BF16 || p->mv == FPCG_FP16);
+}
+
 }  // namespace
 
 namespace fpcg {
@@ -115,8 +121,9 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
     if (e != cudaSuccess) return cuda_fail(e);
   }
   if (batch == 0) return FPCG_OK;
-  const bool tc_possible = tc_capable(k, block_L, prec) &&
-                           (Ain ? aligned16(Ain) && aligned16(bin) : fpcg::tma_pipe_ok(H, y, n_rx));
+  const bool tc_possible = Ain ? tc_prec_ok(prec) && fpcg::solve_tc_supported(k, block_L) && aligned16(Ain) &&
+                                     aligned16(bin)
+                               : tc_capable(k, block_L, prec) && fpcg::tma_pipe_ok(H, y, n_rx);
   if (path == FPCG_PATH_TENSOR_CORE && !tc_possible) return FPCG_ENOTSUP;
   const bool tc_ok = tc_possible && (path == FPCG_PATH_TENSOR_CORE || (path < 0 && !force_simt()));
   if (tc_ok && Ain) {  // given Gram matrices: the tensor-core solver
@@ -191,6 +198,11 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
 int cuda_error(cudaError_t e) { return cuda_fail(e); }
 
 int check_precision(const fpcg_precision* p) { return check_prec(p); }
+
+bool two_pass_capable(int k, int block_L, const fpcg_precision* prec) {
+  return tc_prec_ok(prec) && (prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) && fpcg::gram_mma_supported(k) &&
+         fpcg::solve_tc_supported(k, block_L) && !fpcg::detect_tc_supported(k, block_L);
+}
 
 bool tc_capable(int k, int block_L, const fpcg_precision* prec) {
   return prec->w == FPCG_FP32 && prec->resid == FPCG_FP32 && (prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) &&
@@ -307,9 +319,7 @@ int fpcg_detect_grouped(const void* A, const void* H, const void* y, const int64
   }
   if (n_rhs == 0) return FPCG_OK;
   const int refine_iters = prec->refine_iters < 0 ? iters : prec->refine_iters;
-  const bool tc_prec = prec->w == FPCG_FP32 && prec->resid == FPCG_FP32 &&
-                       (prec->mv == FPCG_BF16 || prec->mv == FPCG_FP16);
-  if (!force_simt() && tc_prec && fpcg::solve_grouped_supported(k, block_L) && aligned16(A)) {
+  if (!force_simt() && tc_prec_ok(prec) && fpcg::solve_grouped_supported(k, block_L) && aligned16(A)) {
     int sms = 0;
     rc = device_sms(&sms);
     if (rc) return rc;
@@ -397,6 +407,11 @@ int fpcg_gram(const void* H, const void* y, const double* sigma2, int32_t n_rx, 
     P.b = (float2*)b;
     P.status = status;
     cudaError_t e = fpcg::launch_gram_tc(P, sms, s);
+    return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+  }
+  if ((gram == FPCG_BF16 || gram == FPCG_FP16) && fpcg::gram_mma_supported(k) && !force_simt()) {
+    fpcg::GramMmaParams P{(const float2*)H, (const float2*)y, sigma2, (float2*)A, (float2*)b, n_rx, k, batch};
+    cudaError_t e = fpcg::launch_gram_mma(P, gram == FPCG_BF16, s);
     return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
   }
   const int fp64 = gram == FPCG_FP64;

@@ -16,6 +16,7 @@ struct fpcg_plan {
     int32_t n, k, L, path;         // path: -1 = default choice, else FPCG_PATH_*
     int64_t first, count;          // plan positions
     int64_t h0, y0, x0;            // first element of the class in H, y, x_hat
+    int64_t a0, b0;                // two-pass classes: first Gram entry / matched-filter entry in the workspace
   };
   int32_t iters, flags;
   fpcg_precision prec;
@@ -23,6 +24,8 @@ struct fpcg_plan {
   std::vector<int64_t> order, h_off, y_off, x_off;
   int64_t tot[3] = {0, 0, 0};
   cudaStream_t cap = nullptr;      // capture stream (graphs cannot be captured on the legacy stream)
+  float2* ws = nullptr;            // workspace: Gram matrices and matched filters of two-pass classes
+  int64_t ws_a = 0;                // complex entries of the Gram part (the matched filters follow)
   cudaGraphExec_t exec = nullptr;  // instantiated graph of the class launches
   const void* key[10] = {};        // the run arguments it was captured with
 };
@@ -38,6 +41,58 @@ void drop_graph(fpcg_plan* p) {
   p->exec = nullptr;
 }
 
+int default_path(const fpcg_plan* p, const fpcg_plan::Class& c) {
+  if (fpcg::two_pass_capable(c.k, c.L, &p->prec)) return FPCG_PATH_TWO_PASS;
+  return fpcg_path(c.n, c.k, c.L, &p->prec);
+}
+
+int path_of(const fpcg_plan* p, const fpcg_plan::Class& c) { return c.path >= 0 ? c.path : default_path(p, c); }
+
+// Device workspace for the two-pass classes (before any capture; grows only).
+int ensure_workspace(fpcg_plan* p) {
+  if (p->ws) return FPCG_OK;
+  int64_t a = 0, b = 0;
+  for (auto& c : p->cls) {
+    if (!fpcg::two_pass_capable(c.k, c.L, &p->prec)) continue;
+    c.a0 = a;
+    c.b0 = b;
+    a += c.count * (int64_t)c.k * c.k;
+    b += c.count * (int64_t)c.k;
+  }
+  if (a == 0) return FPCG_OK;
+  p->ws_a = a;
+  const cudaError_t e = cudaMalloc(&p->ws, sizeof(float2) * (size_t)(a + b));
+  if (e != cudaSuccess) {
+    p->ws = nullptr;
+    return e == cudaErrorMemoryAllocation ? FPCG_ENOMEM : fpcg::cuda_error(e);
+  }
+  return FPCG_OK;
+}
+
+// One class on `s` with the given path.
+int run_class(fpcg_plan* p, const fpcg_plan::Class& c, int path, const void* H, const void* y, const double* sigma2,
+              const int32_t* qam, void* x_hat, uint8_t* sym, double* rel_res, const uint8_t* tx,
+              unsigned long long* bits, int32_t* status, cudaStream_t s) {
+  const float2* Hc = static_cast<const float2*>(H) + c.h0;
+  const float2* yc = static_cast<const float2*>(y) + c.y0;
+  float2* xc = static_cast<float2*>(x_hat) + c.x0;
+  if (path == FPCG_PATH_TWO_PASS) {
+    float2* A = p->ws + c.a0;
+    float2* bv = p->ws + p->ws_a + c.b0;
+    int rc = fpcg_gram(Hc, yc, sigma2 + c.first, c.n, c.k, c.count, p->prec.gram, A, bv,
+                       status ? status + c.first : nullptr, s);
+    if (rc) return rc;
+    return fpcg::run_uniform(nullptr, nullptr, nullptr, qam ? qam + c.first : nullptr, A, bv, c.k, c.k, c.count,
+                             p->iters, c.L, &p->prec, xc, sym ? sym + c.x0 : nullptr,
+                             rel_res ? rel_res + c.first : nullptr, nullptr, tx ? tx + c.x0 : nullptr, bits,
+                             status ? status + c.first : nullptr, s, FPCG_PATH_TENSOR_CORE, false);
+  }
+  return fpcg::run_uniform(Hc, yc, sigma2 + c.first, qam ? qam + c.first : nullptr, nullptr, nullptr, c.n, c.k,
+                           c.count, p->iters, c.L, &p->prec, xc, sym ? sym + c.x0 : nullptr,
+                           rel_res ? rel_res + c.first : nullptr, nullptr, tx ? tx + c.x0 : nullptr, bits,
+                           status ? status + c.first : nullptr, s, path, false);
+}
+
 // Issues every class on `s`; bit_errors is zeroed once.
 int enqueue(fpcg_plan* p, const void* H, const void* y, const double* sigma2, const int32_t* qam,
             void* x_hat, uint8_t* sym, double* rel_res, const uint8_t* tx, unsigned long long* bits,
@@ -47,13 +102,7 @@ int enqueue(fpcg_plan* p, const void* H, const void* y, const double* sigma2, co
     if (e != cudaSuccess) return fpcg::cuda_error(e);
   }
   for (const auto& c : p->cls) {
-    const float2* Hc = static_cast<const float2*>(H) + c.h0;
-    const float2* yc = static_cast<const float2*>(y) + c.y0;
-    float2* xc = static_cast<float2*>(x_hat) + c.x0;
-    const int rc = fpcg::run_uniform(Hc, yc, sigma2 + c.first, qam ? qam + c.first : nullptr, nullptr, nullptr,
-                                     c.n, c.k, c.count, p->iters, c.L, &p->prec, xc, sym ? sym + c.x0 : nullptr,
-                                     rel_res ? rel_res + c.first : nullptr, nullptr, tx ? tx + c.x0 : nullptr, bits,
-                                     status ? status + c.first : nullptr, s, c.path, false);
+    const int rc = run_class(p, c, path_of(p, c), H, y, sigma2, qam, x_hat, sym, rel_res, tx, bits, status, s);
     if (rc) return rc;
   }
   return FPCG_OK;
@@ -105,6 +154,7 @@ int fpcg_plan_create(const fpcg_batch_desc* d, fpcg_plan** out) {
         c.path = -1;
         c.first = pos;
         c.count = 0;
+        c.a0 = c.b0 = 0;
         c.h0 = h = align_up(h);
         c.y0 = yv = align_up(yv);
         c.x0 = x = align_up(x);
@@ -151,7 +201,7 @@ int fpcg_plan_classes(const fpcg_plan* p, int32_t* n_classes, fpcg_class_info* i
       info[c].n_rx = k.n;
       info[c].k = k.k;
       info[c].block_L = k.L;
-      info[c].path = k.path >= 0 ? k.path : fpcg_path(k.n, k.k, k.L, &p->prec);
+      info[c].path = path_of(p, k);
       info[c].first = k.first;
       info[c].count = k.count;
     }
@@ -172,27 +222,25 @@ int fpcg_plan_autotune(fpcg_plan* p, const void* H, const void* y, const double*
     if (e0) cudaEventDestroy(e0);
     return fpcg::cuda_error(ce);
   }
-  int rc = FPCG_OK;
+  int rc = ensure_workspace(p);
   for (auto& c : p->cls) {
-    if (!(fpcg::tc_capable(c.k, c.L, &p->prec) && c.n % 2 == 0)) {
+    if (rc) break;
+    int cand[2] = {-1, FPCG_PATH_SIMT};
+    if (fpcg::two_pass_capable(c.k, c.L, &p->prec)) cand[0] = FPCG_PATH_TWO_PASS;
+    else if (fpcg::tc_capable(c.k, c.L, &p->prec) && c.n % 2 == 0) cand[0] = FPCG_PATH_TENSOR_CORE;
+    if (cand[0] < 0) {
       c.path = FPCG_PATH_SIMT;
       continue;
     }
-    const float2* Hc = static_cast<const float2*>(H) + c.h0;
-    const float2* yc = static_cast<const float2*>(y) + c.y0;
-    float2* xc = static_cast<float2*>(x_hat) + c.x0;
     float best = -1.f;
-    int best_path = FPCG_PATH_TENSOR_CORE;
-    for (int path : {FPCG_PATH_TENSOR_CORE, FPCG_PATH_SIMT}) {
+    int best_path = cand[0];
+    for (int path : cand) {
       float ms = 0.f;
       for (int rep = 0; rep < 4 && rc == FPCG_OK; ++rep) {  // one warm-up, three timed
         if (rep == 1) cudaEventRecord(e0, s);
-        rc = fpcg::run_uniform(Hc, yc, sigma2 + c.first, qam ? qam + c.first : nullptr, nullptr, nullptr, c.n, c.k,
-                               c.count, p->iters, c.L, &p->prec, xc, sym ? sym + c.x0 : nullptr,
-                               rel_res ? rel_res + c.first : nullptr, nullptr, nullptr, nullptr,
-                               status ? status + c.first : nullptr, s, path, false);
+        rc = run_class(p, c, path, H, y, sigma2, qam, x_hat, sym, rel_res, nullptr, nullptr, status, s);
       }
-      if (rc == FPCG_ENOTSUP && path == FPCG_PATH_TENSOR_CORE) {  // e.g. unaligned data
+      if (rc == FPCG_ENOTSUP && path != FPCG_PATH_SIMT) {  // e.g. unaligned data
         rc = FPCG_OK;
         continue;
       }
@@ -225,7 +273,13 @@ int fpcg_plan_run(fpcg_plan* p, const void* H, const void* y, const double* sigm
   if ((sym || bits) && !qam) return FPCG_EINVAL;
   if ((tx != nullptr) != (bits != nullptr)) return FPCG_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (!(p->flags & FPCG_PLAN_GRAPH)) return enqueue(p, H, y, sigma2, qam, x_hat, sym, rel_res, tx, bits, status, s);
+  if (!(p->flags & FPCG_PLAN_GRAPH)) {
+    const int wrc = ensure_workspace(p);
+    if (wrc) return wrc;
+    return enqueue(p, H, y, sigma2, qam, x_hat, sym, rel_res, tx, bits, status, s);
+  }
+  const int wrc = ensure_workspace(p);
+  if (wrc) return wrc;
   const void* key[10] = {H, y, sigma2, qam, x_hat, sym, rel_res, tx, bits, status};
   if (p->exec && !std::equal(key, key + 10, p->key)) drop_graph(p);
   if (!p->exec) {
@@ -258,6 +312,7 @@ int fpcg_plan_destroy(fpcg_plan* p) {
   if (!p) return FPCG_OK;
   drop_graph(p);
   if (p->cap) cudaStreamDestroy(p->cap);
+  if (p->ws) cudaFree(p->ws);
   delete p;
   return FPCG_OK;
 }

@@ -21,12 +21,17 @@ struct SolveTcParams {
   int N, K, gram;             // gram: rounding of H and y in the matched filter
 };
 
-// K in {16, 32, 64}, L in {0, 4, 8, 16}: the CG warp's configurations.
-inline bool solve_tc_supported(int K, int L) { return detect_tc_supported(K, L); }
+// K in {16, 32, 64, 128}, L in {0, 4, 8, 16}: the CG warp's configurations.
+inline bool solve_tc_supported(int K, int L) {
+  return (K == 16 || K == 32 || K == 64 || K == 128) && (L == 0 || L == 4 || L == 8 || L == 16);
+}
 
-constexpr int kSolveWarps = 8;  // CG warps per CTA, one slot each
+constexpr int kSolveWarps = 8;  // CG warps per CTA (grouped mode, and independent systems for K <= 64)
 
-inline size_t solve_tc_smem_bytes(int K, int L) { return 128 + kSolveWarps * tc_slot_bytes(K, L); }
+// Independent systems: one slot per warp; K = 128 slots (~80 KB) allow two per CTA.
+__host__ __device__ constexpr int solve_warps(int K) { return K == 128 ? 2 : kSolveWarps; }
+
+inline size_t solve_tc_smem_bytes(int K, int L) { return 128 + solve_warps(K) * tc_slot_bytes(K, L); }
 
 // Grouped mode (fpcg_detect_grouped): all warps of a CTA share one group's A
 // and inverted blocks; each warp has its own b, matvec result and B fragments.
@@ -64,9 +69,11 @@ cudaError_t launch_solve_tc_k(const SolveTcParams& P, int num_sms, int mv_bf16, 
 extern template cudaError_t launch_solve_tc_k<16>(const SolveTcParams&, int, int, cudaStream_t);
 extern template cudaError_t launch_solve_tc_k<32>(const SolveTcParams&, int, int, cudaStream_t);
 extern template cudaError_t launch_solve_tc_k<64>(const SolveTcParams&, int, int, cudaStream_t);
+extern template cudaError_t launch_solve_tc_k<128>(const SolveTcParams&, int, int, cudaStream_t);
 
 inline cudaError_t launch_solve_tc(const SolveTcParams& P, int num_sms, int mv_bf16, cudaStream_t stream) {
   switch (P.K) {
+    case 128: return launch_solve_tc_k<128>(P, num_sms, mv_bf16, stream);
     case 64: return launch_solve_tc_k<64>(P, num_sms, mv_bf16, stream);
     case 32: return launch_solve_tc_k<32>(P, num_sms, mv_bf16, stream);
     case 16: return launch_solve_tc_k<16>(P, num_sms, mv_bf16, stream);

@@ -100,13 +100,14 @@ __device__ void matched_filter(const float2* Hg, const float2* ys, int N, int gr
 }
 
 template <int K, bool BF, int LT>
-__global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_tc_kernel(const __grid_constant__ SolveTcParams P) {
+__global__ void __launch_bounds__(solve_warps(K) * 32, 1) solve_tc_kernel(const __grid_constant__ SolveTcParams P) {
+  constexpr int NW = solve_warps(K);
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
   const Slot S = slot_carve(base + warp * tc_slot_bytes(K, LT), K, LT);
   CgWarp<K, BF, LT> W(P.D, S, lane);
-  const int64_t tw = (int64_t)gridDim.x * kSolveWarps, gw = (int64_t)blockIdx.x * kSolveWarps + warp;
+  const int64_t tw = (int64_t)gridDim.x * NW, gw = (int64_t)blockIdx.x * NW + warp;
   const int64_t chunk = (P.n + tw - 1) / tw;
   const int64_t s0 = gw * chunk, s1 = min(P.n, s0 + chunk);
   if (s0 >= s1) return;
@@ -139,7 +140,8 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_tc_kernel(const __g
       cur = g;
     }
     if (P.b) {
-      if (lane < K / 2) reinterpret_cast<float4*>(S.b)[lane] = __ldg(reinterpret_cast<const float4*>(P.b + (size_t)s * K) + lane);
+      for (int i = lane; i < K / 2; i += 32)  // two complex entries per float4
+        reinterpret_cast<float4*>(S.b)[i] = __ldg(reinterpret_cast<const float4*>(P.b + (size_t)s * K) + i);
       __syncwarp();
     } else {
       matched_filter<K>(P.H + (size_t)g * K * P.N, P.y + (size_t)s * P.N, P.N, P.gram, S, lane);
@@ -252,15 +254,16 @@ cudaError_t launch_s(const SolveTcParams& P, int num_sms, cudaStream_t stream) {
   cudaError_t e =
       cudaFuncSetAttribute(solve_tc_kernel<K, BF, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  constexpr int W = solve_warps(K);
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_tc_kernel<K, BF, LT>, kSolveWarps * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_tc_kernel<K, BF, LT>, W * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)num_sms * per_sm;
-  const int64_t need = (P.n + kSolveWarps - 1) / kSolveWarps;
+  const int64_t need = (P.n + W - 1) / W;
   if (grid > need) grid = need;
   if (grid <= 0) return cudaSuccess;
-  solve_tc_kernel<K, BF, LT><<<(unsigned)grid, kSolveWarps * 32, smem, stream>>>(P);
+  solve_tc_kernel<K, BF, LT><<<(unsigned)grid, W * 32, smem, stream>>>(P);
   return cudaGetLastError();
 }
 

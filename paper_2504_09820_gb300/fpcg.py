@@ -126,7 +126,7 @@ def lib():
     return _lib
 
 
-PATH_SIMT, PATH_TENSOR_CORE = 0, 1
+PATH_SIMT, PATH_TENSOR_CORE, PATH_TWO_PASS = 0, 1, 2
 
 
 def fpcg_path(N, K, block_L, prec):

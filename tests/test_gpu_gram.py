@@ -73,3 +73,15 @@ def test_gram_simt_fallbacks():
     A, b, st = run_gram(d, "fp64")
     Ar, br = D.gram_emul(d["H"], d["y"], d["sigma2"], "fp64")
     assert np.abs(A - Ar).max() < 1e-12 and np.abs(b - br).max() < 1e-12
+
+
+@pytest.mark.parametrize("K,N", [(128, 512), (128, 256), (128, 130), (64, 255), (32, 97), (16, 33)])
+@pytest.mark.parametrize("gram", ["bf16", "fp16"])
+def test_mma_gram(K, N, gram):
+    """The mma.sync Gram (K = 128, or odd N the TMA pipeline cannot address):
+    several antenna chunks, a ragged last chunk, against the oracle."""
+    d = wl.generate(wl.Spec(N=N, K=K, batch=40, rho=0.5, qam=64, snr_db=15.0, seed=200 + K + N))
+    A, b, st = run_gram(d, gram)
+    # the mma chain rounds the fp32 accumulator twice per 16 antennas (two MMAs per
+    # part); one ulp (2^-23, truncation allowed) of the row scale per rounding
+    check(d, gram, A, b, st, tol=max(2e-6, 2 * (-(-N // 16)) * 2.0 ** -23))

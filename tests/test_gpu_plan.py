@@ -74,11 +74,13 @@ def test_plan_matches_oracle_per_class(mixed):
 
 
 def test_plan_equals_uniform_calls(mixed):
-    """Each class runs the same kernel as a uniform call on its systems."""
+    """Each one-pass class runs the same kernel as a uniform call on its systems."""
     d, p, g = mixed
     out = _run(p, g)
     x = p.unpack(out["x"], d["k"])
     for c in p.classes():
+        if c["path"] == F.PATH_TWO_PASS:
+            continue
         idx = np.sort(p.order[c["first"]:c["first"] + c["count"]])
         cd = _class_data(d, idx)
         t = {k: torch.from_numpy(v).cuda() for k, v in cd.items()}
@@ -103,10 +105,33 @@ def test_autotune_keeps_results(mixed):
     base = _run(p, g)
     tuned = _run(p, g, autotune=True)
     cls = p.classes()
-    assert all(c["path"] in (F.PATH_SIMT, F.PATH_TENSOR_CORE) for c in cls)
-    assert all(c["path"] == F.PATH_SIMT for c in cls if c["k"] in (8, 128))
+    assert all(c["path"] in (F.PATH_SIMT, F.PATH_TENSOR_CORE, F.PATH_TWO_PASS) for c in cls)
+    assert all(c["path"] == F.PATH_SIMT for c in cls if c["k"] == 8)
+    assert all(c["path"] in (F.PATH_SIMT, F.PATH_TWO_PASS) for c in cls if c["k"] == 128)
     # same algorithm on either kernel: within the sum of both kernels' parity bounds
     xb = p.unpack(base["x"], d["k"])
     xt = p.unpack(tuned["x"], d["k"])
     e = np.array([np.linalg.norm(xt[i] - xb[i]) / np.linalg.norm(xb[i]) for i in range(p.batch)])
     assert np.quantile(e, 0.99) < 4e-3 and e.max() < 2e-2
+
+
+def test_two_pass_class_equals_gram_then_solve(mixed):
+    """A two-pass class (K = 128) gives exactly fpcg_gram + fpcg_solve_gram + slicing
+    on its systems."""
+    d, p, g = mixed
+    out = _run(p, g)
+    x = p.unpack(out["x"], d["k"])
+    two = [c for c in p.classes() if c["path"] == F.PATH_TWO_PASS]
+    assert two
+    for c in two:
+        idx = np.sort(p.order[c["first"]:c["first"] + c["count"]])
+        cd = _class_data(d, idx)
+        t = {k: torch.from_numpy(v).cuda() for k, v in cd.items()}
+        n, K = len(idx), c["k"]
+        A = torch.empty((n, K, K), dtype=torch.complex64, device="cuda")
+        b = torch.empty((n, K), dtype=torch.complex64, device="cuda")
+        F.fpcg_gram(t["H"], t["y"], t["sigma2"], PREC["gram"], A, b)
+        xs = torch.empty((n, K), dtype=torch.complex64, device="cuda")
+        F.fpcg_solve_gram(A, b, ITERS, c["block_L"], F.precision(**PREC), xs)
+        torch.cuda.synchronize()
+        assert np.array_equal(xs.cpu().numpy(), np.stack([x[i] for i in idx])), c

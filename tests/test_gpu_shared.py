@@ -134,18 +134,19 @@ def test_grouped_matches_oracle(N, K, L, monkeypatch):
     assert np.quantile(e2, 0.99) < 4e-3 and e2.max() < 2e-2
 
 
-def test_solve_gram_tensor_core_vs_simt(monkeypatch):
+@pytest.mark.parametrize("N,K", [(256, 64), (512, 128)])
+def test_solve_gram_tensor_core_vs_simt(N, K, monkeypatch):
     """fpcg_solve_gram on the tensor-core solver against the SIMT kernel."""
-    d = wl.generate(wl.Spec(N=256, K=64, batch=300, rho=0.7, qam=64, snr_db=18.0, seed=12))
+    d = wl.generate(wl.Spec(N=N, K=K, batch=300, rho=0.7, qam=64, snr_db=18.0, seed=12))
     H = torch.from_numpy(d["H"]).cuda()
-    A = torch.empty((300, 64, 64), dtype=torch.complex64, device="cuda")
-    b = torch.empty((300, 64), dtype=torch.complex64, device="cuda")
+    A = torch.empty((300, K, K), dtype=torch.complex64, device="cuda")
+    b = torch.empty((300, K), dtype=torch.complex64, device="cuda")
     F.fpcg_gram(H, torch.from_numpy(d["y"]).cuda(), torch.from_numpy(d["sigma2"]).cuda(), "bf16", A, b)
     prec = F.precision(gram="bf16", mv="fp16", refine_steps=1)
     outs = []
     for force in ("0", "1"):
         monkeypatch.setenv("FPCG_FORCE_SIMT", force)
-        x = torch.empty((300, 64), dtype=torch.complex64, device="cuda")
+        x = torch.empty((300, K), dtype=torch.complex64, device="cuda")
         st = torch.empty(300, dtype=torch.int32, device="cuda")
         F.fpcg_solve_gram(A, b, 6, 8, prec, x, status=st)
         torch.cuda.synchronize()
