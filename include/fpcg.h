@@ -354,6 +354,29 @@ FPCG_API int fpcg_plan_run(fpcg_plan* plan, const void* H, const void* y, const 
 FPCG_API int fpcg_plan_destroy(fpcg_plan* plan);
 
 /*
+ * fpcg_detect_noalloc -- detection that allocates no device memory (the paper
+ * has no counterpart: this is about the library's memory, not the method).
+ * Same arguments and results as fpbjcg_detect (block_L > 0) or fpcg_detect
+ * (block_L = 0).  Configurations that run in two passes (Gram matrices first,
+ * then the tensor-core solver: K = 128 with a 16-bit matvec, w = resid = FP32,
+ * gram in {BF16, FP16}) keep their Gram matrices and matched filters in one
+ * fixed 64 MiB device array of the library; every other configuration takes
+ * the ordinary path, which allocates nothing either.
+ *   - Limit: batch * K * (K + 1) * 8 bytes <= 64 MiB (K = 128: 496 systems per
+ *     call); a larger batch returns FPCG_ENOTSUP (split it).
+ *   - The array is shared by all calls on a device: calls must not overlap in
+ *     time (issue them on one stream, or wait for one before the next).
+ *   - The first call on each device looks up the array's address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture
+ *     begins.
+ */
+FPCG_API int fpcg_detect_noalloc(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+                                 int32_t n_rx, int32_t k, int64_t batch, int32_t iters, int32_t block_L,
+                                 const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx, double* rel_res,
+                                 float* res_hist, const uint8_t* tx_idx, unsigned long long* bit_errors,
+                                 int32_t* status, void* stream);
+
+/*
  * ---- Precision selection (Section IV-B, eq. heuristic and eq. heuristic_bj) ----
  *
  * fpcg_choose_precision -- the lowest-precision Table I format (BF16, FP16,

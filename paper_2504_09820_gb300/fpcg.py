@@ -110,6 +110,8 @@ def lib():
         L.fpcg_choose_precision.restype = ctypes.c_int
         L.fpcg_kappa_cg.argtypes = [_P, _P, _I32, ctypes.POINTER(ctypes.c_double)]
         L.fpcg_kappa_cg.restype = ctypes.c_int
+        L.fpcg_detect_noalloc.argtypes = det + [_I32, ctypes.POINTER(Precision)] + outs
+        L.fpcg_detect_noalloc.restype = ctypes.c_int
         L.fpcg_plan_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(ctypes.c_void_p)]
         L.fpcg_plan_create.restype = ctypes.c_int
         L.fpcg_plan_layout.argtypes = [_P, _P, _P, _P, _P, _P]
@@ -229,6 +231,14 @@ def fpbjcg_detect(H, y, sigma2, qam_order, iters, block_L, prec, x_hat, sym_idx=
     a, b = _detect_args(H, y, sigma2, qam_order, iters, prec, x_hat, sym_idx, rel_res, res_hist,
                         tx_idx, bit_errors, status)
     _check(lib().fpbjcg_detect(*a, int(block_L), *b, _stream(stream)), "fpbjcg_detect")
+
+
+def fpcg_detect_noalloc(H, y, sigma2, qam_order, iters, block_L, prec, x_hat, sym_idx=None, rel_res=None,
+                        res_hist=None, tx_idx=None, bit_errors=None, status=None, stream=None):
+    """Marshal a call to fpcg_detect_noalloc (no device allocation; block_L 0 = FP-CG)."""
+    a, b = _detect_args(H, y, sigma2, qam_order, iters, prec, x_hat, sym_idx, rel_res, res_hist,
+                        tx_idx, bit_errors, status)
+    _check(lib().fpcg_detect_noalloc(*a, int(block_L or 0), *b, _stream(stream)), "fpcg_detect_noalloc")
 
 
 def fpcg_solve_gram(A, b, iters, block_L, prec, x_hat, rel_res=None, res_hist=None, status=None,
