@@ -300,7 +300,7 @@ def run_serve(args):
                                f"block kept across the slot",
                    "method": HEAD["name"], "block_L": f"min({HEAD['L']}, K)", "iters": HEAD["iters"],
                    "precision": HEAD["prec"], "budget_bytes": budget, "streams": 4,
-                   "path": "fpcg_gram per block + fpcg_detect_grouped (tensor-core solver for K in 16..64)"},
+                   "path": "fpcg_gram per block + fpcg_detect_grouped (tensor-core solver for K in 16..128)"},
         "saturation": {"requests_per_s": sat_rate, "detections_per_s": n_re / makespan,
                        "makespan_s": makespan, "detections": n_re},
         "loads": loads, "status_max": st_max, "clocks": clk.summary(),
