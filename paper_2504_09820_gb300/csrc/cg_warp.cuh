@@ -194,16 +194,21 @@ struct CgWarp {
         const int kt = rl >> 4, j = rl & 15, tt = (j & 7) >> 1, h = j >> 3;
         uint32_t* w = S.Pk + (kt * NCOL * 4 + tt) * 2 + h;
         float a[4] = {v[e].x, nx, v[e].y, ny};
+        if (!split) {  // columns 2..5 feed only outputs the matvec does not read
+          w[0] = pk2<BF>(a[0], a[1]);
+          w[8] = pk2<BF>(a[2], a[3]);
+        } else {
 #pragma unroll
-        for (int s3 = 0; s3 < 3; ++s3) {
-          float hh[4];
+          for (int s3 = 0; s3 < 3; ++s3) {
+            float hh[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            hh[u] = round16<BF>(a[u]);
-            a[u] = split ? a[u] - hh[u] : 0.f;  // exact remainder of the rounding
+            for (int u = 0; u < 4; ++u) {
+              hh[u] = round16<BF>(a[u]);
+              a[u] -= hh[u];  // exact remainder of the rounding
+            }
+            w[(2 * s3) * 8] = pk2<BF>(hh[0], hh[1]);
+            w[(2 * s3 + 1) * 8] = pk2<BF>(hh[2], hh[3]);
           }
-          w[(2 * s3) * 8] = pk2<BF>(hh[0], hh[1]);
-          w[(2 * s3 + 1) * 8] = pk2<BF>(hh[2], hh[3]);
         }
       }
     }
@@ -399,7 +404,7 @@ struct CgWarp {
             it = iters_p;
             continue;
           }
-          const float alpha = rho_prev / phi;
+          const float alpha = __fdividef(rho_prev, phi);  // within 2 ulp of fl(rho / phi)
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             d[e] = make_float2(fmaf(alpha, p[e].x, d[e].x), fmaf(alpha, p[e].y, d[e].y));
@@ -413,7 +418,7 @@ struct CgWarp {
       float rz;
       dot2(r, z, r, r, rz, rr);
       const float rho_new = rip(rz);
-      const float beta = fresh ? 0.f : rho_new / rho_prev;
+      const float beta = fresh ? 0.f : __fdividef(rho_new, rho_prev);
 #pragma unroll
       for (int e = 0; e < E; ++e)
         p[e] = fresh ? z[e] : make_float2(fmaf(beta, p[e].x, z[e].x), fmaf(beta, p[e].y, z[e].y));

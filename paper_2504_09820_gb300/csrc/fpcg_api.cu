@@ -8,6 +8,7 @@
 #include "api_internal.cuh"
 #include "detect_simt.cuh"
 #include "gram_mma.cuh"
+#include "mf_mma.cuh"
 #include "gram_tc.cuh"
 #include "detect_tc.cuh"
 #include "solve_tc.cuh"
@@ -333,6 +334,13 @@ int fpcg_detect_grouped(const void* A, const void* H, const void* y, const int64
     T.H = (const float2*)H;
     T.y = (const float2*)y;
     T.group_start = group_start;
+    if ((prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) && fpcg::mf_mma_supported(k) && aligned16(x_hat)) {
+      // every vector's matched filter at once on the tensor cores, into x_hat (same size)
+      fpcg::MfMmaParams M{(const float2*)H, (const float2*)y, group_start, (float2*)x_hat, n_rx, k, n_groups};
+      cudaError_t e = fpcg::launch_mf_mma(M, prec->gram == FPCG_BF16, s);
+      if (e != cudaSuccess) return cuda_fail(e);
+      T.b = (const float2*)x_hat;
+    }
     T.n = n_rhs;
     T.n_groups = n_groups;
     T.N = n_rx;

@@ -154,7 +154,9 @@ __global__ void __launch_bounds__(solve_warps(K) * 32, 1) solve_tc_kernel(const 
 // Grouped mode: CTA c takes groups c, c + gridDim.x, ...; for each, all its
 // threads round the group's A into the shared slot, warps 0..K/32-1 invert the
 // diagonal blocks (one block column per lane), and the warps take the group's
-// received vectors round-robin: matched filter into their own b, then detect.
+// received vectors round-robin: their b (given, or the matched filter formed
+// here), then detect.  A given b may share memory with x_hat: a vector's b is
+// read before its x_hat is written, by the same warp.
 template <int K, bool BF, int LT>
 __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_grouped_kernel(const __grid_constant__ SolveTcParams P) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -224,7 +226,13 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_grouped_kernel(cons
       __syncthreads();
     }
     for (int64_t s = s0 + warp; s < s1; s += kSolveWarps) {
-      matched_filter<K>(P.H + (size_t)g * K * P.N, P.y + (size_t)s * P.N, P.N, P.gram, S, lane);
+      if (P.b) {  // formed beforehand for the whole group (mf_mma)
+        for (int i = lane; i < K / 2; i += 32)
+          reinterpret_cast<float4*>(S.b)[i] = reinterpret_cast<const float4*>(P.b + (size_t)s * K)[i];
+        __syncwarp();
+      } else {
+        matched_filter<K>(P.H + (size_t)g * K * P.N, P.y + (size_t)s * P.N, P.N, P.gram, S, lane);
+      }
       W.detect(s, true, st0);
       __syncwarp();
     }
