@@ -181,9 +181,10 @@ FPCG_API int fpbjcg_detect(const void* H, const void* y, const double* sigma2, c
  *   block_L  0 = FP-CG (Algorithm 2), else FP-BJ-CG (Algorithm 3) with this L
  * prec->gram is ignored; everything else as fpcg_detect.  rel_res, res_hist
  * and status are nullable.  Runs on the tensor-core solver (one warp per
- * system, A rounded to the matvec format in shared memory) when fpcg_path
- * would pick the tensor-core kernel for (K, block_L, prec) and A, b are
- * 16-byte aligned, else on the SIMT kernel.
+ * system, A rounded to the matvec format in shared memory) for mv in {BF16,
+ * FP16}, w = resid = FP32, K in {8, 16, 32, 64, 128} (K = 8 in 16-wide slots
+ * holding diag(A, I), b padded with zeros: the same iterates), block_L in {0,
+ * 4, 8, 16} and 16-byte aligned A, b; else on the SIMT kernel.
  */
 FPCG_API int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t batch, int32_t iters,
                     int32_t block_L, const fpcg_precision* prec,
@@ -196,7 +197,7 @@ FPCG_API int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t ba
  * every system, fl = rounding of H and y to `gram` (FPCG_BF16 or FPCG_FP16:
  * exact products and fp32 accumulation on the tensor cores -- the tcgen05
  * pipeline for K in {8,16,32,64} with N even and 16-byte aligned H and y,
- * mma.sync for the other K in {16,32,64,128} -- and in fp32 FMAs otherwise;
+ * mma.sync for the other K in {8,16,32,64,128} -- and in fp32 FMAs otherwise;
  * FPCG_FP32: fp32; FPCG_FP64: fp64).  The Hermitian A is written in
  * full.  Useful when one A serves many received vectors.
  *   A       [batch][K][K] row-major, c64 (c128 for FPCG_FP64)
@@ -221,7 +222,7 @@ FPCG_API int fpcg_gram(const void* H, const void* y, const double* sigma2, int32
 #define FPCG_PATH_SIMT 0
 #define FPCG_PATH_TENSOR_CORE 1
 /* (plans only) Gram matrices by mma.sync into plan workspace, then the tensor-core
- * solver; for classes the fused kernel does not take (K = 128) */
+ * solver; for classes the fused kernel does not take (K = 8, K = 128) */
 #define FPCG_PATH_TWO_PASS 2
 FPCG_API int fpcg_path(int32_t n_rx, int32_t k, int32_t block_L, const fpcg_precision* prec);
 
@@ -233,7 +234,12 @@ FPCG_API int fpcg_path(int32_t n_rx, int32_t k, int32_t block_L, const fpcg_prec
  * Gram of its group g = rb_index[s]: its own matched filter b_s = fl(H_g)^H
  * fl(y_s) (eq. inversion, rounded to prec->gram like the Gram), then Algorithm
  * 2 (block_L = 0) or Algorithm 3 (block_L > 0), refinement, slicing, as in
- * fpcg_detect.  One CTA per received vector (the SIMT kernel).
+ * fpcg_detect.  Tensor-core modes (w = resid = FP32, mv = BF16 | FP16) with
+ * K in {8, 16, 32, 64, 128} and block_L in {0, 4, 8, 16} run on the
+ * tensor-core solver: one warp per received vector, the group's 16-bit A and
+ * inverted blocks reloaded only when rb_index changes between consecutive
+ * vectors (so vectors sorted by group share them); other modes run one CTA
+ * per received vector (the SIMT kernel).
  *   A          [n_rb][K][K] complex64 (complex128 in FP64 mode): A_g + sigma_g^2 I,
  *              as fpcg_gram writes it with the same gram format
  *   H          [n_rb][K][N] complex64: the groups' channels (the layout of fpcg_detect)
@@ -258,8 +264,9 @@ FPCG_API int fpcg_detect_shared(const void* A, const void* H, const void* y, con
  * outputs per received vector), with
  *   group_start  device [n_groups + 1] int64, non-decreasing, group_start[0] = 0,
  *                group_start[n_groups] = n_rhs (not checked on the device)
- * Runs on the tensor-core solver when K in {16, 32, 64, 128}, block_L in {0,
- * 4, 8, 16}, mv in {BF16, FP16}, w = resid = FP32 and A is 16-byte aligned:
+ * Runs on the tensor-core solver when K in {8, 16, 32, 64, 128} (8: padded as
+ * in fpcg_solve_gram), block_L in {0, 4, 8, 16}, mv in {BF16, FP16}, w = resid
+ * = FP32 and A is 16-byte aligned:
  * the eight warps of a CTA share one group's A (rounded to the matvec format)
  * and inverted diagonal blocks, and each warp detects one received vector at a
  * time.  Otherwise the SIMT kernel (one CTA per received vector).

@@ -137,16 +137,33 @@ __device__ __noinline__ float round_ip(float v, int fmt) { return round_to(v, fm
 // that runs once per system is fetched cold.  So every step exists once in the
 // code: the solves of all passes and the refinement residuals run in one loop,
 // whose trips are either A p (a CG iteration) or b - A x (a residual).
-template <int K, bool BF, int LT>
+// KR <= K: the system's own size; rows KR..K-1 of the slot are padding
+// (identity rows of A, zeros of b) and are neither read from nor written to
+// global memory.
+//
+// NV = 1: the warp works alone on its slot.  NV = 8: the eight warps of a CTA
+// detect eight systems with one shared A in lockstep, and every product with
+// A is one CTA-wide product A [v_0 .. v_7]: each warp packs its vector into
+// the shared B fragments (S.Pk: n-tile nt, column c of k-tile kt at words
+// ((kt*8 + nt)*8 + c)*8), then computes the rows of one m-tile for a share of
+// the n-tiles, so A is read from shared memory once per trip instead of once
+// per system.  A CG iteration uses two n-tiles (vectors 4nt..4nt+3, columns
+// re, im of each); a residual uses one n-tile per vector (its six columns).
+// S.b and S.W of warp v are at vbase + v * vst (and + 8K bytes).
+template <int K, bool BF, int LT, int KR = K, int NV = 1>
 struct CgWarp {
   static constexpr int KT = K / 16;          // k-tiles (16 users)
   static constexpr int MT = K / 16;          // m-tiles of Re A (and of Im A)
   static constexpr int E = K >= 32 ? K / 32 : 1;  // vector rows per lane
   static constexpr int NCOL = 6;             // B columns (re, im) x (hi, mid, lo)
+  static_assert(NV == 1 || (NV == 8 && MT <= 8), "cooperative mode: eight warps");
   const DetectTcParams& P;
   Slot S;
   int lane, g, t;
   int ipf, alpha_num, iters, refine_steps, refine_iters;  // parameters kept in registers
+  int vw = 0;                // NV = 8: this warp's vector (its warp index)
+  uint8_t* vbase = nullptr;  // NV = 8: per-vector b, W
+  int vst = 0;
 
   __device__ CgWarp(const DetectTcParams& P_, Slot S_, int lane_) : P(P_), S(S_), lane(lane_) {
     g = lane >> 2;
@@ -159,6 +176,8 @@ struct CgWarp {
   }
 
   __device__ __forceinline__ bool vact() const { return lane < K; }
+  // row lane + 32e belongs to the system (not padding)
+  __device__ __forceinline__ bool vout(int e) const { return KR == K ? vact() : lane + 32 * e < KR; }
   __device__ __forceinline__ float rip(float v) { return ipf == F32 ? v : round_ip(v, ipf); }
 
   // Re sum conj(a) b and Re sum conj(c) d over the warp's rows.
@@ -192,7 +211,9 @@ struct CgWarp {
       const int rl = lane + 32 * e;
       if (vact() && (rl & 1) == 0) {
         const int kt = rl >> 4, j = rl & 15, tt = (j & 7) >> 1, h = j >> 3;
-        uint32_t* w = S.Pk + (kt * NCOL * 4 + tt) * 2 + h;
+        uint32_t* w = S.Pk + tt * 2 + h +
+                      (NV == 1 ? kt * NCOL * 8
+                               : (split ? (kt * 8 + vw) * 64 : ((kt * 8 + (vw >> 2)) * 8 + 2 * (vw & 3)) * 8));
         float a[4] = {v[e].x, nx, v[e].y, ny};
         if (!split) {  // columns 2..5 feed only outputs the matvec does not read
           w[0] = pk2<BF>(a[0], a[1]);
@@ -220,6 +241,10 @@ struct CgWarp {
   // (g, t) holds C rows g, g+8 and columns 2t, 2t+1.  Then w = W in the vector
   // layout.
   __device__ __forceinline__ void apply(bool res, float2 (&w)[E]) {
+    if constexpr (NV > 1) {
+      apply_cta(res, w);
+      return;
+    }
     uint32_t b0[KT], b1[KT];
 #pragma unroll
     for (int kt = 0; kt < KT; ++kt) {
@@ -284,6 +309,82 @@ struct CgWarp {
     __syncwarp();
   }
 
+  // NV = 8: n-tiles nt0 .. nt0 + NB - 1 of m-tile mt, A fragments loaded once
+  // per k-tile; results into the W of their vectors.
+  template <int NB>
+  __device__ __forceinline__ void cta_tiles(int mt, int nt0, bool res) {
+    float cr[NB][4], ci[NB][4];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cr[j][q] = ci[j][q] = 0.f;
+    const uint32_t abase = tc::smem_u32(S.A16);
+    const int lr = lane & 15, lc = lane >> 4;
+    const bool bz = res && g >= NCOL;  // residual n-tiles: columns 6, 7 are zero
+#pragma unroll
+    for (int kt = 0; kt < KT; ++kt) {
+      uint32_t ar[4], ai[4];
+      tc::ldmatrix_x4(ar, abase + a16_offset<K>(16 * mt + lr, 2 * kt + lc));
+      tc::ldmatrix_x4(ai, abase + a16_offset<K>(K + 16 * mt + lr, 2 * kt + lc));
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        uint2 pw = *reinterpret_cast<const uint2*>(S.Pk + ((kt * 8 + nt0 + j) * 8 + g) * 8 + 2 * t);
+        if (bz) pw = make_uint2(0u, 0u);
+        mma16<BF>(cr[j], ar, pw.x, pw.y);
+        mma16<BF>(ci[j], ai, pw.x, pw.y);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int nt = nt0 + j;
+      if (res) {  // n-tile = vector nt: add the mid and lo column products into t = 0
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float r1 = __shfl_down_sync(0xffffffffu, cr[j][q], 1);
+          const float r2 = __shfl_down_sync(0xffffffffu, cr[j][q], 2);
+          const float i1 = __shfl_down_sync(0xffffffffu, ci[j][q], 1);
+          const float i2 = __shfl_down_sync(0xffffffffu, ci[j][q], 2);
+          cr[j][q] += r1 + r2;
+          ci[j][q] += i1 + i2;
+        }
+      }
+      if (!res || t == 0) {
+        const int v = res ? nt : 4 * nt + t;
+        float2* Wv = reinterpret_cast<float2*>(vbase + v * vst + 8 * K);
+        float2 w0 = make_float2(cr[j][0] - ci[j][1], cr[j][1] + ci[j][0]);
+        float2 w8 = make_float2(cr[j][2] - ci[j][3], cr[j][3] + ci[j][2]);
+        if (res) {
+          const float2* bv = reinterpret_cast<const float2*>(vbase + v * vst);
+          const float2 bb0 = bv[16 * mt + g], bb8 = bv[16 * mt + g + 8];
+          w0 = make_float2(bb0.x - w0.x, bb0.y - w0.y);
+          w8 = make_float2(bb8.x - w8.x, bb8.y - w8.y);
+        }
+        Wv[16 * mt + g] = w0;
+        Wv[16 * mt + g + 8] = w8;
+      }
+    }
+  }
+
+  // NV = 8: the CTA-wide product; warp vw takes m-tile vw / WPM and its share
+  // of the n-tiles (2 for a CG iteration, 8 for a residual).
+  __device__ __forceinline__ void apply_cta(bool res, float2 (&w)[E]) {
+    constexpr int WPM = 8 / MT;                 // warps per m-tile
+    constexpr int NPI = WPM >= 2 ? 1 : 2;       // iteration n-tiles per warp
+    constexpr int NPR = 8 / WPM;                // residual n-tiles per warp
+    constexpr int NBR = NPR > 4 ? 4 : NPR;      // residual n-tiles per pass over A
+    const int mt = vw / WPM, sub = vw % WPM;
+    __syncthreads();  // every vector is packed
+    if (!res) {
+      if (sub * NPI < 2) cta_tiles<NPI>(mt, sub * NPI, false);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NPR; c += NBR) cta_tiles<NBR>(mt, sub * NPR + c, true);
+    }
+    __syncthreads();  // every W is complete
+#pragma unroll
+    for (int e = 0; e < E; ++e) w[e] = vact() ? S.W[lane + 32 * e] : make_float2(0.f, 0.f);
+  }
+
   // z = M_d r (z = r without a preconditioner): r is staged in W and each
   // lane reads its block's L entries of it (broadcast) and its row of M_d.
   __device__ __forceinline__ void precond(const float2 (&r)[E], float2 (&z)[E]) {
@@ -344,16 +445,30 @@ struct CgWarp {
     return 0;
   }
 
+  // A system whose group index is out of range: x_hat = 0, labels 0,
+  // rel_res = 0, FPCG_ST_BAD_INDEX (64); no bit errors counted.
+  __device__ void bad_index(int64_t sys) {
+    const int64_t base = sys * (int64_t)KR;
+    for (int k = lane; k < KR; k += 32) {
+      P.x_hat[base + k] = make_float2(0.f, 0.f);
+      if (P.sym) P.sym[base + k] = 0;
+    }
+    if (lane == 0) {
+      if (P.rel_res) P.rel_res[sys] = 0.0;
+      if (P.status) P.status[sys] = 64;
+    }
+  }
+
   // st0: status bits already known for this system (from bj_setup).
   __device__ void detect(int64_t sys, bool valid, int st0) {
     int st = st0;
     // per-system inputs of the output stage, loaded now (their latency hides under the solve)
-    const int64_t base = sys * (int64_t)K;
+    const int64_t base = sys * (int64_t)KR;
     const bool want_sym = valid && (P.sym || P.bit_errors);
     const int M = want_sym ? P.qam[sys] : 0;
     int txv[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) txv[e] = (want_sym && P.tx && vact()) ? P.tx[base + lane + 32 * e] : 0;
+    for (int e = 0; e < E; ++e) txv[e] = (want_sym && P.tx && vout(e)) ? P.tx[base + lane + 32 * e] : 0;
     float* hist = (P.res_hist && valid) ? P.res_hist + sys * (int64_t)(iters + 1) : nullptr;
 
     float2 x[E], d[E], r[E], p[E], z[E], w[E];
@@ -364,7 +479,8 @@ struct CgWarp {
     }
     int pass = 0, it = 0, iters_p = iters, mask = ~0;
     float rho = 0.f, rho_prev = 1.f, rr = 0.f;
-    bool fresh = true;  // r is a new right-hand side: start a pass
+    bool fresh = true;    // r is a new right-hand side: start a pass
+    bool frozen = false;  // NV = 8: this pass broke down; its remaining trips change nothing
 #pragma unroll 1
     while (true) {
       if (!fresh) {
@@ -389,7 +505,12 @@ struct CgWarp {
 #pragma unroll
           for (int e = 0; e < E; ++e) d[e] = make_float2(0.f, 0.f);
           fresh = true;
+          frozen = false;
         } else {
+          if (NV > 1 && frozen) {  // lockstep with the other warps: the trip is taken, nothing changes
+            ++it;
+            continue;
+          }
           float phi, rp;
           dot2(p, w, r, p, phi, rp);
           phi = rip(phi);
@@ -401,7 +522,14 @@ struct CgWarp {
             st |= bad & mask;
             if (hist && lane == 0)
               for (int k = it + 1; k <= iters_p; ++k) hist[k] = hist[it];
-            it = iters_p;
+            if constexpr (NV > 1) {  // the other warps still take this pass's trips
+              frozen = true;
+#pragma unroll
+              for (int e = 0; e < E; ++e) p[e] = make_float2(0.f, 0.f);  // packed from now on: finite
+              ++it;
+            } else {
+              it = iters_p;
+            }
             continue;
           }
           const float alpha = __fdividef(rho_prev, phi);  // within 2 ulp of fl(rho / phi)
@@ -442,6 +570,7 @@ struct CgWarp {
         nb += bv.x * bv.x + bv.y * bv.y;
         const int k = lane + 32 * e;
         if (!(isfinite(x[e].x) && isfinite(x[e].y))) nonfinite = 1;
+        if (!vout(e)) continue;
         P.x_hat[base + k] = x[e];
         if (want_sym) {
           int lab = 0;

@@ -268,6 +268,29 @@ int fpcg_detect_shared(const void* A, const void* H, const void* y, const int32_
     if (e != cudaSuccess) return cuda_fail(e);
   }
   if (n_rhs == 0) return FPCG_OK;
+  if (!force_simt() && tc_prec_ok(prec) && fpcg::solve_tc_supported(k, block_L) && aligned16(A)) {
+    // the tensor-core solver: a warp refills its slot when the block index changes
+    int sms = 0;
+    rc = device_sms(&sms);
+    if (rc) return rc;
+    rc = check_device_smem(fpcg::solve_tc_smem_bytes(k, block_L));
+    if (rc) return rc;
+    fpcg::SolveTcParams T;
+    memset(&T, 0, sizeof(T));
+    cg_params(T.D, qam_order, iters, block_L, prec, prec->refine_iters < 0 ? iters : prec->refine_iters, x_hat,
+              sym_idx, rel_res, nullptr, tx_idx, bit_errors, status);
+    T.A = (const float2*)A;
+    T.H = (const float2*)H;
+    T.y = (const float2*)y;
+    T.a_map = rb_index;
+    T.n = n_rhs;
+    T.n_groups = n_rb;
+    T.N = n_rx;
+    T.K = k;
+    T.gram = prec->gram;
+    cudaError_t e = fpcg::launch_solve_tc(T, sms, prec->mv == FPCG_BF16, s);
+    return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+  }
   rc = check_device_smem(fpcg::simt_smem_bytes(fp64, k, block_L, prec->mv));
   if (rc) return rc;
   fpcg::SimtParams P;

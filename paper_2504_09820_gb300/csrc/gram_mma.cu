@@ -3,7 +3,7 @@
 // cannot address): A = fl(H)^H fl(H) + sigma^2 I, b = fl(H)^H fl(y) (Section II,
 // eq. inversion) with fl = bf16 or fp16 (exact products, fp32 sums).
 //
-// One CTA (8 warps) per system.  The antennas are consumed in chunks of 64:
+// One CTA (8 warps) per system; K = 8 runs as K = 16 with zero rows.  The antennas are consumed in chunks of 64:
 // every thread rounds eight complex entries of H per row to the 16-bit format
 // and stores the real and imaginary parts as rows of Xre, Xim (K x 64,
 // 16-byte chunks swizzled by row), y likewise.  The warps own 16 x 8 tiles of
@@ -56,7 +56,9 @@ __device__ __forceinline__ void ldmatrix_x2(uint32_t& r0, uint32_t& r1, uint32_t
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(saddr) : "memory");
 }
 
-template <int K, bool BF>
+// KR <= K users: rows KR..K-1 of the tiles are zero and not written out
+// (A and b of the KR-user system, row stride KR).
+template <int K, int KR, bool BF>
 __global__ void __launch_bounds__(kThreads) gram_mma_kernel(const GramMmaParams P) {
   constexpr int NT = n_tiles(K);
   constexpr int TPW = (NT + kWarps - 1) / kWarps;  // A tiles per warp
@@ -68,7 +70,7 @@ __global__ void __launch_bounds__(kThreads) gram_mma_kernel(const GramMmaParams 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   const int N = P.N;
-  const float2* Hs = P.H + (size_t)sys * K * N;
+  const float2* Hs = P.H + (size_t)sys * KR * N;
   const float2* yv = P.y + (size_t)sys * N;
 
   // this warp's tiles: list index w + 8i of the (m, n >= 2m) tiles in (m, n) order
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) gram_mma_kernel(const GramMmaParams 
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int n = n0 + 8 * q + j;
-        const float2 h = n < N ? Hs[(size_t)k * N + n] : make_float2(0.f, 0.f);
+        const float2 h = (n < N && k < KR) ? Hs[(size_t)k * N + n] : make_float2(0.f, 0.f);
         re[j] = h.x;
         im[j] = h.y;
       }
@@ -148,42 +150,44 @@ __global__ void __launch_bounds__(kThreads) gram_mma_kernel(const GramMmaParams 
 
   // outputs: upper triangle and its mirror; sigma^2 on the diagonal
   const float s2 = (float)P.sigma2[sys];
-  float2* Ao = P.A + (size_t)sys * K * K;
+  float2* Ao = P.A + (size_t)sys * KR * KR;
 #pragma unroll
   for (int i = 0; i < TPW; ++i) {
     if (tm[i] >= K / 16) continue;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int k = 16 * tm[i] + g + 8 * (q >> 1), l = 8 * tn[i] + 2 * t + (q & 1);
-      if (k > l) continue;
+      if (k > l || l >= KR) continue;
       if (k == l) {
-        Ao[(size_t)k * K + l] = make_float2(are[i][q] + s2, 0.f);
+        Ao[(size_t)k * KR + l] = make_float2(are[i][q] + s2, 0.f);
       } else {
-        Ao[(size_t)k * K + l] = make_float2(are[i][q], aim[i][q]);
-        Ao[(size_t)l * K + k] = make_float2(are[i][q], -aim[i][q]);
+        Ao[(size_t)k * KR + l] = make_float2(are[i][q], aim[i][q]);
+        Ao[(size_t)l * KR + k] = make_float2(are[i][q], -aim[i][q]);
       }
     }
   }
   if (warp < MB && t == 0) {
-    float2* bo = P.b + (size_t)sys * K + 16 * warp;
-    bo[g] = make_float2(bb[0], bb[1]);
-    bo[g + 8] = make_float2(bb[2], bb[3]);
+    float2* bo = P.b + (size_t)sys * KR + 16 * warp;
+    if (16 * warp + g < KR) bo[g] = make_float2(bb[0], bb[1]);
+    if (16 * warp + g + 8 < KR) bo[g + 8] = make_float2(bb[2], bb[3]);
   }
 }
 
-template <int K, bool BF>
+template <int KR, bool BF>
 cudaError_t launch_k(const GramMmaParams& P, cudaStream_t s) {
   if (P.batch <= 0) return cudaSuccess;
-  gram_mma_kernel<K, BF><<<(unsigned)P.batch, kThreads, 0, s>>>(P);
+  gram_mma_kernel<(KR < 16 ? 16 : KR), KR, BF><<<(unsigned)P.batch, kThreads, 0, s>>>(P);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool gram_mma_supported(int K) { return K == 16 || K == 32 || K == 64 || K == 128; }
+bool gram_mma_supported(int K) { return K == 8 || K == 16 || K == 32 || K == 64 || K == 128; }
 
 cudaError_t launch_gram_mma(const GramMmaParams& P, int bf16, cudaStream_t s) {
   switch (P.K * 2 + (bf16 ? 1 : 0)) {
+    case 16: return launch_k<8, false>(P, s);
+    case 17: return launch_k<8, true>(P, s);
     case 32: return launch_k<16, false>(P, s);
     case 33: return launch_k<16, true>(P, s);
     case 64: return launch_k<32, false>(P, s);

@@ -16,7 +16,7 @@ struct GramMmaParams {
   int64_t batch;
 };
 
-bool gram_mma_supported(int K);  // K in {16, 32, 64, 128}
+bool gram_mma_supported(int K);  // K in {8, 16, 32, 64, 128} (8: padded to 16)
 cudaError_t launch_gram_mma(const GramMmaParams& P, int bf16, cudaStream_t stream);
 
 }  // namespace fpcg

@@ -2,7 +2,7 @@
 // b_s = fl(H_g)^H fl(y_s) (Section II, eq. inversion) for all vectors s of a
 // group g at once, a (2K x N) x (N x 2 n_g) product per group.
 //
-// One CTA (8 warps) per group.  The group's vectors are taken 32 at a time;
+// One CTA (8 warps) per group; K = 8 runs as K = 16 with zero rows.  The group's vectors are taken 32 at a time;
 // for each batch the antennas are consumed in chunks of 64: H rows as Re h_k
 // and Im h_k (16-bit, like the Gram), and the batch's y as rows
 // (Re y_0, Im y_0, Re y_1, Im y_1, ...) and (Im y_0, -Re y_0, ...).  The warps
@@ -48,7 +48,8 @@ __device__ __forceinline__ void ldmatrix_x2(uint32_t& r0, uint32_t& r1, uint32_t
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(saddr) : "memory");
 }
 
-template <int K, bool BF>
+// KR <= K users: rows KR..K-1 of the tile are zero and not written out.
+template <int K, int KR, bool BF>
 __global__ void __launch_bounds__(kThreads) mf_mma_kernel(const MfMmaParams P) {
   constexpr int MTL = K / 16;                  // m-tiles (16 users)
   constexpr int NTL = 2 * kBatch / 8;          // n-tiles (4 vectors, re and im)
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(kThreads) mf_mma_kernel(const MfMmaParams P) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gq = lane >> 2, t = lane & 3;
   const int N = P.N;
-  const float2* Hg = P.H + (size_t)g * K * N;
+  const float2* Hg = P.H + (size_t)g * KR * N;
   const uint32_t bre = tc::smem_u32(Xre), bim = tc::smem_u32(Xim), by1 = tc::smem_u32(Y1), by2 = tc::smem_u32(Y2);
   const int lr = lane & 15, lc = lane >> 4, lb = lane & 7, lh = (lane >> 3) & 1;
 
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(kThreads) mf_mma_kernel(const MfMmaParams P) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int n = n0 + 8 * q + j;
-          const float2 h = n < N ? Hg[(size_t)k * N + n] : make_float2(0.f, 0.f);
+          const float2 h = (n < N && k < KR) ? Hg[(size_t)k * N + n] : make_float2(0.f, 0.f);
           re[j] = h.x;
           im[j] = h.y;
         }
@@ -133,27 +134,30 @@ __global__ void __launch_bounds__(kThreads) mf_mma_kernel(const MfMmaParams P) {
       const int tile = warp * TPW + i, mt = tile / NTL, nt = tile % NTL;
       const int v = 4 * nt + t;
       if (v < nb) {
-        float2* bo = P.b + (size_t)(s0 + v) * K + 16 * mt + gq;
-        bo[0] = make_float2(acc[i][0], acc[i][1]);
-        bo[8] = make_float2(acc[i][2], acc[i][3]);
+        const int k = 16 * mt + gq;
+        float2* bo = P.b + (size_t)(s0 + v) * KR + k;
+        if (k < KR) bo[0] = make_float2(acc[i][0], acc[i][1]);
+        if (k + 8 < KR) bo[8] = make_float2(acc[i][2], acc[i][3]);
       }
     }
   }
 }
 
-template <int K, bool BF>
+template <int KR, bool BF>
 cudaError_t launch_k(const MfMmaParams& P, cudaStream_t s) {
   if (P.n_groups <= 0) return cudaSuccess;
-  mf_mma_kernel<K, BF><<<(unsigned)P.n_groups, kThreads, 0, s>>>(P);
+  mf_mma_kernel<(KR < 16 ? 16 : KR), KR, BF><<<(unsigned)P.n_groups, kThreads, 0, s>>>(P);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool mf_mma_supported(int K) { return K == 16 || K == 32 || K == 64 || K == 128; }
+bool mf_mma_supported(int K) { return K == 8 || K == 16 || K == 32 || K == 64 || K == 128; }
 
 cudaError_t launch_mf_mma(const MfMmaParams& P, int bf16, cudaStream_t s) {
   switch (P.K * 2 + (bf16 ? 1 : 0)) {
+    case 16: return launch_k<8, false>(P, s);
+    case 17: return launch_k<8, true>(P, s);
     case 32: return launch_k<16, false>(P, s);
     case 33: return launch_k<16, true>(P, s);
     case 64: return launch_k<32, false>(P, s);

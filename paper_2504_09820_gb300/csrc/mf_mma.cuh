@@ -15,7 +15,7 @@ struct MfMmaParams {
   int64_t n_groups;
 };
 
-bool mf_mma_supported(int K);  // K in {16, 32, 64, 128}
+bool mf_mma_supported(int K);  // K in {8, 16, 32, 64, 128} (8: padded to 16)
 cudaError_t launch_mf_mma(const MfMmaParams& P, int bf16, cudaStream_t stream);
 
 }  // namespace fpcg

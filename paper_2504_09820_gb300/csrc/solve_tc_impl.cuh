@@ -1,6 +1,7 @@
 #pragma once
 // Tensor-core solver for given Gram matrices (kernel templates; instantiated
-// per K by solve_tc_k{16,32,64}.cu).  The CG of the fused detector without its
+// per K by solve_tc_k{8,16,32,64,128}.cu; K = 8 runs in 16-wide slots holding
+// diag(A, I)).  The CG of the fused detector without its
 // Gram pipeline: A + sigma^2 I comes from global memory (fpcg_gram's output, or
 // the caller's), every warp of a persistent CTA is an independent CG worker
 // with its own shared-memory slot, and systems that share a Gram matrix share
@@ -23,20 +24,26 @@
 namespace fpcg {
 namespace {
 
-// Round the group's A into the slot: 16-bit [Re A; Im A] chunks of 8 columns,
-// and the fp32 diagonal blocks.
-template <int K, bool BF, int LT>
-__device__ void fill_slot_A(const float2* Ag, const Slot& S, int lane) {
+// Round the group's A (KR x KR, row stride KR) into the slot: 16-bit
+// [Re A; Im A] chunks of 8 columns and the fp32 diagonal blocks; rows and
+// columns KR..K-1 are those of the identity.  Threads tid, tid + nt, ...
+template <int K, int KR, bool BF, int LT>
+__device__ __forceinline__ void fill_A(const float2* Ag, const Slot& S, int tid, int nt) {
   constexpr int CPR = K / 8;
-  for (int idx = lane; idx < K * CPR; idx += 32) {
+  for (int idx = tid; idx < K * CPR; idx += nt) {
     const int k = idx / CPR, c = idx % CPR;
-    const float4* src = reinterpret_cast<const float4*>(Ag + (size_t)k * K + 8 * c);
     float2 a[8];
+    if (KR == K || (k < KR && 8 * c < KR)) {
+      const float4* src = reinterpret_cast<const float4*>(Ag + (size_t)k * KR + 8 * c);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float4 v = __ldg(src + q);
-      a[2 * q] = make_float2(v.x, v.y);
-      a[2 * q + 1] = make_float2(v.z, v.w);
+      for (int q = 0; q < 4; ++q) {
+        const float4 v = __ldg(src + q);
+        a[2 * q] = make_float2(v.x, v.y);
+        a[2 * q + 1] = make_float2(v.z, v.w);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) a[m] = make_float2(k == 8 * c + m ? 1.f : 0.f, 0.f);
     }
     uint4 re, im;
     re.x = pk2<BF>(a[0].x, a[1].x);
@@ -59,13 +66,24 @@ __device__ void fill_slot_A(const float2* Ag, const Slot& S, int lane) {
       }
     }
   }
+}
+
+// b of system s (KR entries, given) into the slot, zeros beyond KR.  Plain
+// loads: b may share memory with x_hat, which this kernel writes.
+template <int K, int KR>
+__device__ __forceinline__ void load_b(const float2* bs, const Slot& S, int lane) {
+  for (int i = lane; i < K / 2; i += 32)  // two complex entries per float4
+    reinterpret_cast<float4*>(S.b)[i] =
+        (KR == K || 2 * i < KR) ? reinterpret_cast<const float4*>(bs)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
 }
 
-// b = fl(H)^H fl(y) for one system into S.b (rounding of the Gram step).
-template <int K>
+// b = fl(H)^H fl(y) for one system into S.b (rounding of the Gram step); H
+// has KR rows, entries KR..K-1 of b are zero.
+template <int K, int KR>
 __device__ void matched_filter(const float2* Hg, const float2* ys, int N, int gram, const Slot& S, int lane) {
-  for (int k0 = 0; k0 < K; k0 += 4) {
+  for (int k = KR + lane; k < K; k += 32) S.b[k] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < KR; k0 += 4) {
     float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
     for (int n = lane; n < N; n += 32) {
       const float2 yy = ys[n];
@@ -99,14 +117,15 @@ __device__ void matched_filter(const float2* Hg, const float2* ys, int N, int gr
   __syncwarp();
 }
 
-template <int K, bool BF, int LT>
-__global__ void __launch_bounds__(solve_warps(K) * 32, 1) solve_tc_kernel(const __grid_constant__ SolveTcParams P) {
-  constexpr int NW = solve_warps(K);
+template <int KR, bool BF, int LT>
+__global__ void __launch_bounds__(solve_warps(KR) * 32, 1) solve_tc_kernel(const __grid_constant__ SolveTcParams P) {
+  constexpr int K = pad_k(KR);
+  constexpr int NW = solve_warps(KR);
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
   const Slot S = slot_carve(base + warp * tc_slot_bytes(K, LT), K, LT);
-  CgWarp<K, BF, LT> W(P.D, S, lane);
+  CgWarp<K, BF, LT, KR> W(P.D, S, lane);
   const int64_t tw = (int64_t)gridDim.x * NW, gw = (int64_t)blockIdx.x * NW + warp;
   const int64_t chunk = (P.n + tw - 1) / tw;
   const int64_t s0 = gw * chunk, s1 = min(P.n, s0 + chunk);
@@ -131,21 +150,24 @@ __global__ void __launch_bounds__(solve_warps(K) * 32, 1) solve_tc_kernel(const 
         ++g;
         g_end = P.group_start[g + 1];
       }
+    } else if (P.a_map) {
+      const int32_t gi = P.a_map[s];
+      if (gi < 0 || gi >= P.n_groups) {  // x_hat = 0, labels 0, status only
+        W.bad_index(s);
+        continue;
+      }
+      g = gi;
     } else {
       g = s;
     }
     if (g != cur) {
-      fill_slot_A<K, BF, LT>(P.A + (size_t)g * K * K, S, lane);
+      fill_A<K, KR, BF, LT>(P.A + (size_t)g * KR * KR, S, lane, 32);
+      __syncwarp();
       st_bj = W.bj_setup();
       cur = g;
     }
-    if (P.b) {
-      for (int i = lane; i < K / 2; i += 32)  // two complex entries per float4
-        reinterpret_cast<float4*>(S.b)[i] = __ldg(reinterpret_cast<const float4*>(P.b + (size_t)s * K) + i);
-      __syncwarp();
-    } else {
-      matched_filter<K>(P.H + (size_t)g * K * P.N, P.y + (size_t)s * P.N, P.N, P.gram, S, lane);
-    }
+    if (P.b) load_b<K, KR>(P.b + (size_t)s * KR, S, lane);
+    else matched_filter<K, KR>(P.H + (size_t)g * KR * P.N, P.y + (size_t)s * P.N, P.N, P.gram, S, lane);
     W.detect(s, true, st_bj);
     __syncwarp();
   }
@@ -153,63 +175,38 @@ __global__ void __launch_bounds__(solve_warps(K) * 32, 1) solve_tc_kernel(const 
 
 // Grouped mode: CTA c takes groups c, c + gridDim.x, ...; for each, all its
 // threads round the group's A into the shared slot, warps 0..K/32-1 invert the
-// diagonal blocks (one block column per lane), and the warps take the group's
-// received vectors round-robin: their b (given, or the matched filter formed
-// here), then detect.  A given b may share memory with x_hat: a vector's b is
-// read before its x_hat is written, by the same warp.
-template <int K, bool BF, int LT>
+// diagonal blocks (one block column per lane), and the eight warps take the
+// group's received vectors eight at a time (warp w: vector 8i + w): their b
+// (given, or the matched filter formed here), then detect in lockstep, every
+// product with A one CTA-wide product for the eight vectors (CgWarp NV = 8).
+// A warp without a vector in the last round runs on b = 0 and writes nothing.
+// A given b may share memory with x_hat: a vector's b is read before its
+// x_hat is written, by the same warp.
+template <int KR, bool BF, int LT>
 __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_grouped_kernel(const __grid_constant__ SolveTcParams P) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  constexpr int CPR = K / 8;
+  constexpr int K = pad_k(KR);
   constexpr int NT = kSolveWarps * 32;
+  constexpr int VST = grouped_vec_bytes(K);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
   Slot S;
   S.A16 = base;
   S.Md = reinterpret_cast<float2*>(base + 4 * K * K);
-  uint8_t* scratch = base + 4 * K * K + md_bytes(K, LT);
-  uint8_t* mine = scratch + (size_t)warp * (16 * K + 12 * K);
-  S.b = reinterpret_cast<float2*>(mine);
-  S.W = reinterpret_cast<float2*>(mine + 8 * K);
-  S.Pk = reinterpret_cast<uint32_t*>(mine + 16 * K);
-  volatile int* flag = reinterpret_cast<volatile int*>(scratch + (size_t)kSolveWarps * (16 * K + 12 * K));
-  CgWarp<K, BF, LT> W(P.D, S, lane);
+  uint8_t* vbase = base + 4 * K * K + md_bytes(K, LT);
+  S.b = reinterpret_cast<float2*>(vbase + warp * VST);
+  S.W = reinterpret_cast<float2*>(vbase + warp * VST + 8 * K);
+  S.Pk = reinterpret_cast<uint32_t*>(vbase + kSolveWarps * VST);
+  volatile int* flag = reinterpret_cast<volatile int*>(vbase + kSolveWarps * VST + grouped_pk_bytes(K));
+  CgWarp<K, BF, LT, KR, kSolveWarps> W(P.D, S, lane);
+  W.vw = warp;
+  W.vbase = vbase;
+  W.vst = VST;
   for (int64_t g = blockIdx.x; g < P.n_groups; g += gridDim.x) {
     const int64_t s0 = P.group_start[g], s1 = P.group_start[g + 1];
     if (s1 <= s0) continue;
     __syncthreads();  // the previous group's vectors are done with the slot
-    const float2* Ag = P.A + (size_t)g * K * K;
-    for (int idx = threadIdx.x; idx < K * CPR; idx += NT) {  // A -> [Re A; Im A] 16-bit, diagonal blocks fp32
-      const int k = idx / CPR, c = idx % CPR;
-      const float4* src = reinterpret_cast<const float4*>(Ag + (size_t)k * K + 8 * c);
-      float2 a[8];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 v = __ldg(src + q);
-        a[2 * q] = make_float2(v.x, v.y);
-        a[2 * q + 1] = make_float2(v.z, v.w);
-      }
-      uint4 re, im;
-      re.x = pk2<BF>(a[0].x, a[1].x);
-      re.y = pk2<BF>(a[2].x, a[3].x);
-      re.z = pk2<BF>(a[4].x, a[5].x);
-      re.w = pk2<BF>(a[6].x, a[7].x);
-      im.x = pk2<BF>(a[0].y, a[1].y);
-      im.y = pk2<BF>(a[2].y, a[3].y);
-      im.z = pk2<BF>(a[4].y, a[5].y);
-      im.w = pk2<BF>(a[6].y, a[7].y);
-      *reinterpret_cast<uint4*>(S.A16 + a16_offset<K>(k, c)) = re;
-      *reinterpret_cast<uint4*>(S.A16 + a16_offset<K>(K + k, c)) = im;
-      if constexpr (LT > 0) {
-        constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
-        const int kb0 = (k / LT) * LT;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int l = 8 * c + m;
-          if (l >= kb0 && l < kb0 + LT) S.Md[(k / LT) * MBS + (k % LT) * MLD + (l - kb0)] = a[m];
-        }
-      }
-    }
+    fill_A<K, KR, BF, LT>(P.A + (size_t)g * KR * KR, S, threadIdx.x, NT);  // A -> [Re A; Im A], blocks
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     int st0 = 0;
@@ -225,15 +222,17 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_grouped_kernel(cons
       }
       __syncthreads();
     }
-    for (int64_t s = s0 + warp; s < s1; s += kSolveWarps) {
-      if (P.b) {  // formed beforehand for the whole group (mf_mma)
-        for (int i = lane; i < K / 2; i += 32)
-          reinterpret_cast<float4*>(S.b)[i] = reinterpret_cast<const float4*>(P.b + (size_t)s * K)[i];
+    for (int64_t s = s0 + warp; s - warp < s1; s += kSolveWarps) {  // the same rounds on every warp
+      const bool valid = s < s1;
+      if (!valid) {
+        for (int k = lane; k < K; k += 32) S.b[k] = make_float2(0.f, 0.f);
         __syncwarp();
+      } else if (P.b) {
+        load_b<K, KR>(P.b + (size_t)s * KR, S, lane);  // formed beforehand for the whole group (mf_mma)
       } else {
-        matched_filter<K>(P.H + (size_t)g * K * P.N, P.y + (size_t)s * P.N, P.N, P.gram, S, lane);
+        matched_filter<K, KR>(P.H + (size_t)g * KR * P.N, P.y + (size_t)s * P.N, P.N, P.gram, S, lane);
       }
-      W.detect(s, true, st0);
+      W.detect(s, valid, st0);
       __syncwarp();
     }
   }
@@ -286,8 +285,8 @@ cudaError_t launch_solve_grouped_k(const SolveTcParams& P, int num_sms, int mv_b
     case 9: return launch_g<K, true, 4>(P, num_sms, stream);
     case 16: return launch_g<K, false, 8>(P, num_sms, stream);
     case 17: return launch_g<K, true, 8>(P, num_sms, stream);
-    case 32: return launch_g<K, false, 16>(P, num_sms, stream);
-    case 33: return launch_g<K, true, 16>(P, num_sms, stream);
+    case 32: if constexpr (K >= 16) return launch_g<K, false, 16>(P, num_sms, stream); else return cudaErrorInvalidValue;
+    case 33: if constexpr (K >= 16) return launch_g<K, true, 16>(P, num_sms, stream); else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
@@ -301,8 +300,8 @@ cudaError_t launch_solve_tc_k(const SolveTcParams& P, int num_sms, int mv_bf16, 
     case 9: return launch_s<K, true, 4>(P, num_sms, stream);
     case 16: return launch_s<K, false, 8>(P, num_sms, stream);
     case 17: return launch_s<K, true, 8>(P, num_sms, stream);
-    case 32: return launch_s<K, false, 16>(P, num_sms, stream);
-    case 33: return launch_s<K, true, 16>(P, num_sms, stream);
+    case 32: if constexpr (K >= 16) return launch_s<K, false, 16>(P, num_sms, stream); else return cudaErrorInvalidValue;
+    case 33: if constexpr (K >= 16) return launch_s<K, true, 16>(P, num_sms, stream); else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

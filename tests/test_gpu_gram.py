@@ -75,7 +75,7 @@ def test_gram_simt_fallbacks():
     assert np.abs(A - Ar).max() < 1e-12 and np.abs(b - br).max() < 1e-12
 
 
-@pytest.mark.parametrize("K,N", [(128, 512), (128, 256), (128, 130), (64, 255), (32, 97), (16, 33)])
+@pytest.mark.parametrize("K,N", [(128, 512), (128, 256), (128, 130), (64, 255), (32, 97), (16, 33), (8, 33), (8, 9)])
 @pytest.mark.parametrize("gram", ["bf16", "fp16"])
 def test_mma_gram(K, N, gram):
     """The mma.sync Gram (K = 128, or odd N the TMA pipeline cannot address):

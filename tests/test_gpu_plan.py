@@ -106,8 +106,7 @@ def test_autotune_keeps_results(mixed):
     tuned = _run(p, g, autotune=True)
     cls = p.classes()
     assert all(c["path"] in (F.PATH_SIMT, F.PATH_TENSOR_CORE, F.PATH_TWO_PASS) for c in cls)
-    assert all(c["path"] == F.PATH_SIMT for c in cls if c["k"] == 8)
-    assert all(c["path"] in (F.PATH_SIMT, F.PATH_TWO_PASS) for c in cls if c["k"] == 128)
+    assert all(c["path"] in (F.PATH_SIMT, F.PATH_TWO_PASS) for c in cls if c["k"] in (8, 128))
     # same algorithm on either kernel: within the sum of both kernels' parity bounds
     xb = p.unpack(base["x"], d["k"])
     xt = p.unpack(tuned["x"], d["k"])
@@ -116,13 +115,13 @@ def test_autotune_keeps_results(mixed):
 
 
 def test_two_pass_class_equals_gram_then_solve(mixed):
-    """A two-pass class (K = 128) gives exactly fpcg_gram + fpcg_solve_gram + slicing
-    on its systems."""
+    """A two-pass class (K = 8 or 128) gives exactly fpcg_gram + fpcg_solve_gram +
+    slicing on its systems."""
     d, p, g = mixed
     out = _run(p, g)
     x = p.unpack(out["x"], d["k"])
     two = [c for c in p.classes() if c["path"] == F.PATH_TWO_PASS]
-    assert two
+    assert {c["k"] for c in two} == {8, 128}
     for c in two:
         idx = np.sort(p.order[c["first"]:c["first"] + c["count"]])
         cd = _class_data(d, idx)

@@ -36,7 +36,7 @@ def test_layout_invariants():
         for off, step in ((p.h_off, c["n_rx"] * c["k"]), (p.y_off, c["n_rx"]), (p.x_off, c["k"])):
             assert off[pos[0]] % 32 == 0
             assert np.all(np.diff(off[pos]) == step)
-        want = {16: F.PATH_TENSOR_CORE, 32: F.PATH_TENSOR_CORE, 64: F.PATH_TENSOR_CORE,
+        want = {8: F.PATH_TWO_PASS, 16: F.PATH_TENSOR_CORE, 32: F.PATH_TENSOR_CORE, 64: F.PATH_TENSOR_CORE,
                 128: F.PATH_TWO_PASS}.get(c["k"], F.PATH_SIMT)
         assert c["path"] == want
     # classes do not overlap and fit in the totals
