@@ -371,7 +371,7 @@ struct CgWarp {
     constexpr int WPM = 8 / MT;                 // warps per m-tile
     constexpr int NPI = WPM >= 2 ? 1 : 2;       // iteration n-tiles per warp
     constexpr int NPR = 8 / WPM;                // residual n-tiles per warp
-    constexpr int NBR = NPR > 4 ? 4 : NPR;      // residual n-tiles per pass over A
+    constexpr int NBR = NPR > 2 ? 2 : NPR;      // residual n-tiles per pass over A (registers)
     const int mt = vw / WPM, sub = vw % WPM;
     __syncthreads();  // every vector is packed
     if (!res) {

@@ -3,7 +3,8 @@
 // cannot address): A = fl(H)^H fl(H) + sigma^2 I, b = fl(H)^H fl(y) (Section II,
 // eq. inversion) with fl = bf16 or fp16 (exact products, fp32 sums).
 //
-// One CTA (8 warps) per system; K = 8 runs as K = 16 with zero rows.  The antennas are consumed in chunks of 64:
+// One CTA per system (16 warps for K = 128, else 8); K = 8 runs as K = 16 with
+// zero rows.  The antennas are consumed in chunks of 64:
 // every thread rounds eight complex entries of H per row to the 16-bit format
 // and stores the real and imaginary parts as rows of Xre, Xim (K x 64,
 // 16-byte chunks swizzled by row), y likewise.  The warps own 16 x 8 tiles of
@@ -23,9 +24,10 @@
 namespace fpcg {
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
 constexpr int kChunk = 64;  // antennas per stage
+
+// 16 warps for K = 128 (72 tiles), 8 otherwise.
+__host__ __device__ constexpr int gram_warps(int K) { return K >= 128 ? 16 : 8; }
 
 __host__ __device__ constexpr int n_tiles(int K) {  // tiles (m, n) with n >= 2m
   return (K / 16) * (K / 8) - (K / 16) * (K / 16 - 1);
@@ -58,11 +60,19 @@ __device__ __forceinline__ void ldmatrix_x2(uint32_t& r0, uint32_t& r1, uint32_t
 
 // KR <= K users: rows KR..K-1 of the tiles are zero and not written out
 // (A and b of the KR-user system, row stride KR).
+//
+// Software pipeline: every thread holds its share of the next chunk of H (and
+// of y) in registers while the warps multiply the current chunk, so the DRAM
+// latency of chunk c+1 hides under the products of chunk c.
 template <int K, int KR, bool BF>
-__global__ void __launch_bounds__(kThreads) gram_mma_kernel(const GramMmaParams P) {
+__global__ void __launch_bounds__(gram_warps(K) * 32, K >= 128 ? 1 : 2) gram_mma_kernel(const GramMmaParams P) {
+  constexpr int NW = gram_warps(K);
+  constexpr int NTH = NW * 32;
   constexpr int NT = n_tiles(K);
-  constexpr int TPW = (NT + kWarps - 1) / kWarps;  // A tiles per warp
-  constexpr int MB = K / 16;                       // b tiles
+  constexpr int TPW = (NT + NW - 1) / NW;    // A tiles per warp
+  constexpr int MB = K / 16;                 // b tiles (on the last MB warps)
+  constexpr int ITEMS = K * (kChunk / 8);    // 8-antenna pieces of H rows per chunk
+  constexpr int IPT = (ITEMS + NTH - 1) / NTH;
   __shared__ __align__(128) uint8_t Xre[K * 128];
   __shared__ __align__(128) uint8_t Xim[K * 128];
   __shared__ __align__(16) uint32_t ys[2][kChunk / 2];  // 16-bit pairs of Re y, Im y
@@ -73,11 +83,11 @@ __global__ void __launch_bounds__(kThreads) gram_mma_kernel(const GramMmaParams 
   const float2* Hs = P.H + (size_t)sys * KR * N;
   const float2* yv = P.y + (size_t)sys * N;
 
-  // this warp's tiles: list index w + 8i of the (m, n >= 2m) tiles in (m, n) order
+  // this warp's tiles: list index w + NW i of the (m, n >= 2m) tiles in (m, n) order
   int tm[TPW], tn[TPW];
 #pragma unroll
   for (int i = 0; i < TPW; ++i) {
-    int idx = warp + kWarps * i, m = 0;
+    int idx = warp + NW * i, m = 0;
     while (m < K / 16 && idx >= K / 8 - 2 * m) {
       idx -= K / 8 - 2 * m;
       ++m;
@@ -85,6 +95,7 @@ __global__ void __launch_bounds__(kThreads) gram_mma_kernel(const GramMmaParams 
     tm[i] = m;  // m == K/16: no tile
     tn[i] = 2 * m + idx;
   }
+  const int bm = NW - 1 - warp;  // b tile of this warp (if < MB)
   float are[TPW][4], aim[TPW][4], bb[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < TPW; ++i)
@@ -94,30 +105,60 @@ __global__ void __launch_bounds__(kThreads) gram_mma_kernel(const GramMmaParams 
   const int lr = lane & 15, lc = lane >> 4;  // ldmatrix.x4 row / chunk half
   const int lb = lane & 7, lh = (lane >> 3) & 1;  // ldmatrix.x2
 
+  // 16-byte loads where every row starts 16-byte aligned
+  const bool vec = (reinterpret_cast<uintptr_t>(P.H) & 15) == 0 && (N & 1) == 0;
+  float2 hp[IPT][8], yp[2];
+  auto load = [&](int n0) {
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      const int it = threadIdx.x + NTH * u;
+      const int k = it / (kChunk / 8), q = it % (kChunk / 8);
+      if (vec && it < ITEMS && k < KR && n0 + 8 * q + 8 <= N) {  // four 16-byte loads
+        const float4* src = reinterpret_cast<const float4*>(Hs + (size_t)k * N + n0 + 8 * q);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 v = src[j];
+          hp[u][2 * j] = make_float2(v.x, v.y);
+          hp[u][2 * j + 1] = make_float2(v.z, v.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int n = n0 + 8 * q + j;
+          hp[u][j] = (it < ITEMS && k < KR && n < N) ? Hs[(size_t)k * N + n] : make_float2(0.f, 0.f);
+        }
+      }
+    }
+    if (threadIdx.x < kChunk / 2) {
+      const int n = n0 + 2 * threadIdx.x;
+      yp[0] = n < N ? yv[n] : make_float2(0.f, 0.f);
+      yp[1] = n + 1 < N ? yv[n + 1] : make_float2(0.f, 0.f);
+    }
+  };
+  load(0);
+
   for (int n0 = 0; n0 < N; n0 += kChunk) {
     __syncthreads();  // the previous chunk is consumed
-    for (int it = threadIdx.x; it < K * (kChunk / 8); it += kThreads) {
-      const int k = it / (kChunk / 8), q = it % (kChunk / 8);
-      float re[8], im[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int n = n0 + 8 * q + j;
-        const float2 h = (n < N && k < KR) ? Hs[(size_t)k * N + n] : make_float2(0.f, 0.f);
-        re[j] = h.x;
-        im[j] = h.y;
+    for (int u = 0; u < IPT; ++u) {
+      const int it = threadIdx.x + NTH * u;
+      if (it < ITEMS) {
+        const int k = it / (kChunk / 8), q = it % (kChunk / 8);
+        const float2* h = hp[u];
+        *reinterpret_cast<uint4*>(Xre + x_off<K>(k, q)) =
+            make_uint4(pack16<BF>(h[0].x, h[1].x), pack16<BF>(h[2].x, h[3].x), pack16<BF>(h[4].x, h[5].x),
+                       pack16<BF>(h[6].x, h[7].x));
+        *reinterpret_cast<uint4*>(Xim + x_off<K>(k, q)) =
+            make_uint4(pack16<BF>(h[0].y, h[1].y), pack16<BF>(h[2].y, h[3].y), pack16<BF>(h[4].y, h[5].y),
+                       pack16<BF>(h[6].y, h[7].y));
       }
-      *reinterpret_cast<uint4*>(Xre + x_off<K>(k, q)) =
-          make_uint4(pack16<BF>(re[0], re[1]), pack16<BF>(re[2], re[3]), pack16<BF>(re[4], re[5]), pack16<BF>(re[6], re[7]));
-      *reinterpret_cast<uint4*>(Xim + x_off<K>(k, q)) =
-          make_uint4(pack16<BF>(im[0], im[1]), pack16<BF>(im[2], im[3]), pack16<BF>(im[4], im[5]), pack16<BF>(im[6], im[7]));
     }
-    for (int j = threadIdx.x; j < kChunk / 2; j += kThreads) {
-      const int n = n0 + 2 * j;
-      const float2 a = n < N ? yv[n] : make_float2(0.f, 0.f), c = n + 1 < N ? yv[n + 1] : make_float2(0.f, 0.f);
-      ys[0][j] = pack16<BF>(a.x, c.x);
-      ys[1][j] = pack16<BF>(a.y, c.y);
+    if (threadIdx.x < kChunk / 2) {
+      ys[0][threadIdx.x] = pack16<BF>(yp[0].x, yp[1].x);
+      ys[1][threadIdx.x] = pack16<BF>(yp[0].y, yp[1].y);
     }
     __syncthreads();
+    if (n0 + kChunk < N) load(n0 + kChunk);  // in flight during the products below
 #pragma unroll
     for (int ks = 0; ks < kChunk / 16; ++ks) {
 #pragma unroll
@@ -133,10 +174,10 @@ __global__ void __launch_bounds__(kThreads) gram_mma_kernel(const GramMmaParams 
         mma<BF>(aim[i], ar, i0, i1);
         mma<BF>(aim[i], ai, r0 ^ 0x80008000u, r1 ^ 0x80008000u);
       }
-      if (warp < MB) {  // b tile m = warp: columns (Re y, Im y) against Xre, (Im y, -Re y) against Xim
+      if (bm < MB) {  // b tile bm: columns (Re y, Im y) against Xre, (Im y, -Re y) against Xim
         uint32_t ar[4], ai[4];
-        tc::ldmatrix_x4(ar, bre + x_off<K>(16 * warp + lr, 2 * ks + lc));
-        tc::ldmatrix_x4(ai, bim + x_off<K>(16 * warp + lr, 2 * ks + lc));
+        tc::ldmatrix_x4(ar, bre + x_off<K>(16 * bm + lr, 2 * ks + lc));
+        tc::ldmatrix_x4(ai, bim + x_off<K>(16 * bm + lr, 2 * ks + lc));
         const int w0 = 8 * ks + t, w1 = 8 * ks + 4 + t;  // 16-bit pair index of antennas 16ks+2t, +8
         const uint32_t yr0 = ys[0][w0], yr1 = ys[0][w1], yi0 = ys[1][w0], yi1 = ys[1][w1];
         const uint32_t b0 = g == 0 ? yr0 : g == 1 ? yi0 : 0u, b1 = g == 0 ? yr1 : g == 1 ? yi1 : 0u;
@@ -166,17 +207,18 @@ __global__ void __launch_bounds__(kThreads) gram_mma_kernel(const GramMmaParams 
       }
     }
   }
-  if (warp < MB && t == 0) {
-    float2* bo = P.b + (size_t)sys * KR + 16 * warp;
-    if (16 * warp + g < KR) bo[g] = make_float2(bb[0], bb[1]);
-    if (16 * warp + g + 8 < KR) bo[g + 8] = make_float2(bb[2], bb[3]);
+  if (bm < MB && t == 0) {
+    float2* bo = P.b + (size_t)sys * KR + 16 * bm;
+    if (16 * bm + g < KR) bo[g] = make_float2(bb[0], bb[1]);
+    if (16 * bm + g + 8 < KR) bo[g + 8] = make_float2(bb[2], bb[3]);
   }
 }
 
 template <int KR, bool BF>
 cudaError_t launch_k(const GramMmaParams& P, cudaStream_t s) {
   if (P.batch <= 0) return cudaSuccess;
-  gram_mma_kernel<(KR < 16 ? 16 : KR), KR, BF><<<(unsigned)P.batch, kThreads, 0, s>>>(P);
+  constexpr int K = KR < 16 ? 16 : KR;
+  gram_mma_kernel<K, KR, BF><<<(unsigned)P.batch, gram_warps(K) * 32, 0, s>>>(P);
   return cudaGetLastError();
 }
 

@@ -6,7 +6,8 @@
 // own allocator owns the device memory.  fpcg_detect and fpbjcg_detect already
 // allocate nothing; the configurations that need scratch memory are the
 // two-pass ones (the Gram matrices are formed first, then the systems are
-// solved from them: K = 128), for which plans keep workspace of their own.
+// solved from them: K = 8 and K = 128), for which plans keep workspace of
+// their own.
 // This entry point gives those callers the two-pass path with its scratch in
 // one fixed, file-scope device array instead.
 #include <cuda_runtime.h>

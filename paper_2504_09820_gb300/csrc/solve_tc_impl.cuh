@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(solve_warps(KR) * 32, 1) solve_tc_kernel(const
 // A given b may share memory with x_hat: a vector's b is read before its
 // x_hat is written, by the same warp.
 template <int KR, bool BF, int LT>
-__global__ void __launch_bounds__(kSolveWarps * 32, 1) solve_grouped_kernel(const __grid_constant__ SolveTcParams P) {
+__global__ void __launch_bounds__(kSolveWarps * 32, 2) solve_grouped_kernel(const __grid_constant__ SolveTcParams P) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   constexpr int K = pad_k(KR);
   constexpr int NT = kSolveWarps * 32;
