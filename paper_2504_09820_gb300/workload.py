@@ -79,10 +79,14 @@ class Spec:
     seed: int = 1000
     noiseless: bool = False   # y = H x exactly (sigma^2 still reported)
     rho_t: float = field(default=None)  # override for the user side, if given
+    n_ue: int = 1             # antennas per user (K = users x n_ue streams)
+    rt_block: bool = False    # Assumption 1: no correlation between different users' antennas
 
     def __post_init__(self):
         if self.rho_t is None:
             self.rho_t = self.rho
+        if self.K % self.n_ue:
+            raise ValueError("K must be a multiple of the antennas per user")
 
 
 def _chunk(spec, c, Rr, Rt):
@@ -110,6 +114,19 @@ def _chunk(spec, c, Rr, Rt):
     return H_store, yc.astype(np.complex64), tx, x
 
 
+def user_corr(spec):
+    """R_t of a Spec: the exponential matrix of eq. (2) over all K streams, or,
+    with rt_block (Section IV-B, Assumption 1), block-diagonal with one
+    n_ue x n_ue exponential block per user and zero blocks between users."""
+    if not spec.rt_block:
+        return exp_corr(spec.K, spec.rho_t)
+    R = np.zeros((spec.K, spec.K))
+    for u in range(spec.K // spec.n_ue):
+        sl = slice(u * spec.n_ue, (u + 1) * spec.n_ue)
+        R[sl, sl] = exp_corr(spec.n_ue, spec.rho_t)
+    return R
+
+
 def generate(spec, chunks=None):
     """Draw the batch (or only the listed chunks, concatenated in order).
 
@@ -118,7 +135,7 @@ def generate(spec, chunks=None):
     symbols, sigma2 (batch,) float64, qam (batch,) int32.
     """
     Rr = None if spec.rho == 0 else sqrt_psd(exp_corr(spec.N, spec.rho))
-    Rt = None if spec.rho_t == 0 else sqrt_psd(exp_corr(spec.K, spec.rho_t))
+    Rt = None if spec.rho_t == 0 else sqrt_psd(user_corr(spec))
     nchunks = -(-spec.batch // CHUNK)
     ids = range(nchunks) if chunks is None else chunks
     parts = [_chunk(spec, c, Rr, Rt) for c in ids]
@@ -240,3 +257,112 @@ def generate_rb(spec):
     return {"H": H, "y": yc.astype(np.complex64), "rb_index": rb, "tx": tx, "x": x,
             "sigma2": np.full(spec.n_rb, sigma2), "qam": np.full(n, spec.qam, dtype=np.int32),
             "N": spec.N, "K": spec.K}
+
+
+# ---- channel-estimate and time-variation input models (Section V-B) ----------
+
+def csi_error(H, eps_db, seed):
+    """Imperfect CSI: H_hat = H + dH (Section V-B), dH i.i.d. CN(0, s2) per
+    entry with the channel-to-error power ratio eps: s2 = P_h 10^(-eps/10),
+    where P_h = 1/N is the average power of an entry of H (Omega's variance,
+    unit diagonal of R_r and R_t).  H in the storage layout (batch, K, N);
+    returns complex64 of the same shape.  y stays the one made with H."""
+    H = np.asarray(H)
+    N = H.shape[-1]
+    s = np.sqrt(0.5 * 10.0 ** (-float(eps_db) / 10.0) / N)
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 0x637369])))
+    dH = (rng.standard_normal(H.shape) + 1j * rng.standard_normal(H.shape)) * s
+    return (H.astype(np.complex128) + dH).astype(np.complex64)
+
+
+def doppler_corr(fd_hz, tau_s):
+    """rho_tau = J_0(2 pi f_d tau), the one-step correlation of the first-order
+    Gauss-Markov channel (Section V-B)."""
+    from scipy.special import j0
+    return float(j0(2.0 * np.pi * float(fd_hz) * float(tau_s)))
+
+
+def gauss_markov(spec, steps, rho_tau):
+    """A time-varying channel: H_0 drawn from spec, then H_i = rho_tau H_{i-1}
+    + sqrt(1 - rho_tau^2) W_i with W_i drawn from the same spatial model
+    (Section V-B), and at each step new symbols and noise: y_i = H_i x_i + n_i.
+    Returns a list of `steps` dicts shaped like generate()'s (the innovation of
+    step i uses seed spec.seed + 7919 i)."""
+    out = [generate(spec)]
+    a, c = float(rho_tau), float(np.sqrt(max(0.0, 1.0 - rho_tau * rho_tau)))
+    for i in range(1, steps):
+        w = generate(Spec(**{**spec.__dict__, "seed": spec.seed + 7919 * i}))
+        H = (a * out[-1]["H"].astype(np.complex128) + c * w["H"].astype(np.complex128))
+        # new symbols and noise from w; y recomputed with the aged channel
+        Hc = H.transpose(0, 2, 1)                                    # (b, N, K)
+        yc = np.einsum("bnk,bk->bn", Hc, w["x"])
+        if not spec.noiseless:
+            rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([spec.seed, 0x676d, i])))
+            sn = np.sqrt(w["sigma2"][0] / 2.0)
+            yc = yc + (rng.standard_normal(yc.shape) + 1j * rng.standard_normal(yc.shape)) * sn
+        out.append(dict(w, H=H.astype(np.complex64), y=yc.astype(np.complex64)))
+    return out
+
+
+# ---- the same models drawn on the GPU (large Monte-Carlo runs) ---------------
+
+def generate_torch(spec, chunk, count, device="cuda", h_true=None):
+    """`count` systems of spec drawn on `device` with torch's generator
+    (Philox) seeded by (spec.seed, chunk): the distributions of generate(),
+    another random stream.  For Monte-Carlo runs of 10^5..10^6 systems, where
+    drawing on the host would dominate; nothing compares them with the
+    oracle.  Returns H (count, K, N) complex64, y (count, N) complex64,
+    tx (count, K) uint8, x (count, K) complex128, sigma2 (count,) float64,
+    qam (count,) int32.  With
+    h_true given (same shape as H), y is formed with h_true instead of a new
+    channel (an aged channel, say)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed((int(spec.seed) * 1000003 + int(chunk)) & 0x7FFFFFFFFFFFFFFF)
+    N, K = spec.N, spec.K
+    if h_true is None:   # complex64 arithmetic: H is stored in complex64 anyway
+        s = float(np.sqrt(0.5 / N))
+        om = torch.complex(torch.randn((count, N, K), generator=g, device=device, dtype=torch.float32),
+                           torch.randn((count, N, K), generator=g, device=device, dtype=torch.float32)) * s
+        if spec.rho != 0:
+            Rr = torch.as_tensor(sqrt_psd(exp_corr(N, spec.rho)), device=device, dtype=torch.complex64)
+            om = Rr @ om
+        if spec.rho_t != 0:
+            Rt = torch.as_tensor(sqrt_psd(user_corr(spec)), device=device, dtype=torch.complex64)
+            om = om @ Rt
+        Hm = om                                                       # (count, N, K)
+    else:
+        Hm = h_true.transpose(1, 2)
+    tx = torch.randint(0, spec.qam, (count, K), generator=g, device=device, dtype=torch.int64)
+    m = int(round(np.sqrt(spec.qam)))
+    b = int(np.log2(m))
+    gi, gq = tx >> b, tx & (m - 1)
+    ji, jq = gi.clone(), gq.clone()
+    sh = 1
+    while sh < 16:              # Gray decode per axis
+        ji ^= ji >> sh
+        jq ^= jq >> sh
+        sh <<= 1
+    d = 1.0 / np.sqrt(2.0 * (spec.qam - 1) / 3.0)
+    x = torch.complex((2 * ji - (m - 1)).double() * d, (2 * jq - (m - 1)).double() * d)
+    sigma2 = float(snr_to_sigma2(spec.snr_db))
+    y = (Hm.to(torch.complex128) @ x.unsqueeze(-1)).squeeze(-1)
+    if not spec.noiseless:
+        sn = float(np.sqrt(sigma2 / 2.0))
+        y = y + torch.complex(torch.randn((count, N), generator=g, device=device, dtype=torch.float64),
+                              torch.randn((count, N), generator=g, device=device, dtype=torch.float64)) * sn
+    return {"H": Hm.transpose(1, 2).contiguous(), "y": y.to(torch.complex64), "tx": tx.to(torch.uint8), "x": x,
+            "sigma2": torch.full((count,), sigma2, device=device, dtype=torch.float64),
+            "qam": torch.full((count,), spec.qam, device=device, dtype=torch.int32)}
+
+
+def csi_error_torch(H, eps_db, seed, chunk):
+    """csi_error on the device (torch generator seeded by (seed, chunk))."""
+    import torch
+    g = torch.Generator(device=H.device)
+    g.manual_seed((int(seed) * 1000033 + int(chunk)) & 0x7FFFFFFFFFFFFFFF)
+    N = H.shape[-1]
+    s = float(np.sqrt(0.5 * 10.0 ** (-float(eps_db) / 10.0) / N))
+    dH = torch.complex(torch.randn(H.shape, generator=g, device=H.device, dtype=torch.float32),
+                       torch.randn(H.shape, generator=g, device=H.device, dtype=torch.float32)) * s
+    return H + dH
