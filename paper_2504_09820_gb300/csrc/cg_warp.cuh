@@ -150,13 +150,21 @@ __device__ __noinline__ float round_ip(float v, int fmt) { return round_to(v, fm
 // per system.  A CG iteration uses two n-tiles (vectors 4nt..4nt+3, columns
 // re, im of each); a residual uses one n-tile per vector (its six columns).
 // S.b and S.W of warp v are at vbase + v * vst (and + 8K bytes).
-template <int K, bool BF, int LT, int KR = K, int NV = 1>
+//
+// NS > 1: NS warps detect one system from one slot.  Every warp keeps the
+// whole iteration state and repeats the scalar steps (identical results);
+// each product with A is split by m-tiles over the NS warps between two
+// barriers (id bar_id), and warp sj packs and writes the rows lane + 32e with
+// e % NS == sj.  The preconditioner stages r in a warp-private buffer (rst),
+// since the slot's W is shared.
+template <int K, bool BF, int LT, int KR = K, int NV = 1, int NS = 1>
 struct CgWarp {
   static constexpr int KT = K / 16;          // k-tiles (16 users)
   static constexpr int MT = K / 16;          // m-tiles of Re A (and of Im A)
   static constexpr int E = K >= 32 ? K / 32 : 1;  // vector rows per lane
   static constexpr int NCOL = 6;             // B columns (re, im) x (hi, mid, lo)
   static_assert(NV == 1 || (NV == 8 && MT <= 8), "cooperative mode: eight warps");
+  static_assert(NS == 1 || (NV == 1 && E % NS == 0 && MT % NS == 0), "split mode: rows and m-tiles per warp");
   const DetectTcParams& P;
   Slot S;
   int lane, g, t;
@@ -164,6 +172,14 @@ struct CgWarp {
   int vw = 0;                // NV = 8: this warp's vector (its warp index)
   uint8_t* vbase = nullptr;  // NV = 8: per-vector b, W
   int vst = 0;
+  int sj = 0, bar_id = 0;    // NS > 1: this warp's index in its system's group, the group's barrier
+  float2* rst = nullptr;     // NS > 1: warp-private staging of r for the preconditioner
+
+  // NS > 1: rows lane + 32e this warp writes (packs, outputs)
+  __device__ __forceinline__ bool mine(int e) const { return NS == 1 || e % NS == sj; }
+  __device__ __forceinline__ void gsync() const {
+    if constexpr (NS > 1) tc::bar_sync(bar_id, NS * 32);
+  }
 
   __device__ CgWarp(const DetectTcParams& P_, Slot S_, int lane_) : P(P_), S(S_), lane(lane_) {
     g = lane >> 2;
@@ -209,7 +225,7 @@ struct CgWarp {
       const float nx = __shfl_down_sync(0xffffffffu, v[e].x, 1);
       const float ny = __shfl_down_sync(0xffffffffu, v[e].y, 1);
       const int rl = lane + 32 * e;
-      if (vact() && (rl & 1) == 0) {
+      if (vact() && (rl & 1) == 0 && mine(e)) {
         const int kt = rl >> 4, j = rl & 15, tt = (j & 7) >> 1, h = j >> 3;
         uint32_t* w = S.Pk + tt * 2 + h +
                       (NV == 1 ? kt * NCOL * 8
@@ -245,6 +261,7 @@ struct CgWarp {
       apply_cta(res, w);
       return;
     }
+    gsync();  // NS > 1: every warp's rows are packed
     uint32_t b0[KT], b1[KT];
 #pragma unroll
     for (int kt = 0; kt < KT; ++kt) {
@@ -258,7 +275,7 @@ struct CgWarp {
     const uint32_t abase = tc::smem_u32(S.A16);
     const int lr = lane & 15, lc = lane >> 4;
 #pragma unroll 1  // unrolled runs slower in the full kernel (code size)
-    for (int mt = 0; mt < MT; ++mt) {
+    for (int mt = sj * (MT / NS); mt < (sj + 1) * (MT / NS); ++mt) {
       float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
       float cr2[4] = {0.f, 0.f, 0.f, 0.f}, ci2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -304,6 +321,7 @@ struct CgWarp {
       }
     }
     __syncwarp();
+    gsync();  // NS > 1: every m-tile of W is written
 #pragma unroll
     for (int e = 0; e < E; ++e) w[e] = vact() ? S.W[lane + 32 * e] : make_float2(0.f, 0.f);
     __syncwarp();
@@ -393,14 +411,15 @@ struct CgWarp {
       for (int e = 0; e < E; ++e) z[e] = r[e];
     } else {
       constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
+      float2* st = NS > 1 ? rst : S.W;
 #pragma unroll
       for (int e = 0; e < E; ++e)
-        if (vact()) S.W[lane + 32 * e] = r[e];
+        if (vact()) st[lane + 32 * e] = r[e];
       __syncwarp();
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int k = vact() ? lane + 32 * e : 0;
-        const float4* rb = reinterpret_cast<const float4*>(S.W + (k & ~(LT - 1)));
+        const float4* rb = reinterpret_cast<const float4*>(st + (k & ~(LT - 1)));
         const float4* mr = reinterpret_cast<const float4*>(S.Md + (k / LT) * MBS + (k % LT) * MLD);
         float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -424,7 +443,20 @@ struct CgWarp {
   // Block-Jacobi setup (eq. pre_BJ) on the slot's M_d: FPCG_ST_BJ_FAIL (8) and
   // M_d = I if a diagonal block was not positive definite, else 0.
   __device__ int bj_setup() {
-    if constexpr (LT > 0) {
+    if constexpr (LT > 0 && NS > 1) {  // warp sj inverts the blocks of columns 32 (sj + NS r) ..
+      constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
+      int fail = 0;
+#pragma unroll 1
+      for (int c0 = 32 * sj; c0 < K; c0 += 32 * NS) fail |= gj_blocks<K, LT, 1>(S.Md, lane, c0);
+      if (tc::bar_or(bar_id, NS * 32, fail)) {  // a failed block: M_d = I for the system
+        for (int i = sj * 32 + lane; i < K * LT; i += NS * 32)
+          S.Md[(i / LT / LT) * MBS + ((i / LT) % LT) * MLD + i % LT] =
+              make_float2((i / LT) % LT == i % LT ? 1.f : 0.f, 0.f);
+        gsync();
+        return 8;
+      }
+      return 0;
+    } else if constexpr (LT > 0) {
       constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
       int fail;
       if constexpr (E <= 2) {
@@ -448,6 +480,7 @@ struct CgWarp {
   // A system whose group index is out of range: x_hat = 0, labels 0,
   // rel_res = 0, FPCG_ST_BAD_INDEX (64); no bit errors counted.
   __device__ void bad_index(int64_t sys) {
+    if (NS > 1 && sj != 0) return;
     const int64_t base = sys * (int64_t)KR;
     for (int k = lane; k < KR; k += 32) {
       P.x_hat[base + k] = make_float2(0.f, 0.f);
@@ -468,7 +501,7 @@ struct CgWarp {
     const int M = want_sym ? P.qam[sys] : 0;
     int txv[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) txv[e] = (want_sym && P.tx && vout(e)) ? P.tx[base + lane + 32 * e] : 0;
+    for (int e = 0; e < E; ++e) txv[e] = (want_sym && P.tx && vout(e) && mine(e)) ? P.tx[base + lane + 32 * e] : 0;
     float* hist = (P.res_hist && valid) ? P.res_hist + sys * (int64_t)(iters + 1) : nullptr;
 
     float2 x[E], d[E], r[E], p[E], z[E], w[E];
@@ -520,7 +553,7 @@ struct CgWarp {
           else if (!(phi > 0.f) || !isfinite(phi) || !isfinite(rho_prev)) bad = 1;
           if (bad) {  // the pass stops here; the history repeats its last value
             st |= bad & mask;
-            if (hist && lane == 0)
+            if (hist && lane == 0 && sj == 0)
               for (int k = it + 1; k <= iters_p; ++k) hist[k] = hist[it];
             if constexpr (NV > 1) {  // the other warps still take this pass's trips
               frozen = true;
@@ -551,7 +584,7 @@ struct CgWarp {
       for (int e = 0; e < E; ++e)
         p[e] = fresh ? z[e] : make_float2(fmaf(beta, p[e].x, z[e].x), fmaf(beta, p[e].y, z[e].y));
       rho = rho_new;
-      if (hist && lane == 0) hist[it] = sqrtf(rr);
+      if (hist && lane == 0 && sj == 0) hist[it] = sqrtf(rr);
       fresh = false;
     }
 
@@ -570,7 +603,7 @@ struct CgWarp {
         nb += bv.x * bv.x + bv.y * bv.y;
         const int k = lane + 32 * e;
         if (!(isfinite(x[e].x) && isfinite(x[e].y))) nonfinite = 1;
-        if (!vout(e)) continue;
+        if (!vout(e) || !mine(e)) continue;
         P.x_hat[base + k] = x[e];
         if (want_sym) {
           int lab = 0;
@@ -590,7 +623,7 @@ struct CgWarp {
       errs = __reduce_add_sync(0xffffffffu, errs);
       if (lane == 0 && errs) atomicAdd(P.bit_errors, (unsigned long long)errs);
     }
-    if (lane == 0) {
+    if (lane == 0 && sj == 0) {
       if (P.rel_res) P.rel_res[sys] = nb > 0.f ? (double)sqrtf(nr / nb) : 0.0;
       if (nonfinite) st |= 4;
       if (want_sym && m == 0) st |= 16;

@@ -36,10 +36,22 @@ __host__ __device__ constexpr int pad_k(int K) { return K < 16 ? 16 : K; }
 
 constexpr int kSolveWarps = 8;  // CG warps per CTA (grouped mode, and independent systems for K <= 64)
 
-// Independent systems: one slot per warp; K = 128 slots (~80 KB) allow two per CTA.
+// Independent systems, K <= 64: one slot per warp, eight warps per CTA (K = 128
+// runs four warps per system: kSplitWarps below).
 __host__ __device__ constexpr int solve_warps(int K) { return K == 128 ? 2 : kSolveWarps; }
 
-inline size_t solve_tc_smem_bytes(int K, int L) { return 128 + solve_warps(K) * tc_slot_bytes(pad_k(K), L); }
+inline size_t solve_tc_smem_bytes(int K, int L);
+
+// K = 128: four warps per system, two systems per CTA; a system's group holds
+// its slot and one K-entry staging buffer per warp.
+constexpr int kSplitWarps = 4;
+constexpr int kSplitGroups = 2;
+__host__ __device__ inline size_t split_group_bytes(int K, int L) { return tc_slot_bytes(K, L) + kSplitWarps * sizeof(float2) * K; }
+inline size_t solve_split_smem_bytes(int K, int L) { return 128 + kSplitGroups * split_group_bytes(K, L); }
+
+inline size_t solve_tc_smem_bytes(int K, int L) {
+  return K == 128 ? solve_split_smem_bytes(K, L) : 128 + solve_warps(K) * tc_slot_bytes(pad_k(K), L);
+}
 
 // Grouped mode (fpcg_detect_grouped): all warps of a CTA share one group's A
 // and inverted blocks; each warp has its own b, matvec result and B fragments.

@@ -80,10 +80,13 @@ __device__ __forceinline__ void load_b(const float2* bs, const Slot& S, int lane
 
 // b = fl(H)^H fl(y) for one system into S.b (rounding of the Gram step); H
 // has KR rows, entries KR..K-1 of b are zero.
+// Rows k0 = 4 first, 4 (first + step), ... (several warps may split them).
 template <int K, int KR>
-__device__ void matched_filter(const float2* Hg, const float2* ys, int N, int gram, const Slot& S, int lane) {
-  for (int k = KR + lane; k < K; k += 32) S.b[k] = make_float2(0.f, 0.f);
-  for (int k0 = 0; k0 < KR; k0 += 4) {
+__device__ void matched_filter(const float2* Hg, const float2* ys, int N, int gram, const Slot& S, int lane,
+                               int first = 0, int step = 1) {
+  if (first == 0)
+    for (int k = KR + lane; k < K; k += 32) S.b[k] = make_float2(0.f, 0.f);
+  for (int k0 = 4 * first; k0 < KR; k0 += 4 * step) {
     float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
     for (int n = lane; n < N; n += 32) {
       const float2 yy = ys[n];
@@ -173,6 +176,80 @@ __global__ void __launch_bounds__(solve_warps(KR) * 32, 1) solve_tc_kernel(const
   }
 }
 
+// K = 128 independent systems: four warps per system (CgWarp NS = 4), two
+// systems per CTA, so an SM works on eight warps where one warp per slot
+// would give it two (the 80 KB slots allow two per SM).  A group of four
+// warps takes a contiguous range of systems; every step that changes the
+// slot is followed by the group's barrier.
+template <int KR, bool BF, int LT>
+__global__ void __launch_bounds__(kSplitWarps * kSplitGroups * 32, 1)
+    solve_split_kernel(const __grid_constant__ SolveTcParams P) {
+  constexpr int K = pad_k(KR);
+  constexpr int GT = kSplitWarps * 32;  // threads per system
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = warp / kSplitWarps, sj = warp % kSplitWarps, gtid = sj * 32 + lane;
+  uint8_t* base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+  uint8_t* gbase = base + grp * split_group_bytes(K, LT);
+  const Slot S = slot_carve(gbase, K, LT);
+  CgWarp<K, BF, LT, KR, 1, kSplitWarps> W(P.D, S, lane);
+  W.sj = sj;
+  W.bar_id = 1 + grp;
+  W.rst = reinterpret_cast<float2*>(gbase + tc_slot_bytes(K, LT) + sj * sizeof(float2) * K);
+  const int64_t tg = (int64_t)gridDim.x * kSplitGroups, gg = (int64_t)blockIdx.x * kSplitGroups + grp;
+  const int64_t chunk = (P.n + tg - 1) / tg;
+  const int64_t s0 = gg * chunk, s1 = min(P.n, s0 + chunk);
+  if (s0 >= s1) return;  // the whole group (its barrier is its own)
+  int64_t g = s0, g_end = s0 + 1;
+  if (P.group_start) {
+    int64_t lo = 0, hi = P.n_groups;  // largest g with start[g] <= s0
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) / 2;
+      if (P.group_start[mid] <= s0) lo = mid;
+      else hi = mid;
+    }
+    g = lo;
+    g_end = P.group_start[g + 1];
+  }
+  int64_t cur = -1;
+  int st_bj = 0;
+  for (int64_t s = s0; s < s1; ++s) {
+    if (P.group_start) {
+      while (s >= g_end && g + 1 < P.n_groups) {
+        ++g;
+        g_end = P.group_start[g + 1];
+      }
+    } else if (P.a_map) {
+      const int32_t gi = P.a_map[s];
+      if (gi < 0 || gi >= P.n_groups) {
+        W.bad_index(s);
+        continue;
+      }
+      g = gi;
+    } else {
+      g = s;
+    }
+    W.gsync();  // the previous system is done with b (and A)
+    if (g != cur) {
+      fill_A<K, KR, BF, LT>(P.A + (size_t)g * KR * KR, S, gtid, GT);
+      W.gsync();
+      st_bj = W.bj_setup();
+      cur = g;
+    }
+    if (P.b) {
+      for (int i = gtid; i < K / 2; i += GT)
+        reinterpret_cast<float4*>(S.b)[i] = (KR == K || 2 * i < KR) ? reinterpret_cast<const float4*>(
+                                                                          P.b + (size_t)s * KR)[i]
+                                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      matched_filter<K, KR>(P.H + (size_t)g * KR * P.N, P.y + (size_t)s * P.N, P.N, P.gram, S, lane, sj,
+                            kSplitWarps);
+    }
+    W.gsync();  // b and the slot are complete
+    W.detect(s, true, st_bj);
+  }
+}
+
 // Grouped mode: CTA c takes groups c, c + gridDim.x, ...; for each, all its
 // threads round the group's A into the shared slot, warps 0..K/32-1 invert the
 // diagonal blocks (one block column per lane), and the eight warps take the
@@ -256,7 +333,29 @@ cudaError_t launch_g(const SolveTcParams& P, int num_sms, cudaStream_t stream) {
 }
 
 template <int K, bool BF, int LT>
+cudaError_t launch_split(const SolveTcParams& P, int num_sms, cudaStream_t stream) {
+  const size_t smem = solve_split_smem_bytes(K, LT);
+  cudaError_t e =
+      cudaFuncSetAttribute(solve_split_kernel<K, BF, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  constexpr int NT = kSplitWarps * kSplitGroups * 32;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_split_kernel<K, BF, LT>, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)num_sms * per_sm;
+  const int64_t need = (P.n + kSplitGroups - 1) / kSplitGroups;
+  if (grid > need) grid = need;
+  if (grid <= 0) return cudaSuccess;
+  solve_split_kernel<K, BF, LT><<<(unsigned)grid, NT, smem, stream>>>(P);
+  return cudaGetLastError();
+}
+
+template <int K, bool BF, int LT>
 cudaError_t launch_s(const SolveTcParams& P, int num_sms, cudaStream_t stream) {
+  if constexpr (K == 128) {
+    return launch_split<K, BF, LT>(P, num_sms, stream);
+  } else {
   const size_t smem = solve_tc_smem_bytes(K, LT);
   cudaError_t e =
       cudaFuncSetAttribute(solve_tc_kernel<K, BF, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -272,6 +371,7 @@ cudaError_t launch_s(const SolveTcParams& P, int num_sms, cudaStream_t stream) {
   if (grid <= 0) return cudaSuccess;
   solve_tc_kernel<K, BF, LT><<<(unsigned)grid, W * 32, smem, stream>>>(P);
   return cudaGetLastError();
+  }
 }
 
 }  // namespace

@@ -87,6 +87,18 @@ __device__ __forceinline__ void bar_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Barrier that also ORs a predicate over its threads: nonzero on every thread
+// if any thread passed nonzero.
+__device__ __forceinline__ int bar_or(int id, int nthreads, int v) {
+  int out;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred p, %2, %3, p;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(out)
+      : "r"(v), "r"(id), "r"(nthreads)
+      : "memory");
+  return out;
+}
+
 // ---- tensor memory -------------------------------------------------------------
 // Whole warp: allocate `ncols` TMEM columns (power of two, >= 32); the base
 // address is written to shared memory at dst.
