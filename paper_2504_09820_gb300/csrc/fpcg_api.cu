@@ -440,6 +440,23 @@ int fpcg_gram(const void* H, const void* y, const double* sigma2, int32_t n_rx, 
     cudaError_t e = fpcg::launch_gram_tc(P, sms, s);
     return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
   }
+  if ((gram == FPCG_BF16 || gram == FPCG_FP16) && k == 128 && fpcg::tma_pipe_ok(H, y, n_rx) &&
+      ((uintptr_t)A % 16) == 0 && !force_simt()) {
+    int sms = 0;
+    int rc = device_sms(&sms);
+    if (rc) return rc;
+    rc = check_device_smem(fpcg::gram_tc128_smem_bytes());
+    if (rc) return rc;
+    fpcg::GramTc128Params P;
+    memset(&P, 0, sizeof(P));
+    if (!fpcg::make_gram_tc128(&P, (const float2*)H, (const float2*)y, (float2*)A, n_rx, batch, gram == FPCG_BF16))
+      return FPCG_ENOTSUP;
+    P.sigma2 = sigma2;
+    P.b = (float2*)b;
+    P.status = status;
+    cudaError_t e = fpcg::launch_gram_tc128(P, sms, s);
+    return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+  }
   if ((gram == FPCG_BF16 || gram == FPCG_FP16) && fpcg::gram_mma_supported(k) && !force_simt()) {
     fpcg::GramMmaParams P{(const float2*)H, (const float2*)y, sigma2, (float2*)A, (float2*)b, n_rx, k, batch};
     cudaError_t e = fpcg::launch_gram_mma(P, gram == FPCG_BF16, s);

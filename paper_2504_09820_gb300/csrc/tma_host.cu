@@ -40,6 +40,19 @@ bool encode(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uin
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D fp32 tensor with a 128-byte swizzle (box {32, box_rows}: 128-byte rows).
+bool encode_sw128(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+  auto fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {inner, rows};
+  const cuuint64_t strides[1] = {inner * 4};
+  const cuuint32_t box[2] = {32, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 bool tma_pipe_ok(const void* H, const void* y, int N) {
@@ -59,6 +72,19 @@ bool make_pipe(tcp::Pipe* p, const float2* H, const float2* y, int N, int K, int
   p->bf16 = bf16;
   return encode(&p->tmH, H, 2ull * N, (uint64_t)batch * K, 64) &&
          encode(&p->tmY, y, 2ull * N, (uint64_t)batch, (uint32_t)p->P);
+}
+
+bool make_gram_tc128(GramTc128Params* p, const float2* H, const float2* y, float2* A, int N, int64_t batch,
+                     int bf16) {
+  if (((uintptr_t)A % 16) != 0) return false;
+  p->H = H;
+  p->A = A;
+  p->N = N;
+  p->nchunks = (N + tcp::kChunk - 1) / tcp::kChunk;
+  p->batch = batch;
+  p->bf16 = bf16;
+  return encode(&p->tmH, H, 2ull * N, (uint64_t)batch * 128, 128) && encode(&p->tmY, y, 2ull * N, (uint64_t)batch, 1) &&
+         encode_sw128(&p->tmA, A, 256, (uint64_t)batch * 128, 128);
 }
 
 }  // namespace fpcg

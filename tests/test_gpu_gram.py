@@ -85,3 +85,18 @@ def test_mma_gram(K, N, gram):
     # the mma chain rounds the fp32 accumulator twice per 16 antennas (two MMAs per
     # part); one ulp (2^-23, truncation allowed) of the row scale per rounding
     check(d, gram, A, b, st, tol=max(2e-6, 2 * (-(-N // 16)) * 2.0 ** -23))
+
+
+@pytest.mark.parametrize("N,batch", [(512, 400), (256, 160), (130, 153), (128, 7)])
+@pytest.mark.parametrize("gram", ["bf16", "fp16"])
+def test_tcgen05_gram_k128(N, batch, gram, monkeypatch):
+    """K = 128 on the tcgen05 pipeline (N even, aligned): Re A and [Im A | b]
+    in two TMEM accumulators, the fourth product through the negate-B bit.
+    More systems than SMs (the accumulators are reused after each drain) and
+    a ragged last antenna chunk, against the oracle."""
+    d = wl.generate(wl.Spec(N=N, K=128, batch=batch, rho=0.5, qam=64, snr_db=15.0, seed=300 + N + batch))
+    A, b, st = run_gram(d, gram)
+    tol = max(2e-6, 2 * (-(-N // 16)) * 2.0 ** -23)
+    check(d, gram, A, b, st, tol=tol)
+    # the two triangles come from different accumulator entries: Hermitian within the bound
+    assert np.abs(A - np.conj(np.swapaxes(A, 1, 2))).max() < 2 * tol * np.abs(A).max()
