@@ -220,12 +220,27 @@ struct CgWarp {
   // remainders when `split` (three pieces carry all 24 bits of an fp32 value;
   // zeros otherwise).
   __device__ __forceinline__ void pack(const float2 (&v)[E], bool split) {
+    if constexpr (NS > 1 && NS == E) {  // split mode: only rows lane + 32 sj
+      float2 vs = v[0];
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
+      for (int e = 1; e < E; ++e)
+        if (e == sj) vs = v[e];
+      const float2 one[1] = {vs};
+      pack_rows<1>(one, split, sj);
+      return;
+    }
+    pack_rows<E>(v, split, 0);
+  }
+
+  // Rows lane + 32 (e0 + e) of v[e], e < NR, as B fragments (see pack).
+  template <int NR>
+  __device__ __forceinline__ void pack_rows(const float2 (&v)[NR], bool split, int e0) {
+#pragma unroll
+    for (int e = 0; e < NR; ++e) {
       const float nx = __shfl_down_sync(0xffffffffu, v[e].x, 1);
       const float ny = __shfl_down_sync(0xffffffffu, v[e].y, 1);
-      const int rl = lane + 32 * e;
-      if (vact() && (rl & 1) == 0 && mine(e)) {
+      const int rl = lane + 32 * (e0 + e);
+      if (vact() && (rl & 1) == 0 && (NR < E || mine(e))) {
         const int kt = rl >> 4, j = rl & 15, tt = (j & 7) >> 1, h = j >> 3;
         uint32_t* w = S.Pk + tt * 2 + h +
                       (NV == 1 ? kt * NCOL * 8
@@ -252,6 +267,66 @@ struct CgWarp {
     __syncwarp();
   }
 
+  // Rows 16mt.. of W = A v (or b - A v) for the NMT m-tiles mt0.. from the B
+  // fragments b0, b1: the m-tiles interleaved along k, two accumulator
+  // chains (even / odd k-tile) per m-tile and part.
+  template <int NMT>
+  __device__ __forceinline__ void apply_mtiles(int mt0, bool res, const uint32_t (&b0)[KT], const uint32_t (&b1)[KT]) {
+    const uint32_t abase = tc::smem_u32(S.A16);
+    const int lr = lane & 15, lc = lane >> 4;
+    float cr[NMT][2][4], ci[NMT][2][4];
+#pragma unroll
+    for (int j = 0; j < NMT; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cr[j][h][q] = ci[j][h][q] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < KT; ++kt) {
+#pragma unroll
+      for (int j = 0; j < NMT; ++j) {
+        uint32_t ar[4], ai[4];
+        tc::ldmatrix_x4(ar, abase + a16_offset<K>(16 * (mt0 + j) + lr, 2 * kt + lc));
+        tc::ldmatrix_x4(ai, abase + a16_offset<K>(K + 16 * (mt0 + j) + lr, 2 * kt + lc));
+        mma16<BF>(cr[j][kt & 1], ar, b0[kt], b1[kt]);
+        mma16<BF>(ci[j][kt & 1], ai, b0[kt], b1[kt]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NMT; ++j) {
+      const int mt = mt0 + j;
+      float r[4], im[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        r[q] = cr[j][0][q] + cr[j][1][q];
+        im[q] = ci[j][0][q] + ci[j][1][q];
+      }
+      if (res) {  // add the mid (t = 1) and lo (t = 2) column products into t = 0
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float r1 = __shfl_down_sync(0xffffffffu, r[q], 1);
+          const float r2 = __shfl_down_sync(0xffffffffu, r[q], 2);
+          const float i1 = __shfl_down_sync(0xffffffffu, im[q], 1);
+          const float i2 = __shfl_down_sync(0xffffffffu, im[q], 2);
+          r[q] += r1 + r2;
+          im[q] += i1 + i2;
+        }
+      }
+      if (t == 0) {
+        // rows 16mt+g / +8: (Re A vr - Im A vi) + i (Re A vi + Im A vr)
+        float2 w0 = make_float2(r[0] - im[1], r[1] + im[0]);
+        float2 w8 = make_float2(r[2] - im[3], r[3] + im[2]);
+        if (res) {
+          const float2 bb0 = S.b[16 * mt + g], bb8 = S.b[16 * mt + g + 8];
+          w0 = make_float2(bb0.x - w0.x, bb0.y - w0.y);
+          w8 = make_float2(bb8.x - w8.x, bb8.y - w8.y);
+        }
+        S.W[16 * mt + g] = w0;
+        S.W[16 * mt + g + 8] = w8;
+      }
+    }
+  }
+
   // W = A v (res = false) or W = b - A v (res = true: the three column pairs
   // of v are summed), one m-tile (16 rows of Re A and of Im A) at a time; lane
   // (g, t) holds C rows g, g+8 and columns 2t, 2t+1.  Then w = W in the vector
@@ -272,53 +347,11 @@ struct CgWarp {
         b1[kt] = pw.y;
       }
     }
-    const uint32_t abase = tc::smem_u32(S.A16);
-    const int lr = lane & 15, lc = lane >> 4;
+    if constexpr (NS > 1) {  // this warp's m-tiles interleaved along k
+      apply_mtiles<MT / NS>(sj * (MT / NS), res, b0, b1);
+    } else {
 #pragma unroll 1  // unrolled runs slower in the full kernel (code size)
-    for (int mt = sj * (MT / NS); mt < (sj + 1) * (MT / NS); ++mt) {
-      float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
-      float cr2[4] = {0.f, 0.f, 0.f, 0.f}, ci2[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int kt = 0; kt < KT; ++kt) {  // two accumulator chains per part (even / odd kt)
-        uint32_t ar[4], ai[4];
-        tc::ldmatrix_x4(ar, abase + a16_offset<K>(16 * mt + lr, 2 * kt + lc));
-        tc::ldmatrix_x4(ai, abase + a16_offset<K>(K + 16 * mt + lr, 2 * kt + lc));
-        if (kt & 1) {
-          mma16<BF>(cr2, ar, b0[kt], b1[kt]);
-          mma16<BF>(ci2, ai, b0[kt], b1[kt]);
-        } else {
-          mma16<BF>(cr, ar, b0[kt], b1[kt]);
-          mma16<BF>(ci, ai, b0[kt], b1[kt]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        cr[q] += cr2[q];
-        ci[q] += ci2[q];
-      }
-      if (res) {  // add the mid (t = 1) and lo (t = 2) column products into t = 0
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float r1 = __shfl_down_sync(0xffffffffu, cr[q], 1);
-          const float r2 = __shfl_down_sync(0xffffffffu, cr[q], 2);
-          const float i1 = __shfl_down_sync(0xffffffffu, ci[q], 1);
-          const float i2 = __shfl_down_sync(0xffffffffu, ci[q], 2);
-          cr[q] += r1 + r2;
-          ci[q] += i1 + i2;
-        }
-      }
-      if (t == 0) {
-        // rows 16mt+g / +8: (Re A vr - Im A vi) + i (Re A vi + Im A vr)
-        float2 w0 = make_float2(cr[0] - ci[1], cr[1] + ci[0]);
-        float2 w8 = make_float2(cr[2] - ci[3], cr[3] + ci[2]);
-        if (res) {
-          const float2 bb0 = S.b[16 * mt + g], bb8 = S.b[16 * mt + g + 8];
-          w0 = make_float2(bb0.x - w0.x, bb0.y - w0.y);
-          w8 = make_float2(bb8.x - w8.x, bb8.y - w8.y);
-        }
-        S.W[16 * mt + g] = w0;
-        S.W[16 * mt + g + 8] = w8;
-      }
+      for (int mt = 0; mt < MT; ++mt) apply_mtiles<1>(mt, res, b0, b1);
     }
     __syncwarp();
     gsync();  // NS > 1: every m-tile of W is written

@@ -26,46 +26,68 @@ namespace {
 
 // Round the group's A (KR x KR, row stride KR) into the slot: 16-bit
 // [Re A; Im A] chunks of 8 columns and the fp32 diagonal blocks; rows and
-// columns KR..K-1 are those of the identity.  Threads tid, tid + nt, ...
-template <int K, int KR, bool BF, int LT>
+// columns KR..K-1 are those of the identity.  Threads tid, tid + nt, ...;
+// each thread issues the loads of UB chunks before it converts any, so UB
+// global loads per thread are in flight instead of one round trip per chunk.
+template <int K, int KR, bool BF, int LT, int UB = 4>
 __device__ __forceinline__ void fill_A(const float2* Ag, const Slot& S, int tid, int nt) {
-  constexpr int CPR = K / 8;
-  for (int idx = tid; idx < K * CPR; idx += nt) {
-    const int k = idx / CPR, c = idx % CPR;
-    float2 a[8];
-    if (KR == K || (k < KR && 8 * c < KR)) {
-      const float4* src = reinterpret_cast<const float4*>(Ag + (size_t)k * KR + 8 * c);
+  constexpr int CPR = K / 8, ITEMS = K * CPR;
+  for (int i0 = tid; i0 < ITEMS; i0 += UB * nt) {
+    float4 v[UB][4];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int idx = i0 + u * nt, k = idx / CPR, c = idx % CPR;
+      if (idx < ITEMS && (KR == K || (k < KR && 8 * c < KR))) {
+        const float4* src = reinterpret_cast<const float4*>(Ag + (size_t)k * KR + 8 * c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[u][q] = __ldg(src + q);
+      } else {  // padding: the identity
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          v[u][q] = make_float4(k == 8 * c + 2 * q ? 1.f : 0.f, 0.f, k == 8 * c + 2 * q + 1 ? 1.f : 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int idx = i0 + u * nt, k = idx / CPR, c = idx % CPR;
+      if (idx >= ITEMS) break;
+      float2 a[8];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float4 v = __ldg(src + q);
-        a[2 * q] = make_float2(v.x, v.y);
-        a[2 * q + 1] = make_float2(v.z, v.w);
+        a[2 * q] = make_float2(v[u][q].x, v[u][q].y);
+        a[2 * q + 1] = make_float2(v[u][q].z, v[u][q].w);
       }
-    } else {
+      uint4 re, im;
+      re.x = pk2<BF>(a[0].x, a[1].x);
+      re.y = pk2<BF>(a[2].x, a[3].x);
+      re.z = pk2<BF>(a[4].x, a[5].x);
+      re.w = pk2<BF>(a[6].x, a[7].x);
+      im.x = pk2<BF>(a[0].y, a[1].y);
+      im.y = pk2<BF>(a[2].y, a[3].y);
+      im.z = pk2<BF>(a[4].y, a[5].y);
+      im.w = pk2<BF>(a[6].y, a[7].y);
+      *reinterpret_cast<uint4*>(S.A16 + a16_offset<K>(k, c)) = re;
+      *reinterpret_cast<uint4*>(S.A16 + a16_offset<K>(K + k, c)) = im;
+      if constexpr (LT > 0) {
+        constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
+        const int kb0 = (k / LT) * LT;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) a[m] = make_float2(k == 8 * c + m ? 1.f : 0.f, 0.f);
-    }
-    uint4 re, im;
-    re.x = pk2<BF>(a[0].x, a[1].x);
-    re.y = pk2<BF>(a[2].x, a[3].x);
-    re.z = pk2<BF>(a[4].x, a[5].x);
-    re.w = pk2<BF>(a[6].x, a[7].x);
-    im.x = pk2<BF>(a[0].y, a[1].y);
-    im.y = pk2<BF>(a[2].y, a[3].y);
-    im.z = pk2<BF>(a[4].y, a[5].y);
-    im.w = pk2<BF>(a[6].y, a[7].y);
-    *reinterpret_cast<uint4*>(S.A16 + a16_offset<K>(k, c)) = re;
-    *reinterpret_cast<uint4*>(S.A16 + a16_offset<K>(K + k, c)) = im;
-    if constexpr (LT > 0) {
-      constexpr int MLD = md_row_stride(LT), MBS = md_block_stride(LT);
-      const int kb0 = (k / LT) * LT;
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int l = 8 * c + m;
-        if (l >= kb0 && l < kb0 + LT) S.Md[(k / LT) * MBS + (k % LT) * MLD + (l - kb0)] = a[m];
+        for (int m = 0; m < 8; ++m) {
+          const int l = 8 * c + m;
+          if (l >= kb0 && l < kb0 + LT) S.Md[(k / LT) * MBS + (k % LT) * MLD + (l - kb0)] = a[m];
+        }
       }
     }
   }
+}
+
+// Ask the bulk-copy engine to pull `bytes` (a multiple of 16, 16-byte aligned)
+// into L2 ahead of the loads that will read them.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  for (uint32_t o = 0; o < bytes; o += 32768)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const char*>(p) + o),
+                 "r"(bytes - o < 32768u ? bytes - o : 32768u)
+                 : "memory");
 }
 
 // b of system s (KR entries, given) into the slot, zeros beyond KR.  Plain
@@ -231,8 +253,15 @@ __global__ void __launch_bounds__(kSplitWarps * kSplitGroups * 32, 1)
     }
     W.gsync();  // the previous system is done with b (and A)
     if (g != cur) {
-      fill_A<K, KR, BF, LT>(P.A + (size_t)g * KR * KR, S, gtid, GT);
+      fill_A<K, KR, BF, LT, 8>(P.A + (size_t)g * KR * KR, S, gtid, GT);
       W.gsync();
+      if (gtid == 0 && s + 1 < s1) {  // the next system's A into L2 while this one is solved
+        int64_t gn = s + 1;
+        if (P.group_start) gn = s + 1 < g_end ? g : g + 1;
+        else if (P.a_map) gn = P.a_map[s + 1];
+        if (gn != g && gn >= 0 && gn < P.n_groups)
+          prefetch_l2(P.A + (size_t)gn * KR * KR, (uint32_t)(sizeof(float2) * KR * KR));
+      }
       st_bj = W.bj_setup();
       cur = g;
     }
