@@ -349,9 +349,10 @@ struct CgWarp {
     }
     if constexpr (NS > 1) {  // this warp's m-tiles interleaved along k
       apply_mtiles<MT / NS>(sj * (MT / NS), res, b0, b1);
-    } else {
-#pragma unroll 1  // unrolled runs slower in the full kernel (code size)
-      for (int mt = 0; mt < MT; ++mt) apply_mtiles<1>(mt, res, b0, b1);
+    } else {  // m-tiles in pairs: more independent chains, a rolled loop keeps the code small
+      constexpr int MP = MT >= 2 ? 2 : 1;
+#pragma unroll 1
+      for (int mt = 0; mt < MT; mt += MP) apply_mtiles<MP>(mt, res, b0, b1);
     }
     __syncwarp();
     gsync();  // NS > 1: every m-tile of W is written
