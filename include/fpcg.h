@@ -365,12 +365,12 @@ FPCG_API int fpcg_plan_destroy(fpcg_plan* plan);
  * has no counterpart: this is about the library's memory, not the method).
  * Same arguments and results as fpbjcg_detect (block_L > 0) or fpcg_detect
  * (block_L = 0).  Configurations that run in two passes (Gram matrices first,
- * then the tensor-core solver: K = 128 with a 16-bit matvec, w = resid = FP32,
- * gram in {BF16, FP16}) keep their Gram matrices and matched filters in one
+ * then the tensor-core solver: K = 8 and K = 128 with a 16-bit matvec, w =
+ * resid = FP32, gram in {BF16, FP16}) keep their Gram matrices and matched filters in one
  * fixed 64 MiB device array of the library; every other configuration takes
  * the ordinary path, which allocates nothing either.
  *   - Limit: batch * K * (K + 1) * 8 bytes <= 64 MiB (K = 128: 496 systems per
- *     call); a larger batch returns FPCG_ENOTSUP (split it).
+ *     call; K = 8: 116508); a larger batch returns FPCG_ENOTSUP (split it).
  *   - The array is shared by all calls on a device: calls must not overlap in
  *     time (issue them on one stream, or wait for one before the next).
  *   - The first call on each device looks up the array's address

@@ -42,18 +42,19 @@ def _noalloc(g, K, L):
     return {k: v.cpu() for k, v in out.items()}
 
 
-def test_two_calls_equal_gram_then_solve():
-    d, g = _data(256, 128, 200, 41)
-    first = _noalloc(g, 128, 8)
-    second = _noalloc(g, 128, 8)
+@pytest.mark.parametrize("N,K,L", [(256, 128, 8), (64, 8, 4)])
+def test_two_calls_equal_gram_then_solve(N, K, L):
+    d, g = _data(N, K, 200, 41)
+    first = _noalloc(g, K, L)
+    second = _noalloc(g, K, L)
     for k in first:
         assert torch.equal(first[k], second[k]), k
-    A = torch.empty((200, 128, 128), dtype=torch.complex64, device="cuda")
-    b = torch.empty((200, 128), dtype=torch.complex64, device="cuda")
+    A = torch.empty((200, K, K), dtype=torch.complex64, device="cuda")
+    b = torch.empty((200, K), dtype=torch.complex64, device="cuda")
     F.fpcg_gram(g["H"], g["y"], g["sigma2"], "bf16", A, b)
-    x = torch.empty((200, 128), dtype=torch.complex64, device="cuda")
+    x = torch.empty((200, K), dtype=torch.complex64, device="cuda")
     rel = torch.empty(200, dtype=torch.float64, device="cuda")
-    F.fpcg_solve_gram(A, b, 6, 8, F.precision(**PREC), x, rel_res=rel)
+    F.fpcg_solve_gram(A, b, 6, L, F.precision(**PREC), x, rel_res=rel)
     torch.cuda.synchronize()
     assert torch.equal(first["x"], x.cpu()) and torch.equal(first["rel"], rel.cpu())
     assert np.array_equal(Q.slice_symbols(first["x"].numpy(), 64, "fp32"), first["sym"].numpy())
