@@ -43,6 +43,23 @@ def workload_spec(rank=0):
     return s
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """The largest x over the ranks of the default process group (x itself
+    when there is none): the job's time is its slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def job_rate(world, per_rank_units, steps, seconds):
+    """Whole-job throughput: the units every rank processed per step, over
+    the (slowest rank's) time of `steps` steps."""
+    return world * per_rank_units * steps / seconds
+
+
 def bytes_per_detection(N, K):
     """Algorithmic HBM bytes of one detection: read H and y once, write x_hat
     (c64), labels (u8), rel_res (f64) and status (i32)."""
@@ -407,12 +424,8 @@ def main():
             b.record(stream)
         end.record(stream)
         torch.cuda.synchronize(dev)
-        total = start.elapsed_time(end) / 1e3
+        total = max_over_ranks(start.elapsed_time(end) / 1e3, dist, dev)
         per = [a.elapsed_time(b) / 1e3 for a, b in ev]
-        if dist:
-            t = torch.tensor([total], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t[0])
         return total, per
 
     o_head = outputs()
@@ -420,7 +433,7 @@ def main():
     with Clocks(dev) as clk:
         total, per = timed(head, args.steps, args.warmup)
     clocks = clk.summary()
-    det_s = world * B * args.steps / total
+    det_s = job_rate(world, B, args.steps, total)
     ms_step = 1e3 * total / args.steps
     launch_avg = statistics.mean(per)
     if args.only_head:
@@ -447,7 +460,7 @@ def main():
     o_comp = outputs()
     comp = make_call(COMP, o_comp, g)
     c_total, _ = timed(comp, max(2, args.steps // 2), 1)
-    comp_det_s = world * B * max(2, args.steps // 2) / c_total
+    comp_det_s = job_rate(world, B, max(2, args.steps // 2), c_total)
 
     # BER of both paths vs fp64 LMMSE on a sample.  The LMMSE estimate is the
     # library's own fp64 path: CG in fp64 for 2K iterations (exact after K in
@@ -529,7 +542,7 @@ def main():
                      "peak_src": pk["src"], "kernel": "detect (whole path, one launch)",
                      "algorithmic_bytes_per_launch": algo_bytes},
         "cpu_baseline": cpu,
-        "e2e": {"value": world * B * e_steps / e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(world, B, e_steps, e_total), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "comparator": {"name": COMP["name"], "iters": COMP["iters"], "value": comp_det_s, "unit": UNIT,
                        "speedup_of_head": det_s / comp_det_s},
