@@ -96,7 +96,8 @@ def test_fused_matches_oracle(K, gram, mv, L, iters, refine):
 
 def test_fused_headline_config_full_size_sampled():
     """The benchmark's workload and launch: N=256, K=64, 16384 Kronecker
-    channels, BF16 Gram and A p, BJ L=8, 6 + 6 iterations; oracle on a sample."""
+    channels, the head configuration of bench.py (bf16 Gram, fp16 A p, FP-BJ-CG
+    with one refinement pass); oracle on a sample."""
     from bench import HEAD
     spec = wl.c3_kron_256x64()
     d = wl.generate(spec)
