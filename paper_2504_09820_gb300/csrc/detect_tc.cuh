@@ -28,8 +28,11 @@ struct DetectTcParams {
 // (float2 units), row i of a block at i * md_row_stride.  Rows are padded to
 // an even length (16-byte aligned rows for vector loads) and blocks by 4 more
 // entries (successive blocks start on different banks).
-__host__ __device__ constexpr int md_row_stride(int L) { return L + 2; }
-__host__ __device__ constexpr int md_block_stride(int L) { return L * (L + 2) + 4; }
+// L = 4: unpadded rows (32 bytes) and blocks 18 entries apart, so the start of
+// block b moves by one 16-byte chunk per block and the 32 lanes' row loads
+// spread over all eight chunks of a 128-byte window.
+__host__ __device__ constexpr int md_row_stride(int L) { return L == 4 ? 4 : L + 2; }
+__host__ __device__ constexpr int md_block_stride(int L) { return L == 4 ? 18 : L * (L + 2) + 4; }
 
 // One system slot in shared memory (carved in detect_tc_impl.cuh): A + sigma^2 I
 // in the matvec format as [Re A; Im A] (2K x K 16-bit), the fp32 diagonal
@@ -47,21 +50,25 @@ constexpr int kTcCgWarps = 6;       // CG warps, one slot each (at most)
 constexpr int kTcStages32 = 4;      // FP32 TMA ring depth of the fused kernel
 constexpr size_t kTcSmemMax = 227 * 1024;
 
+// FP32 stages of the fused kernel: y of the 64 / K systems of a tile only.
+__host__ __device__ constexpr int tc_stage32_bytes(int K) { return tcp::stage32_bytes(64 / K); }
+
 // Offset of the first slot after the stages, barriers, TMEM address and abort flag.
-__host__ __device__ inline size_t tc_slots_offset() {
-  return (tcp::pipe_bytes(kTcStages32) + sizeof(tcp::Bars) + 2 * kTcCgWarps * sizeof(uint64_t) + 16 + 127) &
+__host__ __device__ inline size_t tc_slots_offset(int K) {
+  return (tcp::pipe_bytes(kTcStages32, tc_stage32_bytes(K)) + sizeof(tcp::Bars) + 2 * kTcCgWarps * sizeof(uint64_t) +
+          16 + 127) &
          ~size_t(127);
 }
 
 // Systems in flight per CTA: as many slots as fit beside the pipeline, one per CG warp.
 inline int tc_num_slots(int K, int L) {
-  const size_t avail = kTcSmemMax - 1024 - tc_slots_offset();
+  const size_t avail = kTcSmemMax - 1024 - tc_slots_offset(K);
   const size_t n = avail / tc_slot_bytes(K, L);
   return n < (size_t)kTcCgWarps ? (int)n : kTcCgWarps;
 }
 
 inline size_t detect_tc_smem_bytes(int K, int L) {
-  const size_t s = 1024 + tc_slots_offset() + tc_num_slots(K, L) * tc_slot_bytes(K, L);
+  const size_t s = 1024 + tc_slots_offset(K) + tc_num_slots(K, L) * tc_slot_bytes(K, L);
   return s < 120 * 1024 ? 120 * 1024 : s;  // one CTA (one 512-column TMEM allocation) per SM
 }
 

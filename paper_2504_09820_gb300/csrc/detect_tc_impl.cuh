@@ -187,11 +187,11 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
     const uint32_t a = tc::smem_u32(smem_raw);
     uint8_t* base = smem_raw + ((1024u - (a & 1023u)) & 1023u);
     S.pipe = base;
-    S.bars = reinterpret_cast<tcp::Bars*>(base + tcp::pipe_bytes(kTcStages32));
+    S.bars = reinterpret_cast<tcp::Bars*>(base + tcp::pipe_bytes(kTcStages32, tc_stage32_bytes(K)));
     S.sbars = reinterpret_cast<Bars2*>(S.bars + 1);
     S.tmem_slot = reinterpret_cast<uint32_t*>(S.sbars + 1);
     S.abort = reinterpret_cast<volatile int*>(S.tmem_slot + 1);
-    S.slots = base + tc_slots_offset();
+    S.slots = base + tc_slots_offset(K);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const tcp::Pipe& pp = P.pipe;
@@ -239,6 +239,7 @@ template <int K, bool BF, int LT>
 cudaError_t launch_k(DetectTcParams P, int num_sms, cudaStream_t stream) {
   const size_t smem = detect_tc_smem_bytes(K, P.L);
   P.nslots = tc_num_slots(K, P.L);
+  P.pipe.s32b = tc_stage32_bytes(K);
   cudaError_t e =
       cudaFuncSetAttribute(detect_tc_kernel<K, BF, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

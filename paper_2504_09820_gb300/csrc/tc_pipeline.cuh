@@ -47,7 +47,9 @@ namespace tcp {
 constexpr int kStages32 = 4;                   // FP32 staging ring (at most; a kernel may use fewer)
 constexpr int kChunk32 = 32;                   // antennas per FP32 stage
 constexpr int kStage32HBytes = 64 * 64 * 4;    // 64 columns x 64 floats
-constexpr int kStage32Bytes = kStage32HBytes + 8 * 64 * 4;  // + y of up to 8 systems
+constexpr int kStage32Bytes = kStage32HBytes + 8 * 64 * 4;  // + y of up to 8 systems (the largest stage)
+// FP32 stage for P systems per tile (a multiple of 128 bytes).
+__host__ __device__ constexpr int stage32_bytes(int P) { return kStage32HBytes + ((64 * 4 * P + 127) & ~127); }
 constexpr int kStages = 2;                     // bf16/fp16 operand stages
 constexpr int kStageRows = 144;
 constexpr int kStageBytes = kStageRows * 128;  // 18432, a multiple of 1024
@@ -55,7 +57,9 @@ constexpr int kChunk = 64;                     // antennas per operand stage
 constexpr int kMmaN = 144;
 constexpr int kAccCols = 256;                  // TMEM columns per accumulator buffer
 // Operand stages first (1024-byte aligned for the 128B swizzle), then the ring.
-__host__ __device__ constexpr int pipe_bytes(int stages32) { return kStages * kStageBytes + stages32 * kStage32Bytes; }
+__host__ __device__ constexpr int pipe_bytes(int stages32, int s32b = kStage32Bytes) {
+  return kStages * kStageBytes + stages32 * s32b;
+}
 constexpr int kPipeBytes = pipe_bytes(kStages32);
 
 struct Pipe {
@@ -66,6 +70,7 @@ struct Pipe {
   int N, K, P, nchunks;   // nchunks = operand stages per tile = ceil(N / 64)
   int64_t batch, ntiles;
   int bf16;
+  int s32b;          // bytes per FP32 stage (stage32_bytes(P) or more)
 };
 
 struct Bars {
@@ -87,8 +92,8 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int bf16) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-__device__ __forceinline__ uint8_t* stage32(uint8_t* pipe_base, int s) {
-  return pipe_base + kStages * kStageBytes + s * kStage32Bytes;
+__device__ __forceinline__ uint8_t* stage32(uint8_t* pipe_base, int s, int s32b) {
+  return pipe_base + kStages * kStageBytes + s * s32b;
 }
 __device__ __forceinline__ uint8_t* stage16(uint8_t* pipe_base, int t) {
   return pipe_base + t * kStageBytes;
@@ -111,7 +116,7 @@ __device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B,
         *abort = 1;
         return;
       }
-      uint8_t* st = stage32(pipe_base, (int)s);
+      uint8_t* st = stage32(pipe_base, (int)s, p.s32b);
       tc::mbar_expect_tx(&B.full32[s], tx);
       tc::tma_load_2d(st, &p.tmH, 64 * c, (int)(tile * 64), &B.full32[s]);
       tc::tma_load_2d(st + kStage32HBytes, &p.tmY, 64 * c, (int)(tile * p.P), &B.full32[s]);
@@ -139,7 +144,7 @@ __device__ inline void converter_role(const Pipe& p, uint8_t* pipe_base, Bars& B
         *abort = 1;
         return;
       }
-      const float* src = reinterpret_cast<const float*>(stage32(pipe_base, (int)(half ? s1 : s0)));
+      const float* src = reinterpret_cast<const float*>(stage32(pipe_base, (int)(half ? s1 : s0), p.s32b));
       uint8_t* dst = stage16(pipe_base, (int)t);
 #pragma unroll
       for (int m = 0; m < NM; ++m) {

@@ -70,6 +70,7 @@ bool make_pipe(tcp::Pipe* p, const float2* H, const float2* y, int N, int K, int
   p->batch = batch;
   p->ntiles = (batch + p->P - 1) / p->P;
   p->bf16 = bf16;
+  p->s32b = tcp::kStage32Bytes;
   return encode(&p->tmH, H, 2ull * N, (uint64_t)batch * K, 64) &&
          encode(&p->tmY, y, 2ull * N, (uint64_t)batch, (uint32_t)p->P);
 }
