@@ -181,7 +181,8 @@ FPCG_API int fpbjcg_detect(const void* H, const void* y, const double* sigma2, c
  *   block_L  0 = FP-CG (Algorithm 2), else FP-BJ-CG (Algorithm 3) with this L
  * prec->gram is ignored; everything else as fpcg_detect.  rel_res, res_hist
  * and status are nullable.  Runs on the tensor-core solver (one warp per
- * system, A rounded to the matvec format in shared memory) for mv in {BF16,
+ * system, four for K = 128; A rounded to the matvec format in shared
+ * memory) for mv in {BF16,
  * FP16}, w = resid = FP32, K in {8, 16, 32, 64, 128} (K = 8 in 16-wide slots
  * holding diag(A, I), b padded with zeros: the same iterates), block_L in {0,
  * 4, 8, 16} and 16-byte aligned A, b; else on the SIMT kernel.

@@ -1,11 +1,12 @@
 #pragma once
 // Tensor-core solver for given Gram matrices (kernel templates; instantiated
 // per K by solve_tc_k{8,16,32,64,128}.cu; K = 8 runs in 16-wide slots holding
-// diag(A, I)).  The CG of the fused detector without its
-// Gram pipeline: A + sigma^2 I comes from global memory (fpcg_gram's output, or
-// the caller's), every warp of a persistent CTA is an independent CG worker
-// with its own shared-memory slot, and systems that share a Gram matrix share
-// the slot's 16-bit A and inverted diagonal blocks.
+// diag(A, I)).  The CG of the fused detector without its Gram pipeline:
+// A + sigma^2 I comes from global memory (fpcg_gram's output, or the
+// caller's), every warp of a persistent CTA is an independent CG worker with
+// its own shared-memory slot (K = 128: four warps per system,
+// solve_split_kernel), and systems that share a Gram matrix share the slot's
+// 16-bit A and inverted diagonal blocks.
 //
 // A warp takes a contiguous range of systems.  When the group changes it
 // rounds the group's fp32 A to the matvec format into the slot ([Re A; Im A],
