@@ -68,18 +68,30 @@ def bytes_per_detection(N, K):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per system of the
 # head kernel from an ncu capture of a 2048-system case of this workload, keyed
-# by the hash of the kernel sources it was taken on; a launch moves the same
-# bytes per system, so it scales with the batch.  None once the kernel changed.
-KERNEL_TRAFFIC = {"b16f68f71c63": 135262.0}
+# by the hash of the head kernel's sources (kernel_source_hash) it was taken
+# on; a launch moves the same bytes per system, so it scales with the batch.
+# None once the kernel changed.
+KERNEL_TRAFFIC = {"7cd74558cf59": 135262.0}
 
 
-def kernel_source_hash():
-    import glob
+def kernel_source_hash(tu="detect_tc_k64.cu"):
+    """sha1 (first 12 hex digits) of the head kernel's translation unit and the
+    csrc headers it includes, transitively, in name order."""
     import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2504_09820_gb300", "csrc")
+    seen, todo = set(), [tu]
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(csrc, f)):
+            continue
+        seen.add(f)
+        with open(os.path.join(csrc, f)) as fh:
+            todo += re.findall(r'^#include "([^"/]+)"', fh.read(), re.M)
     h = hashlib.sha1()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2504_09820_gb300", "csrc", "*.cu*"))):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for f in sorted(seen):
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
