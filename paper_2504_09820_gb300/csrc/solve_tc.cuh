@@ -38,7 +38,7 @@ constexpr int kSolveWarps = 8;  // CG warps per CTA (grouped mode, and independe
 
 // Independent systems, K <= 64: one slot per warp, eight warps per CTA (K = 128
 // runs four warps per system: kSplitWarps below).
-__host__ __device__ constexpr int solve_warps(int K) { return K == 128 ? 2 : kSolveWarps; }
+__host__ __device__ constexpr int solve_warps(int) { return kSolveWarps; }
 
 inline size_t solve_tc_smem_bytes(int K, int L);
 
@@ -50,7 +50,7 @@ __host__ __device__ inline size_t split_group_bytes(int K, int L) { return tc_sl
 inline size_t solve_split_smem_bytes(int K, int L) { return 128 + kSplitGroups * split_group_bytes(K, L); }
 
 inline size_t solve_tc_smem_bytes(int K, int L) {
-  return K == 128 ? solve_split_smem_bytes(K, L) : 128 + solve_warps(K) * tc_slot_bytes(pad_k(K), L);
+  return K == 128 ? solve_split_smem_bytes(K, L) : 128 + kSolveWarps * tc_slot_bytes(pad_k(K), L);
 }
 
 // Grouped mode (fpcg_detect_grouped): all warps of a CTA share one group's A
