@@ -1,4 +1,4 @@
-// Precision selection of Section IV-B (eq. heuristic / heuristic_bj) and a
+// Precision selection of Sections III-B and IV-B (eq. heuristic / heuristic_bj) and a
 // condition-number estimate from CG step sizes.  Host code only.
 #include <math.h>
 

@@ -19,7 +19,7 @@ LMMSE solution at these condition numbers (finite termination).
 
 prints one JSON line per experiment (bit error rates, per variant and point).
 Experiments: mv_ip (Fig. ip_mv), heuristic (Fig. Heuristic), convergence
-(Fig. pcg, with the iteration counts of Section V-C.2), ber_snr (Fig.
+(Fig. pcg, with the iteration counts of Section V-C.3), ber_snr (Fig.
 ber_pcg), csi (Fig. ber_pcg_im), time_varying (Fig. ber_time), users
 (Assumption 1 against eq. 2's full R_t, with kappa(A) and kappa(A_bar) of
 Theorem 5).
@@ -213,7 +213,7 @@ def _detect_by_format(H, d, iters, fmts, L):
 def exp_time_varying(trials, zeta=0.8, snrs=tuple(range(0, 31, 4)), iters=10, fd_hz=1000.0, tau_s=0.5e-3,
                      steps=8, device="cuda"):
     """First-order Gauss-Markov channel over `steps` coherence intervals: the
-    heuristic's format chosen once from E{kappa} (footnote of Section III-C)
+    heuristic's format chosen once from E{kappa} (footnote of Section III-B)
     against the format chosen per system from its own kappa."""
     a = wl.doppler_corr(fd_hz, tau_s)
     c = math.sqrt(max(0.0, 1.0 - a * a))

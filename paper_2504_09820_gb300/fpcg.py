@@ -143,7 +143,7 @@ FORMAT_NAME = {v: k for k, v in FORMAT.items() if k != "fp8"}
 
 
 def fpcg_choose_precision(K, kappa):
-    """(format name, u bound) of the heuristic of Section IV-B (host only)."""
+    """(format name, u bound) of the heuristic of Sections III-B and IV-B (host only)."""
     u = ctypes.c_double()
     rc = lib().fpcg_choose_precision(int(K), float(kappa), ctypes.byref(u))
     if rc < 0:

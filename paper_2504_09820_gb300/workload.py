@@ -259,10 +259,10 @@ def generate_rb(spec):
             "N": spec.N, "K": spec.K}
 
 
-# ---- channel-estimate and time-variation input models (Section V-B) ----------
+# ---- channel-estimate and time-variation input models (Section V-C) ----------
 
 def csi_error(H, eps_db, seed):
-    """Imperfect CSI: H_hat = H + dH (Section V-B), dH i.i.d. CN(0, s2) per
+    """Imperfect CSI: H_hat = H + dH (Section V-C), dH i.i.d. CN(0, s2) per
     entry with the channel-to-error power ratio eps: s2 = P_h 10^(-eps/10),
     where P_h = 1/N is the average power of an entry of H (Omega's variance,
     unit diagonal of R_r and R_t).  H in the storage layout (batch, K, N);
@@ -277,7 +277,7 @@ def csi_error(H, eps_db, seed):
 
 def doppler_corr(fd_hz, tau_s):
     """rho_tau = J_0(2 pi f_d tau), the one-step correlation of the first-order
-    Gauss-Markov channel (Section V-B)."""
+    Gauss-Markov channel (Section V-C)."""
     from scipy.special import j0
     return float(j0(2.0 * np.pi * float(fd_hz) * float(tau_s)))
 
@@ -285,7 +285,7 @@ def doppler_corr(fd_hz, tau_s):
 def gauss_markov(spec, steps, rho_tau):
     """A time-varying channel: H_0 drawn from spec, then H_i = rho_tau H_{i-1}
     + sqrt(1 - rho_tau^2) W_i with W_i drawn from the same spatial model
-    (Section V-B), and at each step new symbols and noise: y_i = H_i x_i + n_i.
+    (Section V-C), and at each step new symbols and noise: y_i = H_i x_i + n_i.
     Returns a list of `steps` dicts shaped like generate()'s (the innovation of
     step i uses seed spec.seed + 7919 i)."""
     out = [generate(spec)]

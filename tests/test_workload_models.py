@@ -1,5 +1,5 @@
 """Input models beyond the i.i.d./Kronecker channel (Section IV-B, Section
-V-B): multi-antenna users with Assumption 1's block R_t, imperfect CSI, the
+V-C): multi-antenna users with Assumption 1's block R_t, imperfect CSI, the
 first-order Gauss-Markov channel, and the GPU-side generator (run here on the
 CPU).  Pinned by their defining statistics, not by the generators' own code."""
 import math
