@@ -197,8 +197,9 @@ FPCG_API int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t ba
  * eq. inversion): A = fl(H)^H fl(H) + sigma2[s] I and b = fl(H)^H fl(y) for
  * every system, fl = rounding of H and y to `gram` (FPCG_BF16 or FPCG_FP16:
  * exact products and fp32 accumulation on the tensor cores -- the tcgen05
- * pipeline for K in {8,16,32,64} with N even and 16-byte aligned H and y,
- * mma.sync for the other K in {8,16,32,64,128} -- and in fp32 FMAs otherwise;
+ * pipeline for K in {8,16,32,64,128} with N even and 16-byte aligned H and y
+ * (and A at K = 128), mma.sync for K in {8,16,32,64,128} otherwise -- and in
+ * fp32 FMAs for other K;
  * FPCG_FP32: fp32; FPCG_FP64: fp64).  The Hermitian A is written in
  * full.  Useful when one A serves many received vectors.
  *   A       [batch][K][K] row-major, c64 (c128 for FPCG_FP64)
