@@ -287,13 +287,13 @@ def run_serve(args):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     F.lib()
-    configs = [(64, 8), (128, 32), (256, 64), (512, 128)]
+    slot_shapes = [(64, 8), (128, 32), (256, 64), (512, 128)]
     slots = {(N, K): SV.pin_slot(wl.generate_rb(wl.RBSpec(N=N, K=K, n_rb=275, rho=0.5, qam=64, snr_db=15.0,
                                                           seed=1005 + K)))
-             for N, K in configs}
+             for N, K in slot_shapes}
     n_req = args.batch or 48
     rng = np.random.default_rng(1005)
-    kinds = [configs[i] for i in rng.integers(0, len(configs), n_req)]
+    kinds = [slot_shapes[i] for i in rng.integers(0, len(slot_shapes), n_req)]
     sizes = rng.integers(48, 3301, n_req).tolist()
     budget = 8 << 30
     srv = SV.Server(budget, n_streams=4, iters=HEAD["iters"], block_L=HEAD["L"], prec=HEAD["prec"], device=dev)
@@ -305,7 +305,7 @@ def run_serve(args):
         return rs
     n_re = sum(SV.SYMBOLS_PER_SLOT * S for S in sizes)
     # warm-up: one full-size slot of every kind (first launches of every kernel), then one pass
-    srv.run([SV.slot_request(i, slots[c], 3300, 0.0) for i, c in enumerate(configs)])
+    srv.run([SV.slot_request(i, slots[c], 3300, 0.0) for i, c in enumerate(slot_shapes)])
     srv.run(requests(np.zeros(n_req)))
     with Clocks(dev) as clk:
         spans = []
@@ -330,7 +330,7 @@ def run_serve(args):
         "value": loads[-1]["p99_ms"], "unit": "ms (p99 at 0.8 of saturation)", "higher_is_better": False,
         "n_gpus": 1, "data": "synthetic", "dtype": "bf16-in/f32-acc",
         "config": {"workload": f"{n_req} slot requests: 14 symbols x S subcarriers, S uniform 48..3300, "
-                               f"(N,K) uniform in {configs}, rho 0.5, 64-QAM, 15 dB, one Gram per 12-subcarrier "
+                               f"(N,K) uniform in {slot_shapes}, rho 0.5, 64-QAM, 15 dB, one Gram per 12-subcarrier "
                                f"block kept across the slot",
                    "method": HEAD["name"], "block_L": f"min({HEAD['L']}, K)", "iters": HEAD["iters"],
                    "precision": HEAD["prec"], "budget_bytes": budget, "streams": 4,

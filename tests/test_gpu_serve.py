@@ -11,7 +11,7 @@ from paper_2504_09820_gb300 import workload as wl
 
 pytestmark = pytest.mark.gpu
 
-CONFIGS = [(64, 8), (128, 32), (256, 64), (512, 128)]
+SLOT_SHAPES = [(64, 8), (128, 32), (256, 64), (512, 128)]
 
 
 @pytest.fixture(scope="module")
@@ -21,7 +21,7 @@ def slots():
     F.lib()
     return {(N, K): SV.pin_slot(wl.generate_rb(wl.RBSpec(N=N, K=K, n_rb=10, rho=0.5, qam=64, snr_db=15.0,
                                                           seed=70 + K)))
-            for N, K in CONFIGS}
+            for N, K in SLOT_SHAPES}
 
 
 def _outputs(r):
@@ -40,7 +40,7 @@ def test_alone_equals_in_mix_and_direct(slots):
     # the same request among others that arrive while it runs
     mix = [SV.slot_request(0, slots[(256, 64)], 100, 0.002)]
     for i in range(1, 9):
-        N, K = CONFIGS[rng.integers(len(CONFIGS))]
+        N, K = SLOT_SHAPES[rng.integers(len(SLOT_SHAPES))]
         mix.append(SV.slot_request(i, slots[(N, K)], int(rng.integers(12, 121)), float(rng.uniform(0, 0.004))))
     srv.run(mix)
     assert all(r.done is not None for r in mix)
