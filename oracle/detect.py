@@ -284,12 +284,26 @@ def fp_cg(A_mv, b, iters, mv, ip="fp32", w="fp32", Md=None, alpha_num=0,
 # ---------------------------------------------------------------------------
 
 DEFAULT_PREC = {"gram": "fp32", "mv": "fp32", "ip": "fp32", "w": "fp32",
-                "refine_steps": 0, "refine_iters": None, "alpha_num": 0, "resid": "fp32"}
+                "refine_steps": 0, "refine_iters": None, "alpha_num": 0, "resid": "gram"}
+
+# Matrix of the refinement residual and of rel_res (prec["resid"]); "fp64" and
+# "fp32" are the C ABI's names for "gram" and "mv".
+RESID_MODES = {"gram": "gram", "fp64": "gram", "mv": "mv", "fp32": "mv", "h": "h"}
 
 
 def resid(A, x, b):
     """b - A x formed in float64 (the refinement residual and final check)."""
     return _c128(b) - np.einsum("bkl,bl->bk", _c128(A), _c128(x))
+
+
+def resid_h(H, y, sigma2, x):
+    """H^H (y - H x) - sigma^2 x from the stored (complex64) H and y, in float64:
+    the residual of the LMMSE system of Section II (eq. inversion) itself, with
+    no Gram matrix formed.  H in storage layout (batch, K, N)."""
+    Hs = _c128(H)
+    x = _c128(x)
+    e = _c128(y) - np.einsum("bkn,bk->bn", Hs, x)                 # y - H x
+    return np.einsum("bkn,bn->bk", np.conj(Hs), e) - np.asarray(sigma2, dtype=np.float64)[:, None] * x
 
 
 def detect(H, y, sigma2, qam_order, iters, prec=None, L=None, block=32):
@@ -299,14 +313,25 @@ def detect(H, y, sigma2, qam_order, iters, prec=None, L=None, block=32):
     "e4m3"), refine_steps, refine_iters (default: iters), alpha_num, resid.
     L: block-Jacobi block size (None = FP-CG, Algorithm 2).
 
-    resid selects the matrix of the refinement residual and of rel_res:
-    "fp32" -- the matrix the matvec uses (A rounded to u_MV), "fp64" -- the
-    Gram matrix A itself.  Either residual is formed exactly here (the GPU
-    sums it at fp32, or with fp64-class compensated sums for "fp64").
+    Iterative refinement (not in the paper; Theorem 2 of Section III-B is its
+    motivation: the attainable accuracy of FP-CG is limited by the gap between
+    the true residual b - A x and the recursively updated r, which grows with
+    u_MV, so the true residual is recomputed above the working precision and
+    a correction is solved for).  resid selects the residual, always formed in
+    float64, that drives the corrections and defines rel_res:
+      "gram" (default, C ABI FPCG_FP64): b - A x with A, b the Gram matrix and
+             matched filter of the gram step (for gram = fp64 the exact ones);
+      "mv"   (C ABI FPCG_FP32): b - A_mv x with A rounded to u_MV, the matrix
+             the CG products use -- refinement then removes only the CG
+             iteration error, not the rounding of A;
+      "h":   H^H (y - H x) - sigma^2 x from the stored H and y (resid_h) -- the
+             residual of the unrounded LMMSE system; rel_res divides by
+             ||H^H y||.
     """
     pr = dict(DEFAULT_PREC)
     pr.update(prec or {})
     w = pr["w"]
+    mode = RESID_MODES[pr.get("resid", "gram")]
     A, b = gram_emul(H, y, sigma2, pr["gram"])
     B = A.shape[0]
     status = np.zeros(B, dtype=np.int32)
@@ -315,17 +340,27 @@ def detect(H, y, sigma2, qam_order, iters, prec=None, L=None, block=32):
         Md, fail = bj_inverse(A, L, w)
         status[fail] |= ST_BJ_FAIL
     A_mv = round_matvec_operand(A, pr["mv"], block)
-    A_res = A if (pr.get("resid", "fp32") == "fp64" or w == "fp64") else A_mv
+    if mode == "h":
+        _, b_ref = gram_mf(H, y, sigma2)
+
+        def true_res(x):
+            return resid_h(H, y, sigma2, x)
+    else:
+        A_res = A_mv if mode == "mv" else A
+        b_ref = b
+
+        def true_res(x):
+            return resid(A_res, x, b)
     x, st, hist, _ = fp_cg(A_mv, b, iters, pr["mv"], pr["ip"], w, Md, pr["alpha_num"], block)
     status |= st
     ri = pr["refine_iters"] if pr["refine_iters"] is not None else iters
     for _ in range(int(pr["refine_steps"])):
-        rr = flc(resid(A_res, x, b), w)
+        rr = flc(true_res(x), w)
         d, st2, _, _ = fp_cg(A_mv, rr, ri, pr["mv"], pr["ip"], w, Md, pr["alpha_num"], block)
         status |= st2 & ST_BREAKDOWN
         x = flc(x + d, w)
-    nb = np.linalg.norm(_c128(b), axis=1)
-    nr = np.linalg.norm(resid(A_res, x, b), axis=1)
+    nb = np.linalg.norm(_c128(b_ref), axis=1)
+    nr = np.linalg.norm(true_res(x), axis=1)
     rel = np.where(nb > 0, nr / np.where(nb > 0, nb, 1.0), 0.0)
     status[~np.all(np.isfinite(x), axis=1)] |= ST_NONFINITE
     qam_order = np.broadcast_to(np.asarray(qam_order), (B,))

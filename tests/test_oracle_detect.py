@@ -204,14 +204,60 @@ def test_refinement_with_exact_inner_solve():
 
 
 def test_refinement_recovers_reduced_precision_loss():
+    """Each refinement pass brings x closer to the solution of the Gram system
+    (the default residual is b - A x on the Gram matrix itself)."""
     d = wl.generate(wl.Spec(N=128, K=32, batch=64, rho=0.5, qam=64, snr_db=20.0, seed=5))
-    A, b = D.gram_mf(d["H"], d["y"], d["sigma2"])
+    A, b = D.gram_emul(d["H"], d["y"], d["sigma2"], "bf16")
     xs = _solve(A, b)
     e = []
     for rs in (0, 1, 2):
         r = D.detect(d["H"], d["y"], d["sigma2"], 64, 8, {"gram": "bf16", "mv": "bf16", "refine_steps": rs}, L=8)
         e.append(np.median(np.linalg.norm(r["x"] - xs, axis=1) / np.linalg.norm(xs, axis=1)))
-    assert e[0] > e[1] > e[2]
+    assert e[0] > 10 * e[1] > 100 * e[2]
+
+
+def test_refinement_one_step_with_exact_inner_solve_is_exact():
+    """Iterative refinement is Newton's method on the linear system: from a
+    reduced-precision iterate x0, x0 + A^-1 r(x0) is the solution, to FP64
+    accuracy, for the residual of the Gram system and for the residual formed
+    from H and y without any Gram matrix (eq. inversion)."""
+    d = wl.generate(wl.Spec(N=64, K=16, batch=16, rho=0.5, qam=16, snr_db=15.0, seed=21))
+    Aq, bq = D.gram_emul(d["H"], d["y"], d["sigma2"], "bf16")
+    x0, _, _, _ = D.fp_cg(D.round_matvec_operand(Aq, "bf16"), bq, 3, "bf16")
+    xq = _solve(Aq, bq)
+    assert np.median(np.linalg.norm(x0 - xq, axis=1) / np.linalg.norm(xq, axis=1)) > 1e-3
+    x1 = x0 + D.cholesky_solve(Aq, D.resid(Aq, x0, bq))
+    assert np.max(np.linalg.norm(x1 - xq, axis=1) / np.linalg.norm(xq, axis=1)) < 1e-13
+    A64, b64 = D.gram_mf(d["H"], d["y"], d["sigma2"])
+    xs = D.cholesky_solve(A64, b64)                        # the unrounded LMMSE solution
+    x1h = x0 + D.cholesky_solve(A64, D.resid_h(d["H"], d["y"], d["sigma2"], x0))
+    assert np.max(np.linalg.norm(x1h - xs, axis=1) / np.linalg.norm(xs, axis=1)) < 1e-13
+
+
+@pytest.mark.parametrize("mode", ["gram", "mv", "h"])
+def test_refinement_fixed_point_is_the_residual_systems_solution(mode):
+    """Repeated refinement with a contracting reduced-precision inner solver
+    converges to the solution of the system whose residual drives it: the Gram
+    system (A, b) for "gram", the matvec matrix's system (A_mv, b) for "mv",
+    the unrounded LMMSE system for "h" -- and not to the other two."""
+    d = wl.generate(wl.Spec(N=64, K=16, batch=32, rho=0.3, qam=16, snr_db=20.0, seed=9))
+    pk = {"gram": "bf16", "mv": "fp16", "refine_steps": 6, "refine_iters": 8, "resid": mode}
+    r = D.detect(d["H"], d["y"], d["sigma2"], 16, 8, pk, L=4)
+    Aq, bq = D.gram_emul(d["H"], d["y"], d["sigma2"], "bf16")
+    A64, b64 = D.gram_mf(d["H"], d["y"], d["sigma2"])
+    sols = {"gram": _solve(Aq, bq), "mv": _solve(D.round_matvec_operand(Aq, "fp16"), bq), "h": _solve(A64, b64)}
+    err = {k: np.median(np.linalg.norm(r["x"] - v, axis=1) / np.linalg.norm(v, axis=1)) for k, v in sols.items()}
+    assert err[mode] < 2e-6, err                           # fp32 working precision
+    for other in sols:
+        if other != mode:
+            assert err[other] > 20 * err[mode], err
+    # rel_res is the residual of that system at the returned x
+    if mode == "h":
+        want = np.linalg.norm(D.resid_h(d["H"], d["y"], d["sigma2"], r["x"]), axis=1) / np.linalg.norm(b64, axis=1)
+    else:
+        Ar = Aq if mode == "gram" else D.round_matvec_operand(Aq, "fp16")
+        want = np.linalg.norm(D.resid(Ar, r["x"], bq), axis=1) / np.linalg.norm(bq, axis=1)
+    assert np.allclose(r["rel_res"], want, rtol=1e-12, atol=0)
 
 
 def test_zero_rhs_and_zero_iterations():
