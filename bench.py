@@ -32,7 +32,7 @@ UNIT = "detections/s"
 
 # Headline configuration (FP-BJ-CG) and the plain fp32 CG comparator.
 HEAD = dict(name="FP-BJ-CG", L=4, iters=7,
-            prec=dict(gram="bf16", mv="fp16", ip="fp32", w="fp32", refine_steps=1, refine_iters=7))
+            prec=dict(gram="bf16", mv="fp16", ip="fp32", w="fp32", refine_steps=1, refine_iters=7, resid="fp64"))
 COMP = dict(name="FP32 plain CG", L=None, iters=20,
             prec=dict(gram="fp32", mv="fp32", ip="fp32", w="fp32", refine_steps=0))
 

@@ -30,7 +30,14 @@
  *     default stream).  The return code reports argument errors and launch
  *     failures only; numerical trouble in a system is reported through that
  *     system's status word and never aborts the batch.
- *   - Entry points are thread-safe; they allocate no device memory.
+ *   - Entry points are thread-safe.  None calls cudaMalloc or another
+ *     allocator, except the batch-plan functions, which own device
+ *     workspace for two-pass classes (see the plan section).  Two paths use
+ *     fixed device arrays of the library instead (static storage, held by
+ *     every process that loads it): the fused tensor-core kernel's residual
+ *     against the Gram matrix (resid = FPCG_FP64; a pool of one region per
+ *     SM, 30 MiB at K = 64, shared safely by concurrent calls, since at most
+ *     one of its CTAs runs per SM), and fpcg_detect_noalloc (below).
  */
 #ifndef FPCG_H
 #define FPCG_H
@@ -98,11 +105,21 @@ enum {
  *                 writes it, 1 = r^H z (textbook PCG); equal in exact arithmetic.
  *   fp8_block     e4m3 scale block in real components; must be 32.
  *   resid         the residual b - A x of the refinement and of rel_res:
+ *                 FPCG_FP64 = A is the Gram matrix as formed (fp32 entries),
+ *                 i.e. the refinement converges to the solution of the Gram
+ *                 system itself.  On the fused tensor-core kernel A enters as
+ *                 its matvec copy A16 plus the 16-bit remainder pieces of
+ *                 fl32(A) - A16 (one for fp16: 22 of the 24 significand bits,
+ *                 two for bf16: all 24), products exact, fp32 sums, so the
+ *                 residual is within about 2^-22 |A||x| of the exact one; the
+ *                 SIMT kernel uses compensated double-fp32 products and sums
+ *                 (fp64-accurate; GB300's fp64 units are far slower).
  *                 FPCG_FP32 = A is the matvec matrix (A rounded to u_MV) and
- *                 the sums are fp32 (both kernels); FPCG_FP64 = A is the fp32
- *                 Gram matrix and the sums are fp64-accurate (compensated
- *                 double-fp32 products and sums, far cheaper than fp64 units
- *                 on GB300; SIMT kernel).  The fp64 mode always uses fp64.
+ *                 the sums are fp32: refinement then removes the CG iteration
+ *                 error only, not the rounding of A (cheaper; both kernels,
+ *                 and the only mode of the solvers for given Gram matrices'
+ *                 tensor-core paths).  rel_res is always the ratio of the two
+ *                 norms formed in fp64.  The fp64 mode always uses fp64.
  */
 typedef struct fpcg_precision {
   int32_t gram;
@@ -213,8 +230,8 @@ FPCG_API int fpcg_gram(const void* H, const void* y, const double* sigma2, int32
 /*
  * fpcg_path -- which kernel fpcg_detect / fpbjcg_detect (block_L = 0 for
  * FP-CG) would use for this configuration: FPCG_PATH_TENSOR_CORE (the fused
- * tcgen05 Gram + mma.sync CG kernel: gram and mv in {BF16, FP16}, w = resid
- * = FP32, K in {16, 32, 64}, L in {0, 4, 8, 16}, N even; H and y must also be
+ * tcgen05 Gram + mma.sync CG kernel: gram and mv in {BF16, FP16}, w = FP32,
+ * resid in {FP32, FP64}, K in {16, 32, 64}, L in {0, 4, 8, 16}, N even; H and y must also be
  * 16-byte aligned, which this query cannot see) or FPCG_PATH_SIMT (one CTA per system, every
  * other configuration); FPCG_EINVAL (negative) for an invalid configuration.
  * Setting the environment variable FPCG_FORCE_SIMT=1 makes every call take

@@ -51,6 +51,16 @@ __device__ __forceinline__ uint32_t a16_offset(int r, int chunk) {
   return (uint32_t)(r * (2 * K) + ((chunk ^ ((r >> SH) & MASK)) << 4));
 }
 
+// Byte offset of the 512-byte block holding one m16n8k16 A fragment (lane l's
+// four registers at 16 l) of remainder piece pc, part pr (0: Re A, 1: Im A),
+// m-tile mt and k-tile kt of a [2K][K] 16-bit matrix.  Element (r, c) of the
+// 16 x 16 tile sits in lane (r % 8) * 4 + (c % 8) / 2, register r / 8 + 2 (c / 8),
+// half c % 2.
+template <int K>
+__device__ __forceinline__ uint32_t rem_block(int pc, int pr, int mt, int kt) {
+  return (uint32_t)((((pc * 2 + pr) * (K / 16) + mt) * (K / 16) + kt) * 512);
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -157,7 +167,12 @@ __device__ __noinline__ float round_ip(float v, int fmt) { return round_to(v, fm
 // barriers (id bar_id), and warp sj packs and writes the rows lane + 32e with
 // e % NS == sj.  The preconditioner stages r in a warp-private buffer (rst),
 // since the slot's W is shared.
-template <int K, bool BF, int LT, int KR = K, int NV = 1, int NS = 1>
+//
+// RM = 1: a residual trip also applies the remainder A - A16 of the fp32 Gram
+// matrix (tc_rem_pieces 16-bit pieces, fragment order, at `rem`; skipped while
+// rem is null), so that b - A x is formed against the fp32 Gram to within
+// about 2^-22 of |A||x| (fp16) instead of against A16.
+template <int K, bool BF, int LT, int KR = K, int NV = 1, int NS = 1, int RM = 0>
 struct CgWarp {
   static constexpr int KT = K / 16;          // k-tiles (16 users)
   static constexpr int MT = K / 16;          // m-tiles of Re A (and of Im A)
@@ -174,6 +189,7 @@ struct CgWarp {
   int vst = 0;
   int sj = 0, bar_id = 0;    // NS > 1: this warp's index in its system's group, the group's barrier
   float2* rst = nullptr;     // NS > 1: warp-private staging of r for the preconditioner
+  const uint8_t* rem = nullptr;  // RM = 1: this slot's remainder pieces (global scratch)
 
   // NS > 1: rows lane + 32e this warp writes (packs, outputs)
   __device__ __forceinline__ bool mine(int e) const { return NS == 1 || e % NS == sj; }
@@ -327,11 +343,65 @@ struct CgWarp {
     }
   }
 
+  // Remainder fragments of round i = piece * MT + m-tile (both parts), from
+  // src: the global scratch, or the slot's A16 region once they are staged there.
+  __device__ __forceinline__ void rem_load(const uint8_t* src, int i, uint4 (&q)[2][KT]) {
+    const int pc = i / MT, mt = i % MT;
+    if (src == rem) {  // global scratch
+      const uint64_t keep = tc::policy_evict_last();
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) {
+        q[0][kt] = tc::ld_global_hint(src + rem_block<K>(pc, 0, mt, kt) + 16 * lane, keep);
+        q[1][kt] = tc::ld_global_hint(src + rem_block<K>(pc, 1, mt, kt) + 16 * lane, keep);
+      }
+    } else {  // staged in the slot
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) {
+        q[0][kt] = *reinterpret_cast<const uint4*>(src + rem_block<K>(pc, 0, mt, kt) + 16 * lane);
+        q[1][kt] = *reinterpret_cast<const uint4*>(src + rem_block<K>(pc, 1, mt, kt) + 16 * lane);
+      }
+    }
+  }
+
+  // W -= (A - A16) x after the A16 part of a residual trip: one m-tile (of
+  // one remainder piece) per round, the next round's fragments loaded while
+  // this round's products are combined.  Rows of W belong to the lanes t = 0
+  // that wrote them.
+  __device__ __forceinline__ void rem_apply(const uint8_t* src, const uint32_t (&b0)[KT], const uint32_t (&b1)[KT],
+                                            uint4 (&q)[2][KT]) {
+    constexpr int NR = tc_rem_pieces(BF) * MT;
+#pragma unroll 1
+    for (int i = 0; i < NR; ++i) {
+      float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) {
+        const uint32_t ar[4] = {q[0][kt].x, q[0][kt].y, q[0][kt].z, q[0][kt].w};
+        const uint32_t ai[4] = {q[1][kt].x, q[1][kt].y, q[1][kt].z, q[1][kt].w};
+        mma16<BF>(cr, ar, b0[kt], b1[kt]);
+        mma16<BF>(ci, ai, b0[kt], b1[kt]);
+      }
+      if (i + 1 < NR) rem_load(src, i + 1, q);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {  // the mid (t = 1) and lo (t = 2) column products into t = 0
+        cr[u] += __shfl_down_sync(0xffffffffu, cr[u], 1) + __shfl_down_sync(0xffffffffu, cr[u], 2);
+        ci[u] += __shfl_down_sync(0xffffffffu, ci[u], 1) + __shfl_down_sync(0xffffffffu, ci[u], 2);
+      }
+      if (t == 0) {
+        const int mt = i % MT;
+        float2* w0 = S.W + 16 * mt + g;
+        const float2 a0 = w0[0], a8 = w0[8];
+        w0[0] = make_float2(a0.x - (cr[0] - ci[1]), a0.y - (cr[1] + ci[0]));
+        w0[8] = make_float2(a8.x - (cr[2] - ci[3]), a8.y - (cr[3] + ci[2]));
+      }
+    }
+  }
+
   // W = A v (res = false) or W = b - A v (res = true: the three column pairs
   // of v are summed), one m-tile (16 rows of Re A and of Im A) at a time; lane
   // (g, t) holds C rows g, g+8 and columns 2t, 2t+1.  Then w = W in the vector
   // layout.
-  __device__ __forceinline__ void apply(bool res, float2 (&w)[E]) {
+  // last: this residual is the system's final one (the slot's A16 is free afterwards).
+  __device__ __forceinline__ void apply(bool res, float2 (&w)[E], bool last = false) {
     if constexpr (NV > 1) {
       apply_cta(res, w);
       return;
@@ -353,6 +423,24 @@ struct CgWarp {
       constexpr int MP = MT >= 2 ? 2 : 1;
 #pragma unroll 1
       for (int mt = 0; mt < MT; mt += MP) apply_mtiles<MP>(mt, res, b0, b1);
+      if constexpr (RM == 1)
+        if (res && rem != nullptr) {
+          const uint8_t* src = rem;
+          if (last && tc_rem_pieces(BF) == 1) {  // A16 (as large as one piece) is not read again:
+            // stage the remainder there, one round trip from L2 for all of it
+            constexpr int kChunks = (int)tc_rem_piece_bytes(K) / 512;
+            const uint32_t dst = tc::smem_u32(S.A16);
+            __syncwarp();  // every lane's reads of A16 come first
+#pragma unroll 4
+            for (int c = 0; c < kChunks; ++c) tc::cp_async16(dst + 512 * c + 16 * lane, rem + 512 * c + 16 * lane);
+            tc::cp_async_wait_all();  // each lane reads back only the bytes it copied
+            src = S.A16;
+          }
+          uint4 q[2][KT];
+          rem_load(src, 0, q);
+          __syncwarp();
+          rem_apply(src, b0, b1, q);
+        }
     }
     __syncwarp();
     gsync();  // NS > 1: every m-tile of W is written
@@ -559,7 +647,7 @@ struct CgWarp {
 #pragma unroll
         for (int e = 0; e < E; ++e) w[e] = rt ? x[e] : p[e];
         pack(w, rt);
-        apply(rt, w);
+        apply(rt, w, rt && pass >= refine_steps);
         if (rt) {
 #pragma unroll
           for (int e = 0; e < E; ++e) r[e] = w[e];  // r = b - A x
@@ -623,7 +711,7 @@ struct CgWarp {
     }
 
     if (!valid) return;
-    float nr = 0.f, nb = 0.f;
+    float nr = 0.f, nb = 0.f;  // squared norms of the final residual and of b (the ratio in fp64)
     int nonfinite = 0;
     unsigned errs = 0;
     const int m = qam_sqrt(M);
@@ -633,8 +721,8 @@ struct CgWarp {
 #pragma unroll  // x, r, txv stay in registers only with static indices
       for (int e = 0; e < E; ++e) {
         const float2 bv = S.b[lane + 32 * e];
-        nr += r[e].x * r[e].x + r[e].y * r[e].y;
-        nb += bv.x * bv.x + bv.y * bv.y;
+        nr = fmaf(r[e].x, r[e].x, fmaf(r[e].y, r[e].y, nr));
+        nb = fmaf(bv.x, bv.x, fmaf(bv.y, bv.y, nb));
         const int k = lane + 32 * e;
         if (!(isfinite(x[e].x) && isfinite(x[e].y))) nonfinite = 1;
         if (!vout(e) || !mine(e)) continue;
@@ -658,7 +746,7 @@ struct CgWarp {
       if (lane == 0 && errs) atomicAdd(P.bit_errors, (unsigned long long)errs);
     }
     if (lane == 0 && sj == 0) {
-      if (P.rel_res) P.rel_res[sys] = nb > 0.f ? (double)sqrtf(nr / nb) : 0.0;
+      if (P.rel_res) P.rel_res[sys] = nb > 0.f ? sqrt((double)nr / (double)nb) : 0.0;
       if (nonfinite) st |= 4;
       if (want_sym && m == 0) st |= 16;
       if (P.status) P.status[sys] = st;

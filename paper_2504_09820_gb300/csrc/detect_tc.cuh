@@ -14,7 +14,8 @@ struct DetectTcParams {
   const double* sigma2;
   const int32_t* qam;
   int iters, L, refine_steps, refine_iters, alpha_num, ip;
-  int nslots;  // systems in flight per CTA (tc_num_slots)
+  int nslots;      // systems in flight per CTA (tc_num_slots)
+  int resid_gram;  // fused kernel: residuals against the fp32 Gram (remainder pieces in global scratch)
   float2* x_hat;
   uint8_t* sym;
   double* rel_res;
@@ -47,6 +48,18 @@ __host__ __device__ inline size_t tc_slot_bytes(int K, int L) {
 }
 
 constexpr int kTcCgWarps = 6;       // CG warps, one slot each (at most)
+
+// Remainder of the fp32 Gram matrix beyond its matvec-format copy, for the
+// residual b - A x of the fused kernel: A - A16 as one more 16-bit piece
+// (fp16: 11 + 11 significant bits of the 24) or two (bf16: 8 + 8 + 8), in
+// mma.sync A-fragment order, kept in a device scratch pool (one region per
+// resident CTA, at most one CTA per SM) instead of shared memory.
+constexpr int kTcScratchRegions = 160;  // >= SMs of the GPU (checked at launch)
+__host__ __device__ constexpr int tc_rem_pieces(bool bf16) { return bf16 ? 2 : 1; }
+__host__ __device__ constexpr size_t tc_rem_piece_bytes(int K) { return 4 * (size_t)K * K; }
+__host__ __device__ constexpr size_t tc_rem_region_bytes(int K) {
+  return (size_t)kTcCgWarps * 2 * tc_rem_piece_bytes(K);
+}
 constexpr int kTcStages32 = 4;      // FP32 TMA ring depth of the fused kernel
 constexpr size_t kTcSmemMax = 227 * 1024;
 

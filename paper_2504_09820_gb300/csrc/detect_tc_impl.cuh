@@ -24,9 +24,12 @@
 //   * Algorithm 2 / 3: one or two rows of every vector per lane, inner
 //     products by warp shuffles (u_IP rounding), z = M_d r by shuffles within
 //     the block's lanes, updates by FMA at u_W = fp32;
-//   * refinement: r = b - A x on the tensor cores with the same A and
-//     x = x_hi + x_mid + x_lo split over B columns, a correction solve,
-//     x += d; rel_res; Gray-QAM decision; bit errors.
+//   * refinement: r = b - A x on the tensor cores with x = x_hi + x_mid +
+//     x_lo split over B columns and A the fp32 Gram matrix, as A16 plus its
+//     16-bit remainder pieces (written by the drain into a global scratch
+//     region of this CTA, read back by the residual trips; with resid_gram
+//     off, A16 alone), a correction solve, x += d; rel_res (norms in fp64);
+//     Gray-QAM decision; bit errors.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,13 +60,29 @@ struct Smem {
   Bars2* sbars;
   uint32_t* tmem_slot;
   volatile int* abort;
+  int* region;       // this CTA's scratch region (-1: none)
   uint8_t* slots;
 };
+
+// Scratch pool of the remainder pieces: one region per resident CTA.  The
+// kernel needs more than half of an SM's shared memory, so at most one of its
+// CTAs (of any K) runs per SM, and kTcScratchRegions >= the SM count leaves a
+// free region for every CTA that starts.  A CTA takes one with atomicCAS and
+// gives it back before it exits.
+template <int K>
+__device__ __align__(256) uint8_t g_rem[(size_t)kTcScratchRegions * tc_rem_region_bytes(K)];
+template <int K>
+__device__ int g_rem_busy[kTcScratchRegions];
+
+template <int K>
+__device__ __forceinline__ uint8_t* rem_slot(int region, int slot) {
+  return g_rem<K> + (size_t)region * tc_rem_region_bytes(K) + (size_t)slot * 2 * tc_rem_piece_bytes(K);
+}
 
 // Drain warpgroup: tile j of this CTA (TMEM buffer j & 1) holds systems
 // seq = j*P + p, p < P, which go to slots seq % nslots.  Thread = TMEM lane =
 // row 2k + odd of its system's block.
-template <int K, bool BF, int LT>
+template <int K, bool BF, int LT, int RG>
 __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem, int64_t tile0, int64_t tstep) {
   const tcp::Pipe& pp = P.pipe;
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -76,6 +95,7 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
   const int blk0 = ps * twoK;
   const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
   const size_t slot_bytes = tc_slot_bytes(K, LT);
+  const uint64_t keep = tc::policy_evict_last();  // remainder pieces: read back by the CG warps
   int64_t j = 0;
   for (int64_t tile = tile0; tile < pp.ntiles; tile += tstep, ++j) {
     const uint32_t b = (uint32_t)(j & 1), qa = (uint32_t)(j >> 1);
@@ -94,7 +114,9 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
     }
     tc::tc_fence_after();
     const uint32_t tb = lane_base + b * (uint32_t)tcp::kAccCols;
-    Slot sl = slot_carve(S.slots + ((j * PP + ps) % ns) * slot_bytes, K, LT);
+    const int slot = (int)((j * PP + ps) % ns);
+    Slot sl = slot_carve(S.slots + slot * slot_bytes, K, LT);
+    uint8_t* rem = (RG && *S.region >= 0) ? rem_slot<K>(*S.region, slot) : nullptr;
     const int arow = odd ? K + k : k;           // row of [Re A; Im A]
     const int kb0 = (k / (LT > 0 ? LT : 1)) * LT;  // first column of k's diagonal block
 #pragma unroll 1
@@ -103,9 +125,9 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
       tc::tmem_ld16_async(tb + (uint32_t)cg, v[0]);
       tc::tmem_ld16_async(tb + (uint32_t)(cg + 16), v[1]);
       tc::tmem_wait_ld();
+      float a[2][8];  // columns l0(u) .. l0(u) + 7 of row arow, u = 0, 1: one k-tile
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        float a[8];
         const int l0 = (cg + 16 * u - blk0) >> 1;  // first of the 8 columns l of this chunk
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -114,21 +136,62 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
           float val = odd ? (other - vm) : (vm + other);
           if (!valid) val = 0.f;
           if (l0 + m == k) val = odd ? 0.f : val + s2;
-          a[m] = val;
+          a[u][m] = val;
         }
+      }
+      if (RG && rem) {
+        // A - A16 in 16-bit pieces, in mma A-fragment order (rem_block): the warp
+        // owns one m-tile (16 rows of Re A and of Im A); each piece of this
+        // k-tile goes row-major through the slot's A16 area (rewritten below)
+        // and comes back by ldmatrix as fragments, one 16-byte store per lane.
+        const int kt = (cg - blk0) >> 5, mt = (k & (K - 1)) >> 4;
+        float lo[2][8];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int m = 0; m < 8; ++m) lo[u][m] = a[u][m] - round16<BF>(a[u][m]);  // exact
+#pragma unroll
+        for (int pc = 0; pc < tc_rem_pieces(BF); ++pc) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            uint4 q;
+            q.x = pk2<BF>(lo[u][0], lo[u][1]);
+            q.y = pk2<BF>(lo[u][2], lo[u][3]);
+            q.z = pk2<BF>(lo[u][4], lo[u][5]);
+            q.w = pk2<BF>(lo[u][6], lo[u][7]);
+            *reinterpret_cast<uint4*>(sl.A16 + a16_offset<K>(arow, 2 * kt + u)) = q;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) lo[u][m] -= round16<BF>(lo[u][m]);  // exact
+          }
+          __syncwarp();
+          const uint32_t abase = tc::smem_u32(sl.A16);
+          const int lr = lane & 15, lc = lane >> 4;
+#pragma unroll
+          for (int pr = 0; pr < 2; ++pr) {
+            uint32_t f[4];
+            tc::ldmatrix_x4(f, abase + a16_offset<K>(pr * K + 16 * mt + lr, 2 * kt + lc));
+            tc::st_global_hint(rem + rem_block<K>(pc, pr, mt, kt) + 16 * lane, make_uint4(f[0], f[1], f[2], f[3]),
+                               keep);
+          }
+          __syncwarp();
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int l0 = (cg + 16 * u - blk0) >> 1;
         // 8 columns -> one 16-byte chunk of row arow
         uint4 pkd;
-        pkd.x = pk2<BF>(a[0], a[1]);
-        pkd.y = pk2<BF>(a[2], a[3]);
-        pkd.z = pk2<BF>(a[4], a[5]);
-        pkd.w = pk2<BF>(a[6], a[7]);
+        pkd.x = pk2<BF>(a[u][0], a[u][1]);
+        pkd.y = pk2<BF>(a[u][2], a[u][3]);
+        pkd.z = pk2<BF>(a[u][4], a[u][5]);
+        pkd.w = pk2<BF>(a[u][6], a[u][7]);
         *reinterpret_cast<uint4*>(sl.A16 + a16_offset<K>(arow, l0 >> 3)) = pkd;
         if constexpr (LT > 0) {
 #pragma unroll
           for (int m = 0; m < 8; ++m) {
             const int l = l0 + m;
             if (l >= kb0 && l < kb0 + LT)
-              reinterpret_cast<float*>(sl.Md + (k / LT) * MBS + (k % LT) * MLD + (l - kb0))[odd] = a[m];
+              reinterpret_cast<float*>(sl.Md + (k / LT) * MBS + (k % LT) * MLD + (l - kb0))[odd] = a[u][m];
           }
         }
       }
@@ -150,14 +213,16 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
 }
 
 // CG warp c: every system whose slot is c, in order.
-template <int K, bool BF, int LT>
+template <int K, bool BF, int LT, int RG>
 __device__ void cg_role(const DetectTcParams& P, const Smem& S, int c, int64_t tile0, int64_t tstep) {
   const tcp::Pipe& pp = P.pipe;
   const int lane = threadIdx.x & 31;
   constexpr int PP = 64 / K;
   const int ns = P.nslots;
   const int64_t nloc = tile0 < pp.ntiles ? (pp.ntiles - tile0 + tstep - 1) / tstep : 0;
-  CgWarp<K, BF, LT> W(P, slot_carve(S.slots + c * tc_slot_bytes(K, LT), K, LT), lane);
+  CgWarp<K, BF, LT, K, 1, 1, RG> W(P, slot_carve(S.slots + c * tc_slot_bytes(K, LT), K, LT), lane);
+  if constexpr (RG == 1)
+    if (*S.region >= 0) W.rem = rem_slot<K>(*S.region, c);
   int64_t seq = c;
   for (; seq / PP < nloc; seq += ns) {
     const uint32_t use = (uint32_t)(seq / ns);
@@ -179,7 +244,10 @@ __device__ void cg_role(const DetectTcParams& P, const Smem& S, int c, int64_t t
   }
 }
 
-template <int K, bool BF, int LT>
+// RG = 1: residuals against the fp32 Gram matrix (resid_gram), with the
+// remainder pieces in a scratch region; RG = 0: against A16 alone (none of
+// that code is compiled in).
+template <int K, bool BF, int LT, int RG>
 __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_constant__ DetectTcParams P) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Smem S;
@@ -191,6 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
     S.sbars = reinterpret_cast<Bars2*>(S.bars + 1);
     S.tmem_slot = reinterpret_cast<uint32_t*>(S.sbars + 1);
     S.abort = reinterpret_cast<volatile int*>(S.tmem_slot + 1);
+    S.region = const_cast<int*>(reinterpret_cast<volatile int*>(S.abort + 1));
     S.slots = base + tc_slots_offset(K);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -204,6 +273,16 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
       tc::mbar_init(&S.sbars->slot_empty[i], 1);
     }
     *S.abort = 0;
+    int got = -1;
+    if (RG) {
+      for (int t = 0; t < 2 * kTcScratchRegions && got < 0; ++t) {
+        const int c = (int)((blockIdx.x + t) % kTcScratchRegions);
+        if (atomicCAS(&g_rem_busy<K>[c], 0, 1) == 0) got = c;
+      }
+      __threadfence();  // the previous holder's accesses happen before ours
+      if (got < 0) *S.abort = 1;  // not expected (one CTA per SM): no work, status FPCG_ST_TIMEOUT
+    }
+    *S.region = got;
     tc::fence_mbar_init();
   }
   if (warp == kMmaWarp) tc::tmem_alloc(S.tmem_slot, 2 * tcp::kAccCols);
@@ -214,7 +293,12 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
   const uint32_t tmem = *S.tmem_slot;
   const int64_t tile0 = blockIdx.x, tstep = gridDim.x;
 
-  if (warp == kMmaWarp) {
+  if (*S.abort) {  // no scratch region: nothing was started; this CTA's systems are reported
+    if (warp == kCg0 && P.status)
+      for (int64_t tile = tile0; tile < pp.ntiles; tile += tstep)
+        for (int p = lane; p < 64 / K; p += 32)
+          if (tile * (64 / K) + p < pp.batch) P.status[tile * (64 / K) + p] = 32;
+  } else if (warp == kMmaWarp) {
     if (lane == 0) tcp::mma_role(pp, S.pipe, *S.bars, S.abort, tmem, tile0, tstep);
     __syncwarp();
   } else if (warp == kProdWarp) {
@@ -223,9 +307,9 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
   } else if (warp >= kConv0) {
     tcp::converter_role<kConv, kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, warp - kConv0, lane);
   } else if (warp >= kCg0) {
-    if (warp - kCg0 < P.nslots) cg_role<K, BF, LT>(P, S, warp - kCg0, tile0, tstep);
+    if (warp - kCg0 < P.nslots) cg_role<K, BF, LT, RG>(P, S, warp - kCg0, tile0, tstep);
   } else {
-    drain_role<K, BF, LT>(P, S, tmem, tile0, tstep);
+    drain_role<K, BF, LT, RG>(P, S, tmem, tile0, tstep);
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -233,19 +317,23 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, 2 * tcp::kAccCols);
   }
+  if (RG && threadIdx.x == 0 && *S.region >= 0) {  // every access of this CTA to its region is done
+    __threadfence();
+    atomicExch(&g_rem_busy<K>[*S.region], 0);
+  }
 }
 
-template <int K, bool BF, int LT>
+template <int K, bool BF, int LT, int RG>
 cudaError_t launch_k(DetectTcParams P, int num_sms, cudaStream_t stream) {
   const size_t smem = detect_tc_smem_bytes(K, P.L);
   P.nslots = tc_num_slots(K, P.L);
   P.pipe.s32b = tc_stage32_bytes(K);
   cudaError_t e =
-      cudaFuncSetAttribute(detect_tc_kernel<K, BF, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(detect_tc_kernel<K, BF, LT, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t grid = P.pipe.ntiles < num_sms ? P.pipe.ntiles : num_sms;
   if (grid <= 0) return cudaSuccess;
-  detect_tc_kernel<K, BF, LT><<<(unsigned)grid, kThreads, smem, stream>>>(P);
+  detect_tc_kernel<K, BF, LT, RG><<<(unsigned)grid, kThreads, smem, stream>>>(P);
   return cudaGetLastError();
 }
 
@@ -253,15 +341,23 @@ cudaError_t launch_k(DetectTcParams P, int num_sms, cudaStream_t stream) {
 
 template <int K>
 cudaError_t launch_detect_tc_k(const DetectTcParams& P, int num_sms, int mv_bf16, cudaStream_t stream) {
-  switch (P.L * 2 + (mv_bf16 ? 1 : 0)) {
-    case 0: return launch_k<K, false, 0>(P, num_sms, stream);
-    case 1: return launch_k<K, true, 0>(P, num_sms, stream);
-    case 8: return launch_k<K, false, 4>(P, num_sms, stream);
-    case 9: return launch_k<K, true, 4>(P, num_sms, stream);
-    case 16: return launch_k<K, false, 8>(P, num_sms, stream);
-    case 17: return launch_k<K, true, 8>(P, num_sms, stream);
-    case 32: return launch_k<K, false, 16>(P, num_sms, stream);
-    case 33: return launch_k<K, true, 16>(P, num_sms, stream);
+  switch ((P.L * 2 + (mv_bf16 ? 1 : 0)) * 2 + (P.resid_gram ? 1 : 0)) {
+    case 0: return launch_k<K, false, 0, 0>(P, num_sms, stream);
+    case 1: return launch_k<K, false, 0, 1>(P, num_sms, stream);
+    case 2: return launch_k<K, true, 0, 0>(P, num_sms, stream);
+    case 3: return launch_k<K, true, 0, 1>(P, num_sms, stream);
+    case 16: return launch_k<K, false, 4, 0>(P, num_sms, stream);
+    case 17: return launch_k<K, false, 4, 1>(P, num_sms, stream);
+    case 18: return launch_k<K, true, 4, 0>(P, num_sms, stream);
+    case 19: return launch_k<K, true, 4, 1>(P, num_sms, stream);
+    case 32: return launch_k<K, false, 8, 0>(P, num_sms, stream);
+    case 33: return launch_k<K, false, 8, 1>(P, num_sms, stream);
+    case 34: return launch_k<K, true, 8, 0>(P, num_sms, stream);
+    case 35: return launch_k<K, true, 8, 1>(P, num_sms, stream);
+    case 64: return launch_k<K, false, 16, 0>(P, num_sms, stream);
+    case 65: return launch_k<K, false, 16, 1>(P, num_sms, stream);
+    case 66: return launch_k<K, true, 16, 0>(P, num_sms, stream);
+    case 67: return launch_k<K, true, 16, 1>(P, num_sms, stream);
     default: return cudaErrorInvalidValue;
   }
 }

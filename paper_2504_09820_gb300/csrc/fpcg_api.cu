@@ -147,10 +147,16 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
     cudaError_t e = fpcg::launch_solve_tc(T, sms, prec->mv == FPCG_BF16, s);
     return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
   }
-  if (tc_ok) {
-    int sms = 0;
-    rc = device_sms(&sms);
+  int sms_tc = 0;
+  if (tc_ok && !Ain) {
+    rc = device_sms(&sms_tc);
     if (rc) return rc;
+  }
+  // the Gram residual's scratch pool has one region per SM (kTcScratchRegions of them)
+  const bool scratch_ok = prec->resid != FPCG_FP64 || sms_tc <= fpcg::kTcScratchRegions;
+  if (path == FPCG_PATH_TENSOR_CORE && tc_ok && !Ain && !scratch_ok) return FPCG_ENOTSUP;
+  if (tc_ok && scratch_ok) {
+    const int sms = sms_tc;
     rc = check_device_smem(fpcg::detect_tc_smem_bytes(k, block_L));
     if (rc) return rc;
     fpcg::DetectTcParams T;
@@ -160,6 +166,7 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
     T.sigma2 = sigma2;
     cg_params(T, qam_order, iters, block_L, prec, refine_iters, x_hat, sym_idx, rel_res, res_hist, tx_idx,
               bit_errors, status);
+    T.resid_gram = prec->resid == FPCG_FP64;
     cudaError_t e = fpcg::launch_detect_tc(T, sms, prec->mv == FPCG_BF16, s);
     return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
   }
@@ -206,7 +213,7 @@ bool two_pass_capable(int k, int block_L, const fpcg_precision* prec) {
 }
 
 bool tc_capable(int k, int block_L, const fpcg_precision* prec) {
-  return prec->w == FPCG_FP32 && prec->resid == FPCG_FP32 && (prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) &&
+  return prec->w == FPCG_FP32 && (prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) &&
          (prec->mv == FPCG_BF16 || prec->mv == FPCG_FP16) && fpcg::detect_tc_supported(k, block_L);
 }
 

@@ -105,6 +105,7 @@ template <int S32 = kStages32>
 __device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B, volatile int* abort,
                                      int64_t tile0, int64_t tstep) {
   const uint32_t tx = kStage32HBytes + 64 * 4 * p.P;
+  const uint64_t once = tc::policy_evict_first();  // H and y are read once
   uint32_t u = 0;
   // No L2 prefetch of later tiles: measured on the N = 256, K = 64 batch it cost
   // 2% (and a third of the bandwidth with 512 KB systems); the ring of TMA
@@ -118,8 +119,8 @@ __device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B,
       }
       uint8_t* st = stage32(pipe_base, (int)s, p.s32b);
       tc::mbar_expect_tx(&B.full32[s], tx);
-      tc::tma_load_2d(st, &p.tmH, 64 * c, (int)(tile * 64), &B.full32[s]);
-      tc::tma_load_2d(st + kStage32HBytes, &p.tmY, 64 * c, (int)(tile * p.P), &B.full32[s]);
+      tc::tma_load_2d_hint(st, &p.tmH, 64 * c, (int)(tile * 64), &B.full32[s], once);
+      tc::tma_load_2d_hint(st + kStage32HBytes, &p.tmY, 64 * c, (int)(tile * p.P), &B.full32[s], once);
     }
   }
 }

@@ -45,8 +45,13 @@ class Precision(ctypes.Structure):
                 ("fp8_block", ctypes.c_int32), ("resid", ctypes.c_int32)]
 
 
+# resid: "fp64" = refinement residual and rel_res against the fp32 Gram matrix,
+# "fp32" = against the matvec-format matrix (see fpcg_precision in fpcg.h)
+DEFAULT_RESID = "fp32"
+
+
 def precision(gram="fp32", mv="fp32", ip="fp32", w="fp32", refine_steps=0, refine_iters=-1,
-              alpha_num=0, fp8_block=32, resid="fp32"):
+              alpha_num=0, fp8_block=32, resid=DEFAULT_RESID):
     """Build an fpcg_precision from format names ("fp64", "fp32", "fp16", "bf16", "e4m3")."""
     if w == "fp64":
         gram = mv = ip = resid = "fp64"

@@ -32,6 +32,7 @@ ORACLE_KEYS = ("gram", "mv", "ip", "w", "refine_steps", "refine_iters", "alpha_n
 
 def oracle_detect(d, iters, prec_kw, L=None, sel=None):
     pk = {k: v for k, v in prec_kw.items() if k in ORACLE_KEYS}
+    pk.setdefault("resid", F.DEFAULT_RESID)   # the binding's default, not the oracle's
     if pk.get("w") == "fp64":
         pk.update(gram="fp64", mv="fp64", ip="fp64")
     if pk.get("refine_iters", -1) is not None and pk.get("refine_iters", -1) < 0:

@@ -32,12 +32,13 @@ def _check(d, res, ref, tol=2e-3):
     assert np.all(res["status"] & ~F.ST_RHO_ZERO == 0)
 
 
-def _own_residual(d, res, gram, mv):
-    """||b - A x|| / ||b|| of the GPU's own x, with A the GPU's own fp32 Gram
-    (fpcg_gram runs the same tensor-core pipeline) rounded to the matvec format,
-    as the refinement residual uses it.  The oracle's fp32 Gram sums in another
-    order, and an entry next to a rounding boundary of the 16-bit format can
-    round the other way there, which moves a residual of ~1e-3 noticeably."""
+def _own_residual(d, res, gram, mv, resid="fp32"):
+    """||b - A x|| / ||b|| of the GPU's own x in float64, with A the GPU's own
+    fp32 Gram (fpcg_gram runs the same tensor-core pipeline): as it is for
+    resid = "fp64", rounded to the matvec format for resid = "fp32".  The
+    oracle's fp32 Gram sums in another order, and an entry next to a rounding
+    boundary of the 16-bit format can round the other way there, which moves a
+    residual of ~1e-3 noticeably."""
     from oracle.formats import round_matvec_operand
     g = to_dev(d)
     B, K, _ = d["H"].shape
@@ -46,23 +47,27 @@ def _own_residual(d, res, gram, mv):
     F.fpcg_gram(g["H"], g["y"], g["sigma2"], gram, A, b)
     A = A.cpu().numpy().astype(np.complex128)
     b = b.cpu().numpy().astype(np.complex128)
-    A_mv = round_matvec_operand(A, mv, 32)
-    return np.linalg.norm(D.resid(A_mv, res["x"], b), axis=1) / np.linalg.norm(b, axis=1)
+    A_r = A if resid == "fp64" else round_matvec_operand(A, mv, 32)
+    return np.linalg.norm(D.resid(A_r, res["x"], b), axis=1) / np.linalg.norm(b, axis=1)
 
 
 CASES = [
-    # K, gram, mv, L, iters, refine
-    (64, "bf16", "bf16", 8, 6, 1),
-    (64, "fp16", "fp16", 8, 6, 1),
-    (64, "bf16", "bf16", 0, 10, 1),
-    (64, "bf16", "fp16", 16, 5, 2),
-    (64, "fp16", "bf16", 4, 6, 0),
-    (32, "bf16", "bf16", 8, 8, 1),
-    (32, "fp16", "fp16", 16, 6, 1),
-    (16, "bf16", "bf16", 4, 8, 1),
-    (16, "bf16", "bf16", 0, 12, 1),
-    (64, "bf16", "bf16", 16, 4, 1),
-    (32, "bf16", "bf16", 4, 6, 2),
+    # K, gram, mv, L, iters, refine, resid ("fp64": against the fp32 Gram; "fp32": the matvec matrix)
+    (64, "bf16", "bf16", 8, 6, 1, "fp64"),
+    (64, "fp16", "fp16", 8, 6, 1, "fp64"),
+    (64, "bf16", "bf16", 0, 10, 1, "fp64"),
+    (64, "bf16", "fp16", 16, 5, 2, "fp64"),
+    (64, "bf16", "fp16", 4, 7, 1, "fp64"),
+    (64, "fp16", "bf16", 4, 6, 0, "fp64"),
+    (32, "bf16", "bf16", 8, 8, 1, "fp64"),
+    (32, "fp16", "fp16", 16, 6, 1, "fp64"),
+    (16, "bf16", "bf16", 4, 8, 1, "fp64"),
+    (16, "bf16", "fp16", 0, 12, 1, "fp64"),
+    (64, "bf16", "bf16", 16, 4, 1, "fp64"),
+    (32, "bf16", "fp16", 4, 6, 2, "fp64"),
+    (64, "bf16", "bf16", 8, 6, 1, "fp32"),
+    (32, "bf16", "fp16", 4, 6, 2, "fp32"),
+    (16, "bf16", "bf16", 0, 12, 1, "fp32"),
 ]
 
 
@@ -73,24 +78,25 @@ def test_routing_to_simt():
     assert F.fpcg_path(256, 64, 2, F.precision(**bf)) == F.PATH_SIMT
     assert F.fpcg_path(256, 128, 8, F.precision(**bf)) == F.PATH_SIMT         # K > 64
     assert F.fpcg_path(64, 8, 4, F.precision(**bf)) == F.PATH_SIMT           # K < 16
-    assert F.fpcg_path(256, 64, 8, F.precision(**bf, resid="fp64")) == F.PATH_SIMT  # compensated residual
+    assert F.fpcg_path(256, 64, 8, F.precision(**bf, resid="fp64")) == F.PATH_TENSOR_CORE  # Gram residual
+    assert F.fpcg_path(256, 64, 8, F.precision(gram="fp32", mv="bf16")) == F.PATH_SIMT  # fp32 Gram
     assert F.fpcg_path(256, 64, 8, F.precision(gram="bf16", mv="e4m3")) == F.PATH_SIMT
     assert F.fpcg_path(255, 64, 8, F.precision(**bf)) == F.PATH_SIMT          # odd N (no TMA)
     assert F.fpcg_path(256, 64, 8, F.precision(**bf)) == F.PATH_TENSOR_CORE
 
 
-@pytest.mark.parametrize("K,gram,mv,L,iters,refine", CASES)
-def test_fused_matches_oracle(K, gram, mv, L, iters, refine):
+@pytest.mark.parametrize("K,gram,mv,L,iters,refine,resid", CASES)
+def test_fused_matches_oracle(K, gram, mv, L, iters, refine, resid):
     N = 4 * K
     P = 64 // K
     batch = 152 * P * 2 + P // 2 + 1       # every CTA reuses both accumulators; ragged last tile
     d = wl.generate(wl.Spec(N=N, K=K, batch=batch, rho=0.5, qam=64, snr_db=14.0, seed=500 + K + L))
-    pk = dict(gram=gram, mv=mv, refine_steps=refine)
+    pk = dict(gram=gram, mv=mv, refine_steps=refine, resid=resid)
     assert F.fpcg_path(N, K, L, F.precision(**pk)) == F.PATH_TENSOR_CORE
     res = gpu_detect(d, iters, pk, L=(L or None))
     ref = oracle_detect(d, iters, pk, L=(L or None))
     _check(d, res, ref)
-    own = _own_residual(d, res, gram, mv)
+    own = _own_residual(d, res, gram, mv, resid)
     assert np.allclose(res["rel_res"], own, rtol=2e-3, atol=1e-6)
 
 
