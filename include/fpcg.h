@@ -388,13 +388,19 @@ FPCG_API int fpcg_plan_destroy(fpcg_plan* plan);
  * resid = FP32, gram in {BF16, FP16}) keep their Gram matrices and matched filters in one
  * fixed 64 MiB device array of the library; every other configuration takes
  * the ordinary path, which allocates nothing either.
- *   - Limit: batch * K * (K + 1) * 8 bytes <= 64 MiB (K = 128: 496 systems per
+ *   - Limit: batch * K * (K + 1) * 8 bytes <= 64 MiB (K = 128: 508 systems per
  *     call; K = 8: 116508); a larger batch returns FPCG_ENOTSUP (split it).
+ *     Every argument is checked before any work is issued, so a refused call
+ *     changes nothing (not the array, status or bit_errors).
  *   - The array is shared by all calls on a device: calls must not overlap in
  *     time (issue them on one stream, or wait for one before the next).
- *   - The first call on each device looks up the array's address
- *     (cudaGetSymbolAddress); make that first call before any stream capture
- *     begins.
+ *   - status[] holds the Gram pass's bits (FPCG_ST_TIMEOUT) OR-ed with the
+ *     solve's.
+ *   - Outside a stream capture every call looks up the array's address
+ *     (cudaGetSymbolAddress; the array moves when cudaDeviceReset reloads the
+ *     library's module); inside a capture the address found by the previous
+ *     call on that device is used, so make one call on each device before any
+ *     capture begins, and after a cudaDeviceReset.
  */
 FPCG_API int fpcg_detect_noalloc(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
                                  int32_t n_rx, int32_t k, int64_t batch, int32_t iters, int32_t block_L,

@@ -12,12 +12,21 @@ namespace fpcg {
 // dispatch to a kernel.  path: -1 = as fpcg_path chooses, FPCG_PATH_SIMT or
 // FPCG_PATH_TENSOR_CORE (FPCG_ENOTSUP if the tensor-core kernel cannot run
 // it).  reset_bits: zero *bit_errors first (a plan zeroes it once for all of
-// its classes).
+// its classes).  status_or (given Gram matrices, tensor-core solver): OR the
+// solve's status bits into status[], which the Gram pass filled, instead of
+// overwriting them.
 int run_uniform(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
                 const void* Ain, const void* bin, int32_t n_rx, int32_t k, int64_t batch, int32_t iters,
                 int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
                 double* rel_res, float* res_hist, const uint8_t* tx_idx,
-                unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits);
+                unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits,
+                bool status_or = false);
+
+// Checks of the arguments common to every detection entry point (no GPU
+// work): FPCG_OK or FPCG_EINVAL.
+int check_detect_args(int32_t k, int64_t batch, int32_t iters, int32_t block_L, const void* x_hat,
+                      const uint8_t* sym_idx, const int32_t* qam_order, const uint8_t* tx_idx,
+                      const unsigned long long* bit_errors);
 
 // Whether the fused tensor-core kernel supports this configuration (alignment
 // of the data aside).

@@ -749,7 +749,7 @@ struct CgWarp {
       if (P.rel_res) P.rel_res[sys] = nb > 0.f ? sqrt((double)nr / (double)nb) : 0.0;
       if (nonfinite) st |= 4;
       if (want_sym && m == 0) st |= 16;
-      if (P.status) P.status[sys] = st;
+      if (P.status) P.status[sys] = P.status_or ? (P.status[sys] | st) : st;
     }
   }
 };

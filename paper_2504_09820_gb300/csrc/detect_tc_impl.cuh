@@ -102,13 +102,13 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
     const int64_t sys = tile * PP + ps;
     const bool valid = sys < pp.batch;
     const float s2 = valid ? (float)P.sigma2[sys] : 1.f;  // issued before the wait
-    bool ok = tc::mbar_wait(&S.bars->acc_full[b], qa & 1u, S.abort);
+    bool ok = tc::mbar_wait(&S.bars->acc_full[b], qa & 1u, S.abort, pp.budget);
     for (int p = 0; ok && p < PP; ++p) {
       const int64_t seq = j * PP + p;
       const uint32_t sl = (uint32_t)(seq % ns), use = (uint32_t)(seq / ns);
-      if (use > 0) ok = tc::mbar_wait(&S.sbars->slot_empty[sl], (use - 1) & 1u, S.abort);
+      if (use > 0) ok = tc::mbar_wait(&S.sbars->slot_empty[sl], (use - 1) & 1u, S.abort, pp.budget);
     }
-    if (!ok) {
+    if (tc::bar_or(1, 128, !ok)) {  // the four drain warps leave together
       *S.abort = 1;
       break;
     }
@@ -226,7 +226,7 @@ __device__ void cg_role(const DetectTcParams& P, const Smem& S, int c, int64_t t
   int64_t seq = c;
   for (; seq / PP < nloc; seq += ns) {
     const uint32_t use = (uint32_t)(seq / ns);
-    if (!tc::mbar_wait(&S.sbars->slot_full[c], use & 1u, S.abort)) {
+    if (!__all_sync(0xffffffffu, tc::mbar_wait(&S.sbars->slot_full[c], use & 1u, S.abort, pp.budget))) {
       *S.abort = 1;
       break;
     }

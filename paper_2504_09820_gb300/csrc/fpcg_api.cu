@@ -103,16 +103,14 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
                 const void* Ain, const void* bin, int32_t n_rx, int32_t k, int64_t batch, int32_t iters,
                 int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
                 double* rel_res, float* res_hist, const uint8_t* tx_idx,
-                unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits) {
+                unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits,
+                bool status_or) {
   int rc = check_prec(prec);
   if (rc) return rc;
-  if (k < 1 || k > 128 || batch < 0 || iters < 0) return FPCG_EINVAL;
+  rc = check_detect_args(k, batch, iters, block_L, x_hat, sym_idx, qam_order, tx_idx, bit_errors);
+  if (rc) return rc;
   if (!Ain && (n_rx < k || n_rx > 65536)) return FPCG_EINVAL;
-  if (block_L < 0 || block_L > 32 || (block_L > 0 && k % block_L)) return FPCG_EINVAL;
-  if (!x_hat) return FPCG_EINVAL;
   if (Ain ? (!bin) : (!H || !y || !sigma2)) return FPCG_EINVAL;
-  if ((sym_idx || bit_errors) && !qam_order) return FPCG_EINVAL;
-  if ((tx_idx != nullptr) != (bit_errors != nullptr)) return FPCG_EINVAL;
   const int fp64 = prec->w == FPCG_FP64;
   if (fp64 && k > 64) return FPCG_ENOTSUP;
   const int refine_iters = prec->refine_iters < 0 ? iters : prec->refine_iters;
@@ -144,6 +142,7 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
     T.N = k;
     T.K = k;
     T.gram = prec->gram;
+    T.D.status_or = status_or && status;
     cudaError_t e = fpcg::launch_solve_tc(T, sms, prec->mv == FPCG_BF16, s);
     return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
   }
@@ -204,6 +203,17 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
 }
 
 int cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+int check_detect_args(int32_t k, int64_t batch, int32_t iters, int32_t block_L, const void* x_hat,
+                      const uint8_t* sym_idx, const int32_t* qam_order, const uint8_t* tx_idx,
+                      const unsigned long long* bit_errors) {
+  if (k < 1 || k > 128 || batch < 0 || iters < 0) return FPCG_EINVAL;
+  if (block_L < 0 || block_L > 32 || (block_L > 0 && k % block_L)) return FPCG_EINVAL;
+  if (!x_hat) return FPCG_EINVAL;
+  if ((sym_idx || bit_errors) && !qam_order) return FPCG_EINVAL;
+  if ((tx_idx != nullptr) != (bit_errors != nullptr)) return FPCG_EINVAL;
+  return FPCG_OK;
+}
 
 int check_precision(const fpcg_precision* p) { return check_prec(p); }
 

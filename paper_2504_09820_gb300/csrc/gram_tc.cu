@@ -76,8 +76,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(const __grid_const
     int64_t tile = tile0;
     for (; tile < pp.ntiles; tile += tstep, ++j) {
       const uint32_t b = (uint32_t)(j & 1), qa = (uint32_t)(j >> 1);
-      if (!tc::mbar_wait(&S.bars->acc_full[b], qa & 1u, S.abort)) {
-        *S.abort = 1;
+      if (tc::bar_or(1, 128, !tc::mbar_wait(&S.bars->acc_full[b], qa & 1u, S.abort, P.pipe.budget))) {
+        *S.abort = 1;  // the four drain warps leave together
         break;
       }
       tc::tc_fence_after();

@@ -21,6 +21,8 @@ bool gram_tc_supported(int K);
 size_t gram_tc_smem_bytes();
 // The TMA pipeline needs N even and 16-byte aligned H and y.
 bool tma_pipe_ok(const void* H, const void* y, int N);
+// SM cycles a tensor-core pipeline wait may take (FPCG_TC_WAIT_CYCLES, else ~2 s).
+long long wait_budget_cycles();
 // Fill the pipeline description (tensor maps included); false if the driver
 // refused a tensor map.
 bool make_pipe(tcp::Pipe* p, const float2* H, const float2* y, int N, int K, int64_t batch, int bf16);

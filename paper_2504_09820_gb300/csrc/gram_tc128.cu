@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc128_kernel(const __grid_co
         tc::mma_commit(&B->acc_full[ab]);
       }
       tc::mma_commit(&B->done);  // nothing in flight before the TMEM is released
-      tc::mbar_wait(&B->done, 0, abort, 2000000000LL);
+      tc::mbar_wait_issued(&B->done, 0);  // no MMA may still write TMEM when it is freed
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -158,12 +158,14 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc128_kernel(const __grid_co
             *abort = 1;
             break;
           }
+          if (*abort) break;
           uint8_t* st = st32(pipe, (int)s);
           tc::mbar_expect_tx(&B->full32[s], tx);
           tc::tma_load_2d(st, &P.tmH, 64 * c, (int)(sys * kK), &B->full32[s]);
           tc::tma_load_2d(st + kSt32H, &P.tmY, 64 * c, (int)sys, &B->full32[s]);
         }
       }
+      if (*abort) tcp::wait_issued_loads<kS32>(B->full32, u);  // none may land after the CTA is gone
     }
     __syncwarp();
   } else if (warp >= 8) {  // converters: rows cw + 8m; lane l fills k-positions 2l, 2l+1
@@ -180,8 +182,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc128_kernel(const __grid_co
         const uint32_t s0 = u32 % kS32, q0 = u32 / kS32;
         const uint32_t s1 = (u32 + 1) % kS32, q1 = (u32 + 1) / kS32;
         const uint32_t t = u16 % kStages, qt = u16 / kStages;
-        if (!tc::mbar_wait(&B->full32[s0], q0 & 1u, abort) || !tc::mbar_wait(&B->full32[s1], q1 & 1u, abort) ||
-            (qt > 0 && !tc::mbar_wait(&B->empty[t], (qt - 1) & 1u, abort))) {
+        const bool ok = tc::mbar_wait(&B->full32[s0], q0 & 1u, abort) && tc::mbar_wait(&B->full32[s1], q1 & 1u, abort) &&
+                        (qt == 0 || tc::mbar_wait(&B->empty[t], (qt - 1) & 1u, abort));
+        if (!__all_sync(0xffffffffu, ok)) {  // the whole warp leaves together
           *abort = 1;
           break;
         }
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc128_kernel(const __grid_co
           tc::mbar_arrive(&B->empty32[s1]);
         }
       }
-      if (*abort) break;
+      if (__any_sync(0xffffffffu, *abort != 0)) break;
       // sum the 32 values over the lanes; lane l ends with value l (reduce-scatter)
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) {
@@ -230,8 +233,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc128_kernel(const __grid_co
     int64_t j = 0, sys = sys0;
     for (; sys < P.batch; sys += sstep, ++j) {
       const uint32_t ab = (uint32_t)(j & 1);
-      if (!tc::mbar_wait(&B->acc_full[ab], (uint32_t)((j >> 1) & 1), abort)) {
-        *abort = 1;
+      if (tc::bar_or(1, 128, !tc::mbar_wait(&B->acc_full[ab], (uint32_t)((j >> 1) & 1), abort))) {
+        *abort = 1;  // the four drain warps leave together
         break;
       }
       tc::tc_fence_after();

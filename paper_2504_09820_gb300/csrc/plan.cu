@@ -85,7 +85,8 @@ int run_class(fpcg_plan* p, const fpcg_plan::Class& c, int path, const void* H, 
     return fpcg::run_uniform(nullptr, nullptr, nullptr, qam ? qam + c.first : nullptr, A, bv, c.k, c.k, c.count,
                              p->iters, c.L, &p->prec, xc, sym ? sym + c.x0 : nullptr,
                              rel_res ? rel_res + c.first : nullptr, nullptr, tx ? tx + c.x0 : nullptr, bits,
-                             status ? status + c.first : nullptr, s, FPCG_PATH_TENSOR_CORE, false);
+                             status ? status + c.first : nullptr, s, FPCG_PATH_TENSOR_CORE, false,
+                             true);  // keep a Gram-pass FPCG_ST_TIMEOUT
   }
   return fpcg::run_uniform(Hc, yc, sigma2 + c.first, qam ? qam + c.first : nullptr, nullptr, nullptr, c.n, c.k,
                            c.count, p->iters, c.L, &p->prec, xc, sym ? sym + c.x0 : nullptr,

@@ -49,6 +49,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
   }
 }
 
+// Wait for a phase that is bound to complete (issued bulk copies or MMAs),
+// whatever the abort flag says; gives up after ~`budget` cycles.  An aborting
+// CTA uses it so that nothing it issued still writes its shared memory or
+// tensor memory when it exits.
+__device__ __forceinline__ bool mbar_wait_issued(uint64_t* bar, uint32_t parity, long long budget = 4000000000LL) {
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > budget) return false;
+  }
+}
+
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

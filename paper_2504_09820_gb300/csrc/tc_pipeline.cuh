@@ -71,7 +71,15 @@ struct Pipe {
   int64_t batch, ntiles;
   int bf16;
   int s32b;          // bytes per FP32 stage (stage32_bytes(P) or more)
+  long long budget;  // SM cycles a pipeline wait may take before the CTA aborts
 };
+
+// Wait for the TMA loads still in flight when the producer stops: the last
+// min(u, S) of the u loads it issued (load i went to stage i % S, phase i / S).
+template <int S>
+__device__ inline void wait_issued_loads(uint64_t* full, uint32_t u) {
+  for (uint32_t i = u > (uint32_t)S ? u - S : 0; i < u; ++i) tc::mbar_wait_issued(&full[i % S], (i / S) & 1u);
+}
 
 struct Bars {
   uint64_t full32[kStages32];
@@ -113,8 +121,9 @@ __device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B,
   for (int64_t tile = tile0; tile < p.ntiles; tile += tstep) {
     for (int c = 0; c < 2 * p.nchunks; ++c, ++u) {
       const uint32_t s = u % S32, q = u / S32;
-      if (q > 0 && !tc::mbar_wait(&B.empty32[s], (q - 1) & 1u, abort)) {
+      if (q > 0 && !tc::mbar_wait(&B.empty32[s], (q - 1) & 1u, abort, p.budget)) {
         *abort = 1;
+        wait_issued_loads<S32>(B.full32, u);  // none may land after the CTA is gone
         return;
       }
       uint8_t* st = stage32(pipe_base, (int)s, p.s32b);
@@ -140,8 +149,10 @@ __device__ inline void converter_role(const Pipe& p, uint8_t* pipe_base, Bars& B
       const uint32_t s0 = u32 % S32, q0 = u32 / S32;
       const uint32_t s1 = (u32 + 1) % S32, q1 = (u32 + 1) / S32;
       const uint32_t t = u16 % kStages, qt = u16 / kStages;
-      if (!tc::mbar_wait(&B.full32[s0], q0 & 1u, abort) || !tc::mbar_wait(&B.full32[s1], q1 & 1u, abort) ||
-          (qt > 0 && !tc::mbar_wait(&B.empty[t], (qt - 1) & 1u, abort))) {
+      const bool ok = tc::mbar_wait(&B.full32[s0], q0 & 1u, abort, p.budget) &&
+                      tc::mbar_wait(&B.full32[s1], q1 & 1u, abort, p.budget) &&
+                      (qt == 0 || tc::mbar_wait(&B.empty[t], (qt - 1) & 1u, abort, p.budget));
+      if (!__all_sync(0xffffffffu, ok)) {  // the whole warp leaves together
         *abort = 1;
         return;
       }
@@ -185,7 +196,7 @@ __device__ inline void mma_role(const Pipe& p, uint8_t* pipe_base, Bars& B, vola
   int64_t j = 0;
   for (int64_t tile = tile0; tile < p.ntiles; tile += tstep, ++j) {
     const uint32_t b = (uint32_t)(j & 1), qa = (uint32_t)(j >> 1);
-    if (qa > 0 && !tc::mbar_wait(&B.acc_empty[b], (qa - 1) & 1u, abort)) {
+    if (qa > 0 && !tc::mbar_wait(&B.acc_empty[b], (qa - 1) & 1u, abort, p.budget)) {
       *abort = 1;
       break;
     }
@@ -193,7 +204,7 @@ __device__ inline void mma_role(const Pipe& p, uint8_t* pipe_base, Bars& B, vola
     const uint32_t dt = tmem + b * kAccCols;
     for (int c = 0; c < p.nchunks; ++c, ++u) {
       const uint32_t st = u % kStages, q = u / kStages;
-      if (!tc::mbar_wait(&B.full[st], q & 1u, abort)) {
+      if (!tc::mbar_wait(&B.full[st], q & 1u, abort, p.budget)) {
         *abort = 1;
         break;
       }
@@ -212,7 +223,7 @@ __device__ inline void mma_role(const Pipe& p, uint8_t* pipe_base, Bars& B, vola
   }
   // make sure nothing is in flight before the TMEM is released
   tc::mma_commit(&B.done);
-  tc::mbar_wait(&B.done, 0, abort, 2000000000LL);
+  tc::mbar_wait_issued(&B.done, 0);
 }
 
 // Initialise the pipeline's barriers (one thread).

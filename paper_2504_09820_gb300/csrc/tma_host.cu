@@ -1,5 +1,6 @@
 // Host side of the TMA pipeline: tensor maps for H and y.
 #include <cuda.h>
+#include <stdlib.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 #include <mutex>
@@ -55,6 +56,14 @@ bool encode_sw128(CUtensorMap* m, const void* base, uint64_t inner, uint64_t row
 
 }  // namespace
 
+long long wait_budget_cycles() {
+  // FPCG_TC_WAIT_CYCLES: diagnostic override of the bounded waits (a tiny value makes
+  // every pipeline wait give up, which exercises the abort path); default ~2 s at 2 GHz.
+  const char* v = getenv("FPCG_TC_WAIT_CYCLES");
+  const long long c = v ? atoll(v) : 0;
+  return c > 0 ? c : 4000000000LL;
+}
+
 bool tma_pipe_ok(const void* H, const void* y, int N) {
   return N % 2 == 0 && ((uintptr_t)H % 16) == 0 && ((uintptr_t)y % 16) == 0;
 }
@@ -71,6 +80,7 @@ bool make_pipe(tcp::Pipe* p, const float2* H, const float2* y, int N, int K, int
   p->ntiles = (batch + p->P - 1) / p->P;
   p->bf16 = bf16;
   p->s32b = tcp::kStage32Bytes;
+  p->budget = wait_budget_cycles();
   return encode(&p->tmH, H, 2ull * N, (uint64_t)batch * K, 64) &&
          encode(&p->tmY, y, 2ull * N, (uint64_t)batch, (uint32_t)p->P);
 }

@@ -28,18 +28,30 @@ def _data(N, K, B, seed):
     return d, {k: torch.from_numpy(d[k]).cuda() for k in ("H", "y", "sigma2", "qam", "tx")}
 
 
-def _noalloc(g, K, L):
+def _noalloc(g, K, L, iters=6):
     B = g["H"].shape[0]
     out = {"x": torch.empty((B, K), dtype=torch.complex64, device="cuda"),
            "sym": torch.empty((B, K), dtype=torch.uint8, device="cuda"),
            "rel": torch.empty(B, dtype=torch.float64, device="cuda"),
-           "st": torch.empty(B, dtype=torch.int32, device="cuda"),
+           "st": torch.full((B,), 7, dtype=torch.int32, device="cuda"),
            "be": torch.zeros(1, dtype=torch.int64, device="cuda")}
-    F.fpcg_detect_noalloc(g["H"], g["y"], g["sigma2"], g["qam"], 6, L, F.precision(**PREC), out["x"],
+    F.fpcg_detect_noalloc(g["H"], g["y"], g["sigma2"], g["qam"], iters, L, F.precision(**PREC), out["x"],
                           sym_idx=out["sym"], rel_res=out["rel"], tx_idx=g["tx"], bit_errors=out["be"],
                           status=out["st"])
     torch.cuda.synchronize()
     return {k: v.cpu() for k, v in out.items()}
+
+
+def _gram_then_solve(g, K, L):
+    B = g["H"].shape[0]
+    A = torch.empty((B, K, K), dtype=torch.complex64, device="cuda")
+    b = torch.empty((B, K), dtype=torch.complex64, device="cuda")
+    F.fpcg_gram(g["H"], g["y"], g["sigma2"], "bf16", A, b)
+    x = torch.empty((B, K), dtype=torch.complex64, device="cuda")
+    rel = torch.empty(B, dtype=torch.float64, device="cuda")
+    F.fpcg_solve_gram(A, b, 6, L, F.precision(**PREC), x, rel_res=rel)
+    torch.cuda.synchronize()
+    return x.cpu(), rel.cpu()
 
 
 @pytest.mark.parametrize("N,K,L", [(256, 128, 8), (64, 8, 4)])
@@ -49,16 +61,42 @@ def test_two_calls_equal_gram_then_solve(N, K, L):
     second = _noalloc(g, K, L)
     for k in first:
         assert torch.equal(first[k], second[k]), k
-    A = torch.empty((200, K, K), dtype=torch.complex64, device="cuda")
-    b = torch.empty((200, K), dtype=torch.complex64, device="cuda")
-    F.fpcg_gram(g["H"], g["y"], g["sigma2"], "bf16", A, b)
-    x = torch.empty((200, K), dtype=torch.complex64, device="cuda")
-    rel = torch.empty(200, dtype=torch.float64, device="cuda")
-    F.fpcg_solve_gram(A, b, 6, L, F.precision(**PREC), x, rel_res=rel)
-    torch.cuda.synchronize()
-    assert torch.equal(first["x"], x.cpu()) and torch.equal(first["rel"], rel.cpu())
+    x, rel = _gram_then_solve(g, K, L)
+    assert torch.equal(first["x"], x) and torch.equal(first["rel"], rel)
     assert np.array_equal(Q.slice_symbols(first["x"].numpy(), 64, "fp32"), first["sym"].numpy())
     assert int(first["be"][0]) == Q.bit_errors(first["sym"].numpy(), d["tx"])
+    assert torch.all(first["st"] & ~F.ST_RHO_ZERO == 0)   # the Gram pass's status, OR-ed with the solve's
+
+
+def test_largest_batch_is_accepted_and_one_more_is_refused():
+    """The limit batch * K * (K + 1) * 8 bytes <= 64 MiB, at its boundary for
+    K = 128: 508 systems fit (and give the two-pass result), 509 do not."""
+    limit = (64 << 20) // (128 * 129 * 8)
+    assert limit == 508
+    _, g = _data(256, 128, limit + 1, 44)
+    with pytest.raises(F.FpcgError) as e:
+        _noalloc(g, 128, 8)
+    assert e.value.code == F.ENOTSUP
+    g = {k: v[:limit].contiguous() for k, v in g.items()}
+    a = _noalloc(g, 128, 8)
+    x, rel = _gram_then_solve(g, 128, 8)
+    assert torch.equal(a["x"], x) and torch.equal(a["rel"], rel)
+
+
+def test_bad_arguments_have_no_side_effects():
+    """A refused call returns before any GPU work: the status array it was
+    given is not zeroed (the Gram pass would zero it first)."""
+    _, g = _data(256, 128, 64, 45)
+    with pytest.raises(F.FpcgError) as e:
+        _noalloc(g, 128, 8, iters=-1)
+    assert e.value.code == F.EINVAL
+    st = torch.full((64,), 7, dtype=torch.int32, device="cuda")
+    x = torch.empty((64, 128), dtype=torch.complex64, device="cuda")
+    with pytest.raises(F.FpcgError):   # bit_errors without tx_idx
+        F.fpcg_detect_noalloc(g["H"], g["y"], g["sigma2"], g["qam"], 6, 8, F.precision(**PREC), x,
+                              bit_errors=torch.zeros(1, dtype=torch.int64, device="cuda"), status=st)
+    torch.cuda.synchronize()
+    assert torch.all(st == 7)
 
 
 def test_oversize_is_refused():
