@@ -71,7 +71,7 @@ def gram_mf(H, y, sigma2):
     return A, b
 
 
-def gram_emul(H, y, sigma2, gram):
+def gram_emul(H, y, sigma2, gram, order_seed=None):
     """Gram step at precision ``gram`` -> (A, b).
 
     * fp64: A = H^H H + sigma^2 I and b = H^H y exactly in float64.
@@ -82,6 +82,14 @@ def gram_emul(H, y, sigma2, gram):
       products are exact and summed at fp32: A = fl32(fl_g(H)^H fl_g(H)) +
       fl32(sigma^2), b = fl32(fl_g(H)^H fl_g(y)).
     A is exactly Hermitian (only one triangle is formed and mirrored).
+
+    order_seed (not the default model): the sums over the antennas are
+    instead accumulated one term at a time in fp32, in an order drawn from
+    this seed (the same for every system).  The products and every rounding
+    format stay those above; only the order of the fp32 additions, which the
+    tensor-core model leaves open, changes.  The spread between the two gives
+    the part of a GPU-vs-oracle difference that comes from the order of
+    summation alone.
     """
     Hs = _c128(H)
     ys = _c128(y)
@@ -94,9 +102,19 @@ def gram_emul(H, y, sigma2, gram):
     elif gram != "fp32":
         raise ValueError(gram)
     s2 = fl(s2, "fp32")
-    G = flc(_hermitian(np.conj(Hs) @ np.swapaxes(Hs, -1, -2)), "fp32")
+    if order_seed is None:
+        G = flc(_hermitian(np.conj(Hs) @ np.swapaxes(Hs, -1, -2)), "fp32")
+        b = flc(np.einsum("bkn,bn->bk", np.conj(Hs), ys), "fp32")
+    else:
+        perm = np.random.default_rng(order_seed).permutation(Hs.shape[-1])
+        G = np.zeros(Hs.shape[:-1] + (Hs.shape[-2],), dtype=np.complex128)
+        b = np.zeros(Hs.shape[:-1], dtype=np.complex128)
+        for n in perm:
+            h = Hs[..., n]                                           # (batch, K)
+            G = flc(G + np.conj(h)[..., :, None] * h[..., None, :], "fp32")
+            b = flc(b + np.conj(h) * ys[..., n, None], "fp32")
+        G = _hermitian(G)
     A = flc(_add_diag(G, s2), "fp32")
-    b = flc(np.einsum("bkn,bn->bk", np.conj(Hs), ys), "fp32")
     return A, b
 
 
@@ -210,31 +228,54 @@ def _acc_fmt(mv):
     return "fp64" if mv == "fp64" else "fp32"
 
 
-def _dot_re(u, v, fmt):
-    """fl_fmt(Re(u^H v)) with the sum formed in float64."""
-    return fl(np.real(np.einsum("bk,bk->b", np.conj(u), v)), fmt)
+def _dot_re(u, v, fmt, perm=None):
+    """fl_fmt(Re(u^H v)) with the sum formed in float64 (perm: instead
+    accumulated term by term in fp32 in that order, then rounded to fmt)."""
+    if perm is None:
+        return fl(np.real(np.einsum("bk,bk->b", np.conj(u), v)), fmt)
+    t = np.real(np.conj(u) * v)
+    acc = np.zeros(t.shape[0])
+    for k in perm:
+        acc = fl(acc + t[:, k], "fp32")
+    return fl(acc, fmt)
+
+
+def _matvec(A_mv, pq, acc, perm=None):
+    """fl_acc(A_mv pq) (perm: the sum over columns accumulated in fp32 in that order)."""
+    if perm is None:
+        return flc(np.einsum("bkl,bl->bk", A_mv, pq), acc)
+    out = np.zeros(pq.shape, dtype=np.complex128)
+    for j in perm:
+        out = flc(out + A_mv[:, :, j] * pq[:, j, None], acc)
+    return out
 
 
 def fp_cg(A_mv, b, iters, mv, ip="fp32", w="fp32", Md=None, alpha_num=0,
-          block=32, trace=False):
+          block=32, trace=False, order_seed=None):
     """Algorithm 2 (Md is None) or Algorithm 3 (Md = block inverses).
 
     A_mv must already hold A rounded for the matvec (``round_matvec_operand``).
     Returns (x, status, hist, tr): hist[:, i] = ||r_i||_2 (recursive residual,
     i = 0..iters) and tr = per-iteration (x_i, r_i) lists when ``trace``.
+    order_seed (not the default model): the fp32 sums of the matvec and of the
+    inner products accumulate term by term in an order drawn from the seed.
     """
     b = _c128(b)
     B, K = b.shape
     acc = _acc_fmt(mv)
+    perm = None if order_seed is None else np.random.default_rng(order_seed).permutation(K)
+    if perm is not None and acc != "fp32":
+        perm = None                                       # fp64 mode: no fp32 sums to reorder
+    _dot = (lambda u, v, f: _dot_re(u, v, f, perm))
     x = np.zeros_like(b)
     r = flc(b, w)
     if Md is None:
         p = r.copy()
-        rho = _dot_re(r, r, ip)                           # r_0^H r_0
+        rho = _dot(r, r, ip)                           # r_0^H r_0
     else:
         z = flc(bj_apply(Md, r), w)                       # p_0 = M_d r_0
         p = z
-        rho = _dot_re(r, z, ip)                           # r_0^H z_0 (alpha_num=1)
+        rho = _dot(r, z, ip)                           # r_0^H z_0 (alpha_num=1)
     status = np.zeros(B, dtype=np.int32)
     active = np.ones(B, dtype=bool)
     hist = np.zeros((B, iters + 1))
@@ -242,10 +283,10 @@ def fp_cg(A_mv, b, iters, mv, ip="fp32", w="fp32", Md=None, alpha_num=0,
     tr = {"x": [x.copy()], "r": [r.copy()]} if trace else None
     for i in range(iters):
         pq = round_matvec_operand(p, mv, block)
-        varpi = flc(np.einsum("bkl,bl->bk", A_mv, pq), acc)        # u_MV
-        phi = _dot_re(p, varpi, ip)                                # u_IP
+        varpi = _matvec(A_mv, pq, acc, perm)                       # u_MV
+        phi = _dot(p, varpi, ip)                                # u_IP
         if Md is not None and alpha_num == 0:
-            rho_prev = _dot_re(r, p, ip)                           # r^H p (Alg. 3)
+            rho_prev = _dot(r, p, ip)                           # r^H p (Alg. 3)
         else:
             rho_prev = rho
         zero = active & (rho_prev == 0)
@@ -259,10 +300,10 @@ def fp_cg(A_mv, b, iters, mv, ip="fp32", w="fp32", Md=None, alpha_num=0,
         r_n = flc(r - alpha[:, None] * varpi, w)
         if Md is None:
             z_n = r_n
-            rho_n = _dot_re(r_n, r_n, ip)
+            rho_n = _dot(r_n, r_n, ip)
         else:
             z_n = flc(bj_apply(Md, r_n), w)
-            rho_n = _dot_re(r_n, z_n, ip)
+            rho_n = _dot(r_n, z_n, ip)
         safe_rho = np.where(active, rho_prev, 1.0)
         beta = fl(np.where(active, rho_n, 0.0) / safe_rho, w)
         p_n = flc(z_n + beta[:, None] * p, w)
@@ -306,12 +347,14 @@ def resid_h(H, y, sigma2, x):
     return np.einsum("bkn,bn->bk", np.conj(Hs), e) - np.asarray(sigma2, dtype=np.float64)[:, None] * x
 
 
-def detect(H, y, sigma2, qam_order, iters, prec=None, L=None, block=32):
+def detect(H, y, sigma2, qam_order, iters, prec=None, L=None, block=32, order_seed=None):
     """Emulate one detection call; returns a dict of results.
 
     prec keys: gram, mv, ip, w in {"fp64","fp32","fp16","bf16"} (mv also
     "e4m3"), refine_steps, refine_iters (default: iters), alpha_num, resid.
     L: block-Jacobi block size (None = FP-CG, Algorithm 2).
+    order_seed: the fp32 sums of the Gram step, the matvec and the inner
+    products in other orders (gram_emul, fp_cg); everything else unchanged.
 
     Iterative refinement (not in the paper; Theorem 2 of Section III-B is its
     motivation: the attainable accuracy of FP-CG is limited by the gap between
@@ -332,7 +375,7 @@ def detect(H, y, sigma2, qam_order, iters, prec=None, L=None, block=32):
     pr.update(prec or {})
     w = pr["w"]
     mode = RESID_MODES[pr.get("resid", "gram")]
-    A, b = gram_emul(H, y, sigma2, pr["gram"])
+    A, b = gram_emul(H, y, sigma2, pr["gram"], order_seed)
     B = A.shape[0]
     status = np.zeros(B, dtype=np.int32)
     Md = None
@@ -351,12 +394,13 @@ def detect(H, y, sigma2, qam_order, iters, prec=None, L=None, block=32):
 
         def true_res(x):
             return resid(A_res, x, b)
-    x, st, hist, _ = fp_cg(A_mv, b, iters, pr["mv"], pr["ip"], w, Md, pr["alpha_num"], block)
+    cg_seed = None if order_seed is None else order_seed + 7919
+    x, st, hist, _ = fp_cg(A_mv, b, iters, pr["mv"], pr["ip"], w, Md, pr["alpha_num"], block, order_seed=cg_seed)
     status |= st
     ri = pr["refine_iters"] if pr["refine_iters"] is not None else iters
     for _ in range(int(pr["refine_steps"])):
         rr = flc(true_res(x), w)
-        d, st2, _, _ = fp_cg(A_mv, rr, ri, pr["mv"], pr["ip"], w, Md, pr["alpha_num"], block)
+        d, st2, _, _ = fp_cg(A_mv, rr, ri, pr["mv"], pr["ip"], w, Md, pr["alpha_num"], block, order_seed=cg_seed)
         status |= st2 & ST_BREAKDOWN
         x = flc(x + d, w)
     nb = np.linalg.norm(_c128(b_ref), axis=1)

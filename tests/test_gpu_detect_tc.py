@@ -1,7 +1,9 @@
 """Fused tensor-core detector (tcgen05 Gram + mma.sync FP-(BJ-)CG) against the
-oracle's emulation of the same precisions.  Bar: x_hat within 2e-3 relative
-(99th percentile; 1e-2 for every system), labels equal to the oracle's slicer on
-the same estimates, bit-error counter and residual consistent with them."""
+oracle's emulation of the same precisions.  Bar: x_hat within 2e-3 relative for
+every system, or within twice the oracle's own spread on that system when only
+the fp32 summation order of its Gram step changes (gpu_helpers.
+check_reduced_parity); labels equal to the oracle's slicer on the same
+estimates, bit-error counter and residual consistent with them."""
 import numpy as np
 import pytest
 import torch
@@ -11,7 +13,7 @@ from oracle import qam as Q
 from paper_2504_09820_gb300 import fpcg as F
 from paper_2504_09820_gb300 import workload as wl
 
-from gpu_helpers import gpu_detect, oracle_detect, rel_err, to_dev
+from gpu_helpers import check_reduced_parity, gpu_detect, oracle_detect, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -23,9 +25,8 @@ def _lib():
     F.lib()
 
 
-def _check(d, res, ref, tol=2e-3):
-    e = rel_err(res["x"], ref["x"])
-    assert np.quantile(e, 0.99) < tol and e.max() < 5 * tol, (np.quantile(e, 0.99), e.max())
+def _check(d, res, ref, iters, pk, L, tol=2e-3):
+    check_reduced_parity(d, res["x"], ref["x"], iters, pk, L=L, tol=tol)
     M = int(d["qam"][0])
     assert np.array_equal(Q.slice_symbols(res["x"], M, "fp32"), res["sym"])
     assert int(res["bit_errors"][0]) == Q.bit_errors(res["sym"], d["tx"])
@@ -95,7 +96,7 @@ def test_fused_matches_oracle(K, gram, mv, L, iters, refine, resid):
     assert F.fpcg_path(N, K, L, F.precision(**pk)) == F.PATH_TENSOR_CORE
     res = gpu_detect(d, iters, pk, L=(L or None))
     ref = oracle_detect(d, iters, pk, L=(L or None))
-    _check(d, res, ref)
+    _check(d, res, ref, iters, pk, L or None)
     own = _own_residual(d, res, gram, mv, resid)
     assert np.allclose(res["rel_res"], own, rtol=2e-3, atol=1e-6)
 
@@ -113,8 +114,7 @@ def test_fused_headline_config_full_size_sampled():
     rng = np.random.default_rng(0)
     sel = np.sort(rng.choice(spec.batch, 96, replace=False))
     ref = oracle_detect(d, HEAD["iters"], pk, L=HEAD["L"], sel=sel)
-    e = rel_err(res["x"][sel], ref["x"])
-    assert np.quantile(e, 0.99) < 2e-3 and e.max() < 1e-2, (np.quantile(e, 0.99), e.max())
+    check_reduced_parity(d, res["x"][sel], ref["x"], HEAD["iters"], pk, L=HEAD["L"], sel=sel)
     assert np.array_equal(Q.slice_symbols(res["x"], 64, "fp32"), res["sym"])
     assert int(res["bit_errors"][0]) == Q.bit_errors(res["sym"], d["tx"])
     # BER of the fused path within 5% of the fp64 direct LMMSE solve (sample)
@@ -131,7 +131,7 @@ def test_fused_hist_alpha_and_ip_rounding():
                   (dict(gram="fp16", mv="fp16", refine_steps=2), 4)):
         res = gpu_detect(d, 6, pk, L=L, hist=True)
         ref = oracle_detect(d, 6, pk, L=L)
-        _check(d, res, ref, tol=(5e-3 if pk.get("ip") == "bf16" else 2e-3))
+        _check(d, res, ref, 6, pk, L)
         # ||r_i|| of late iterations is ~1% of ||r_0||; the iterates agree to ~1e-3
         assert np.allclose(res["hist"], ref["hist"], rtol=2e-2, atol=2e-3 * ref["hist"][:, :1])
 
@@ -168,4 +168,4 @@ def test_fused_edge_cases():
     d1 = wl.generate(wl.Spec(N=64, K=16, batch=3, qam=16, snr_db=10.0, seed=4))
     res = gpu_detect(d1, 8, dict(gram="bf16", mv="bf16"), L=4)
     ref = oracle_detect(d1, 8, dict(gram="bf16", mv="bf16"), L=4)
-    assert rel_err(res["x"], ref["x"]).max() < 1e-2
+    check_reduced_parity(d1, res["x"], ref["x"], 8, dict(gram="bf16", mv="bf16"), L=4)

@@ -9,7 +9,7 @@ from oracle import qam as Q
 from paper_2504_09820_gb300 import fpcg as F
 from paper_2504_09820_gb300 import workload as wl
 
-from gpu_helpers import oracle_detect, rel_err
+from gpu_helpers import check_reduced_parity, oracle_detect, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -61,8 +61,7 @@ def test_plan_matches_oracle_per_class(mixed):
         cd = _class_data(d, idx)
         ref = oracle_detect(cd, ITERS, PREC, L=c["block_L"])
         xs = np.stack([x[i] for i in idx])
-        e = rel_err(xs, ref["x"])
-        assert np.quantile(e, 0.99) < 2e-3 and e.max() < 1e-2, (c, np.quantile(e, 0.99), e.max())
+        check_reduced_parity(cd, xs, ref["x"], ITERS, PREC, L=c["block_L"])
         # with one block (L = K) Algorithm 3 is exact after one step (Appendix D); the later
         # steps work on a rounding-level residual, where a frozen breakdown is legitimate
         allowed = F.ST_RHO_ZERO | (F.ST_BREAKDOWN if c["block_L"] == c["k"] else 0)
