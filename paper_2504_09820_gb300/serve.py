@@ -13,6 +13,13 @@ batching: their work overlaps on the GPU); the rest wait in arrival order.
 Latency is measured on the host from a request's arrival to the moment its
 results are in host memory (its completion event is polled).
 
+With gram_max_age > 0 the server also keeps Gram matrices across slots:
+requests that carry a channel key (one user group's channel, aged by the
+Gauss-Markov model of Section V-C from slot to slot) reuse the channel
+estimate and the Gram matrices formed for an earlier slot of that key while
+it is at most gram_max_age slots old, so such a slot is only copies in,
+matched filters and solves; an older (or first) slot forms and keeps new ones.
+
 Everything the detection computes runs in libfpcg's kernels; this module
 moves bytes and keeps time.
 """
@@ -82,9 +89,13 @@ class Request:
     sigma2: torch.Tensor        # [n_rb] float64
     qam: torch.Tensor           # [n_re] int32
     tx: torch.Tensor = None     # [n_re][K] uint8 (optional: bit errors)
+    key: object = None          # channel key (Gram reuse across slots); None: not kept
+    slot_index: int = 0         # slot number of this request's channel estimate
     out: dict = field(default_factory=dict)
     admitted: float = None
     done: float = None
+    reused: bool = False        # detected against a kept Gram of an earlier slot
+    keep: list = field(default_factory=list)  # device tensors the in-flight work reads
 
     @property
     def n_rb(self):
@@ -121,7 +132,7 @@ class Server:
     """Runs requests on `n_streams` streams inside a device memory budget."""
 
     def __init__(self, budget_bytes, n_streams=4, iters=6, block_L=8, prec=None, device="cuda",
-                 max_rb_n=275 * 512):
+                 max_rb_n=275 * 512, gram_max_age=0):
         F.lib()
         self.dev = torch.device(device)
         self.arena = Arena(budget_bytes)
@@ -133,6 +144,8 @@ class Server:
         self.prec = F.precision(**self.prec_kw)
         # fpcg_gram also forms b for one y per system; the Gram is all a slot needs
         self.zero_y = torch.zeros(max_rb_n, dtype=torch.complex64, device=self.dev)
+        self.gram_max_age = int(gram_max_age)
+        self.kept = {}   # key -> dict(H, A, b, slot, shape, ready event): kept outside the budget
 
     def _views(self, off, req):
         v, pos = {}, off
@@ -142,17 +155,46 @@ class Server:
             pos += -(-nb // 256) * 256
         return v
 
+    def _kept_gram(self, req, v, stream):
+        """The channel estimate and Gram matrices this request detects with: a
+        kept entry of its key while young enough, else new ones formed on
+        `stream` (and kept when the request has a key)."""
+        shape = (req.n_rb, req.K, req.N)
+        ent = self.kept.get(req.key) if (self.gram_max_age > 0 and req.key is not None) else None
+        if ent is not None and ent["shape"] == shape and 0 <= req.slot_index - ent["slot"] <= self.gram_max_age:
+            stream.wait_event(ent["ready"])   # formed on another stream, maybe
+            req.reused = True
+            req.keep = [ent["H"], ent["A"]]
+            for t in req.keep:
+                t.record_stream(stream)
+            return ent["H"], ent["A"]
+        if self.gram_max_age > 0 and req.key is not None:
+            # a new entry (tensors of an older one stay alive while requests still read them)
+            H = torch.empty(shape, dtype=torch.complex64, device=self.dev)
+            A = torch.empty((req.n_rb, req.K, req.K), dtype=torch.complex64, device=self.dev)
+            b = torch.empty((req.n_rb, req.K), dtype=torch.complex64, device=self.dev)
+        else:
+            H, A, b = v["H"], v["A"], v["b"]
+        H.copy_(req.H, non_blocking=True)
+        zy = self.zero_y[:req.n_rb * req.N].view(req.n_rb, req.N)
+        F.fpcg_gram(H, zy, v["sigma2"], self.prec_kw["gram"], A, b, stream=stream)
+        if H is not v["H"]:
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            self.kept[req.key] = {"H": H, "A": A, "b": b, "slot": req.slot_index, "shape": shape, "ready": ev}
+            req.keep = [H, A]
+        return H, A
+
     def _issue(self, req, stream, off):
         v = self._views(off, req)
         with torch.cuda.stream(stream):
-            for k in ("H", "y", "rb", "start", "sigma2", "qam"):
+            for k in ("y", "rb", "start", "sigma2", "qam"):
                 v[k].copy_(getattr(req, k), non_blocking=True)
             if req.tx is not None:
                 v["tx"].copy_(req.tx, non_blocking=True)
-            zy = self.zero_y[:req.n_rb * req.N].view(req.n_rb, req.N)
-            F.fpcg_gram(v["H"], zy, v["sigma2"], self.prec_kw["gram"], v["A"], v["b"], stream=stream)
+            H, A = self._kept_gram(req, v, stream)
             L = min(self.block_L, req.K) if self.block_L else 0
-            F.fpcg_detect_grouped(v["A"], v["H"], v["y"], v["start"], v["qam"], self.iters, L, self.prec, v["x"],
+            F.fpcg_detect_grouped(A, H, v["y"], v["start"], v["qam"], self.iters, L, self.prec, v["x"],
                                   sym_idx=v["sym"], rel_res=v["rel"],
                                   tx_idx=v["tx"] if req.tx is not None else None,
                                   bit_errors=v["bits"] if req.tx is not None else None,
