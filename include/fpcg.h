@@ -347,6 +347,9 @@ typedef struct fpcg_class_info {
   int32_t n_rx, k, block_L; /* the class's N, K and block size (0: FP-CG) */
   int32_t path;             /* FPCG_PATH_SIMT, FPCG_PATH_TENSOR_CORE or FPCG_PATH_TWO_PASS */
   int64_t first, count;     /* its systems: plan positions [first, first + count) */
+  int32_t mv;               /* its matvec format (the plan's, or fpcg_plan_autoprec's choice) */
+  int32_t reserved;
+  double kappa;             /* fpcg_plan_autoprec's condition-number estimate, 0 before */
 } fpcg_class_info;
 
 /* Builds a plan (host only, no GPU work).  FPCG_EINVAL for a bad descriptor,
@@ -366,6 +369,21 @@ FPCG_API int fpcg_plan_classes(const fpcg_plan* plan, int32_t* n_classes, fpcg_c
 FPCG_API int fpcg_plan_autotune(fpcg_plan* plan, const void* H, const void* y, const double* sigma2,
                                 const int32_t* qam_order, void* x_hat, uint8_t* sym_idx,
                                 double* rel_res, int32_t* status, void* stream);
+
+/* Precision selection per class (Sections III-B and IV-B): for every class,
+ * fp32 CG (and, with block_L > 0, fp32 FP-BJ-CG) runs min(K, 32) steps on up
+ * to 64 of its systems and fpcg_kappa_cg_batch turns the step sizes into
+ * condition-number estimates (the median is kept: kappa of A, and kappa_bar
+ * of the preconditioned matrix).  The matvec format is then the one eq.
+ * heuristic (eq. heuristic_bj for FP-BJ-CG) chooses, capped at fp32, and
+ * FP-CG or FP-BJ-CG is chosen by the break-even criterion of Remark 4
+ * (fpcg_choose_method with target accuracy tol).  The choices replace the
+ * class's mv and block size; its kernel is chosen again (the default, until the
+ * next autotune).  Synchronises `stream`; drops a captured graph and the
+ * two-pass workspace (allocated again by the next run).  Allocates, and
+ * frees, a small device buffer of its own. */
+FPCG_API int fpcg_plan_autoprec(fpcg_plan* plan, const void* H, const void* y, const double* sigma2, double tol,
+                                void* stream);
 
 /* Detects the whole batch (plan order), asynchronously on `stream`.  Arguments
  * as for fpcg_detect, with the packed buffers of fpcg_plan_layout; bit_errors
@@ -409,6 +427,25 @@ FPCG_API int fpcg_detect_noalloc(const void* H, const void* y, const double* sig
                                  int32_t* status, void* stream);
 
 /*
+ * fpcg_detect_coeffs -- fpcg_detect (block_L = 0) or fpbjcg_detect (block_L > 0)
+ * that also returns the step sizes of the main solve (Algorithm 2 / 3):
+ *   coeffs  [batch][2][iters] float, device, required: coeffs[s][0][j] = alpha_j
+ *           and coeffs[s][1][j] = beta_j for j < iters (0 after a breakdown or
+ *           rho = 0 stopped the solve).  Refinement passes are not recorded.
+ * These are what the exact-arithmetic relation between CG and the Lanczos
+ * process turns into Ritz values of A (of the preconditioned matrix for
+ * Algorithm 3): fpcg_kappa_cg / fpcg_kappa_cg_batch estimate the condition
+ * number that the precision heuristic of Section III-B needs from them.
+ * Runs on the SIMT kernel (one CTA per system), which records them; other
+ * arguments and errors as fpcg_detect (no res_hist).
+ */
+FPCG_API int fpcg_detect_coeffs(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+                                int32_t n_rx, int32_t k, int64_t batch, int32_t iters, int32_t block_L,
+                                const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx, double* rel_res,
+                                const uint8_t* tx_idx, unsigned long long* bit_errors, int32_t* status,
+                                float* coeffs, void* stream);
+
+/*
  * ---- Precision selection (Section IV-B, eq. heuristic and eq. heuristic_bj) ----
  *
  * fpcg_choose_precision -- the lowest-precision Table I format (BF16, FP16,
@@ -431,6 +468,32 @@ FPCG_API int fpcg_choose_precision(int32_t k, double kappa, double* u_bound);
  * FPCG_EINVAL for m < 1, alpha_j <= 0 or beta_j < 0.  Host only.
  */
 FPCG_API int fpcg_kappa_cg(const double* alpha, const double* beta, int32_t m, double* kappa_hat);
+
+/*
+ * fpcg_kappa_cg_batch -- fpcg_kappa_cg for every system of a coefficient array
+ * as fpcg_detect_coeffs writes it (host memory, [batch][2][iters]), from the
+ * first m <= iters step sizes: kappa_hat[s] (host, [batch]) is the estimate,
+ * or NaN where the coefficients do not define one (a solve stopped before m
+ * steps).  FPCG_EINVAL for m < 1, m > iters or a null pointer.  Host only.
+ */
+FPCG_API int fpcg_kappa_cg_batch(const float* coeffs, int32_t iters, int32_t m, int64_t batch, double* kappa_hat);
+
+/*
+ * fpcg_choose_method -- the break-even criterion of Remark 4 between FP-CG and
+ * FP-BJ-CG with block size L: preconditioning pays when the iterations it
+ * saves exceed C_BJ / C_CG^it + k_PCG (C_PCG^it / C_CG^it - 1).  Costs are the
+ * multiplications of the paper's cost model (Section V-A.1, weights bf16 = fp16
+ * = 1, fp32 = 2, fp64 = 4): C_CG^it = K^2 w(mv_cg), C_PCG^it = K^2 w(mv_bj) +
+ * K L w(w), C_BJ = (K / L) L^3 w(w).  The iteration counts k are those the CG
+ * bound 2 ((sqrt(kappa) - 1) / (sqrt(kappa) + 1))^k <= tol asks for, with
+ * kappa for FP-CG and kappa_bar (the preconditioned matrix's) for FP-BJ-CG.
+ * Returns L (use FP-BJ-CG) or 0 (use FP-CG); *k_cg and *k_pcg (nullable)
+ * receive the counts.  -FPCG_EINVAL for K < 1, L < 1, K % L, kappa or
+ * kappa_bar < 1 or not finite, tol outside (0, 1), or an unknown format.
+ * Host only.
+ */
+FPCG_API int fpcg_choose_method(int32_t k, int32_t block_L, double kappa, double kappa_bar, double tol,
+                                int32_t mv_cg, int32_t mv_bj, int32_t w, int32_t* k_cg, int32_t* k_pcg);
 
 /* Human-readable text for a return code (static storage). */
 FPCG_API const char* fpcg_strerror(int code);

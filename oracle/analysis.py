@@ -103,3 +103,29 @@ def bj_preconditioned(A, Md_blocks):
         w, V = np.linalg.eigh(Md_blocks[:, i])
         Mh[:, i * L:(i + 1) * L, i * L:(i + 1) * L] = (V * np.sqrt(w)[:, None, :]) @ np.conj(np.swapaxes(V, -1, -2))
     return Mh @ np.asarray(A, dtype=np.complex128) @ Mh
+
+
+def cg_iterations(kappa, tol):
+    """Iterations k that the classical CG bound 2 q^k <= tol asks for, with
+    q = (sqrt(kappa) - 1) / (sqrt(kappa) + 1) (the A-norm error bound the
+    iteration counts of a break-even comparison are read from); 1 for kappa = 1."""
+    sk = np.sqrt(float(kappa))
+    q = (sk - 1.0) / (sk + 1.0)
+    if q <= 0.0:
+        return 1
+    return int(np.ceil(np.log(tol / 2.0) / np.log(q)))
+
+
+def break_even(N, L, kappa, kappa_bar, tol, mv_cg="fp16", mv_bj="fp16", w="fp32"):
+    """Remark 4's break-even criterion: FP-BJ-CG (block L) is preferable when
+    k_CG - k_PCG > C_BJ / C_CG^it + k_PCG (C_PCG^it / C_CG^it - 1), with the
+    per-iteration and setup costs of the cost model (Section V-A.1: C_CG^it =
+    N^2 w(mv_cg), C_PCG^it = N^2 w(mv_bj) + N L w(w), C_BJ = (N/L) L^3 w(w))
+    and the iteration counts of cg_iterations for kappa and kappa_bar.
+    Returns (L or 0, k_CG, k_PCG)."""
+    k_cg, k_pcg = cg_iterations(kappa, tol), cg_iterations(kappa_bar, tol)
+    c_it = N * N * WEIGHT[mv_cg]
+    p_it = N * N * WEIGHT[mv_bj] + N * L * WEIGHT[w]
+    c_bj = cost_bj_setup(N, L, w)
+    use_bj = (k_cg - k_pcg) > c_bj / c_it + k_pcg * (p_it / c_it - 1.0)
+    return (L if use_bj else 0), k_cg, k_pcg

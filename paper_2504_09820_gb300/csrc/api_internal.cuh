@@ -20,7 +20,7 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
                 int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
                 double* rel_res, float* res_hist, const uint8_t* tx_idx,
                 unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits,
-                bool status_or = false);
+                bool status_or = false, float* coeffs = nullptr);
 
 // Checks of the arguments common to every detection entry point (no GPU
 // work): FPCG_OK or FPCG_EINVAL.

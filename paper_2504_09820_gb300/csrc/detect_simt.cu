@@ -425,7 +425,7 @@ __device__ inline void apply_precond(const SimtParams& P, const Smem<T>& S, cons
 // ---------------------------------------------------------------------------
 template <typename T, int MV>
 __device__ int cg_phase(const SimtParams& P, const Smem<T>& S, const cplx<T>* rhs, int iters,
-                        float* hist) {
+                        float* hist, float* coef = nullptr) {
   const int K = P.K, AS = K + 1, L = P.L, NB = (2 * K + 31) / 32;
   const int tid = threadIdx.x;
   int tpr = 32;
@@ -528,6 +528,7 @@ __device__ int cg_phase(const SimtParams& P, const Smem<T>& S, const cplx<T>* rh
       continue;
     }
     const T alpha = rho_prev / phi;
+    if (coef && tid == 0) coef[it] = (float)alpha;
     for (int k = tid; k < K; k += NT) {
       cplx<T> x = S.x[k], r = S.r[k];
       const cplx<T> p = S.p[k], w = S.w[k];
@@ -551,6 +552,7 @@ __device__ int cg_phase(const SimtParams& P, const Smem<T>& S, const cplx<T>* rh
     block_sum2(rz, rr, S.red);
     const T rho_new = round_ip(rz, P.ip);
     const T beta = rho_new / rho_prev;
+    if (coef && tid == 0) coef[iters + it] = (float)beta;
     for (int k = tid; k < K; k += NT) {
       cplx<T> p = S.p[k];
       const cplx<T> z = zz[k];
@@ -697,7 +699,11 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
     __syncthreads();
   }
   float* hist = P.res_hist ? P.res_hist + (size_t)sys * (P.iters + 1) : nullptr;
-  st |= cg_phase<T, MV>(P, S, S.b, P.iters, hist);
+  float* coef = P.coeffs ? P.coeffs + (size_t)sys * 2 * P.iters : nullptr;
+  if (coef)  // a solve that stops early leaves zeros
+    for (int k = threadIdx.x; k < 2 * P.iters; k += NT) coef[k] = 0.f;
+  __syncthreads();
+  st |= cg_phase<T, MV>(P, S, S.b, P.iters, hist, coef);
 
   // refinement: x_hat += solve(A, b - A x_hat)
   for (int rs = 0; rs < P.refine_steps; ++rs) {

@@ -28,6 +28,7 @@ struct SimtParams {
   int32_t* status;
   void* A_out;              // gram-only mode: write A [batch][K][K] and b, then stop
   void* b_out;
+  float* coeffs;            // [batch][2][iters] or null: alpha_j, beta_j of the main solve
 };
 
 size_t simt_smem_bytes(int fp64, int K, int L, int mv);

@@ -104,7 +104,7 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
                 int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
                 double* rel_res, float* res_hist, const uint8_t* tx_idx,
                 unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits,
-                bool status_or) {
+                bool status_or, float* coeffs) {
   int rc = check_prec(prec);
   if (rc) return rc;
   rc = check_detect_args(k, batch, iters, block_L, x_hat, sym_idx, qam_order, tx_idx, bit_errors);
@@ -124,7 +124,8 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
                                      aligned16(bin)
                                : tc_capable(k, block_L, prec) && fpcg::tma_pipe_ok(H, y, n_rx);
   if (path == FPCG_PATH_TENSOR_CORE && !tc_possible) return FPCG_ENOTSUP;
-  const bool tc_ok = tc_possible && (path == FPCG_PATH_TENSOR_CORE || (path < 0 && !force_simt()));
+  // the step sizes are recorded by the SIMT kernel only (keeping the tensor-core CG loop small)
+  const bool tc_ok = tc_possible && !coeffs && (path == FPCG_PATH_TENSOR_CORE || (path < 0 && !force_simt()));
   if (tc_ok && Ain) {  // given Gram matrices: the tensor-core solver
     int sms = 0;
     rc = device_sms(&sms);
@@ -197,6 +198,7 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
   P.tx = tx_idx;
   P.bit_errors = bit_errors;
   P.status = status;
+  P.coeffs = coeffs;
   cudaError_t e = fpcg::launch_detect_simt(P, fp64, fp64 ? FPCG_FP64 : prec->mv, s);
   if (e != cudaSuccess) return cuda_fail(e);
   return FPCG_OK;
@@ -418,6 +420,16 @@ int fpcg_detect_grouped(const void* A, const void* H, const void* y, const int64
   P.status = status;
   cudaError_t e = fpcg::launch_detect_simt(P, fp64, fp64 ? FPCG_FP64 : prec->mv, s);
   return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+}
+
+int fpcg_detect_coeffs(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
+                       int32_t n_rx, int32_t k, int64_t batch, int32_t iters, int32_t block_L,
+                       const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx, double* rel_res,
+                       const uint8_t* tx_idx, unsigned long long* bit_errors, int32_t* status, float* coeffs,
+                       void* stream) {
+  if (!coeffs) return FPCG_EINVAL;
+  return fpcg::run_uniform(H, y, sigma2, qam_order, nullptr, nullptr, n_rx, k, batch, iters, block_L, prec, x_hat,
+                           sym_idx, rel_res, nullptr, tx_idx, bit_errors, status, stream, -1, true, false, coeffs);
 }
 
 int fpcg_solve_gram(const void* A, const void* b, int32_t k, int64_t batch, int32_t iters,

@@ -46,6 +46,25 @@ double eig(const std::vector<double>& d, const std::vector<double>& e, int j) {
   return 0.5 * (lo + hi);
 }
 
+// Multiplication weights of the cost model (Section V-A.1): 16-bit 1, fp32 2, fp64 4.
+double weight(int32_t fmt) {
+  switch (fmt) {
+    case FPCG_BF16:
+    case FPCG_FP16: return 1.0;
+    case FPCG_FP32: return 2.0;
+    case FPCG_FP64: return 4.0;
+    default: return 0.0;
+  }
+}
+
+// Iterations the CG bound 2 q^k <= tol asks for, q = (sqrt(kappa) - 1) / (sqrt(kappa) + 1).
+int cg_iterations(double kappa, double tol) {
+  const double sk = sqrt(kappa);
+  const double q = (sk - 1.0) / (sk + 1.0);
+  if (q <= 0.0) return 1;
+  return (int)ceil(log(tol / 2.0) / log(q));
+}
+
 }  // namespace
 
 extern "C" {
@@ -71,6 +90,36 @@ int fpcg_kappa_cg(const double* alpha, const double* beta, int32_t m, double* ka
   if (!(lmin > 0.0)) return FPCG_EINVAL;
   *kappa_hat = lmax / lmin;
   return FPCG_OK;
+}
+
+int fpcg_kappa_cg_batch(const float* coeffs, int32_t iters, int32_t m, int64_t batch, double* kappa_hat) {
+  if (!coeffs || !kappa_hat || m < 1 || m > iters || batch < 0) return FPCG_EINVAL;
+  std::vector<double> a((size_t)m), b((size_t)m);
+  for (int64_t s = 0; s < batch; ++s) {
+    const float* c = coeffs + (size_t)s * 2 * iters;
+    for (int j = 0; j < m; ++j) {
+      a[(size_t)j] = c[j];
+      b[(size_t)j] = c[iters + j];
+    }
+    double k = NAN;
+    if (fpcg_kappa_cg(a.data(), b.data(), m, &k) != FPCG_OK) k = NAN;
+    kappa_hat[s] = k;
+  }
+  return FPCG_OK;
+}
+
+int fpcg_choose_method(int32_t k, int32_t block_L, double kappa, double kappa_bar, double tol, int32_t mv_cg,
+                       int32_t mv_bj, int32_t w, int32_t* k_cg, int32_t* k_pcg) {
+  const double wc = weight(mv_cg), wb = weight(mv_bj), ww = weight(w);
+  if (k < 1 || block_L < 1 || k % block_L || !(kappa >= 1.0) || !isfinite(kappa) || !(kappa_bar >= 1.0) ||
+      !isfinite(kappa_bar) || !(tol > 0.0 && tol < 1.0) || wc <= 0.0 || wb <= 0.0 || ww <= 0.0)
+    return -FPCG_EINVAL;
+  const int kc = cg_iterations(kappa, tol), kp = cg_iterations(kappa_bar, tol);
+  if (k_cg) *k_cg = kc;
+  if (k_pcg) *k_pcg = kp;
+  const double K = k, L = block_L;
+  const double c_it = K * K * wc, p_it = K * K * wb + K * L * ww, c_bj = (K / L) * L * L * L * ww;
+  return (double)(kc - kp) > c_bj / c_it + kp * (p_it / c_it - 1.0) ? block_L : 0;
 }
 
 }  // extern "C"

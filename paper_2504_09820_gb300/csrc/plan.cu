@@ -14,6 +14,8 @@
 struct fpcg_plan {
   struct Class {
     int32_t n, k, L, path;         // path: -1 = default choice, else FPCG_PATH_*
+    fpcg_precision prec;           // the plan's, or the one fpcg_plan_autoprec chose for the class
+    double kappa = 0.0;            // fpcg_plan_autoprec's estimate (0: none)
     int64_t first, count;          // plan positions
     int64_t h0, y0, x0;            // first element of the class in H, y, x_hat
     int64_t a0, b0;                // two-pass classes: first Gram entry / matched-filter entry in the workspace
@@ -42,8 +44,9 @@ void drop_graph(fpcg_plan* p) {
 }
 
 int default_path(const fpcg_plan* p, const fpcg_plan::Class& c) {
-  if (fpcg::two_pass_capable(c.k, c.L, &p->prec)) return FPCG_PATH_TWO_PASS;
-  return fpcg_path(c.n, c.k, c.L, &p->prec);
+  (void)p;
+  if (fpcg::two_pass_capable(c.k, c.L, &c.prec)) return FPCG_PATH_TWO_PASS;
+  return fpcg_path(c.n, c.k, c.L, &c.prec);
 }
 
 int path_of(const fpcg_plan* p, const fpcg_plan::Class& c) { return c.path >= 0 ? c.path : default_path(p, c); }
@@ -53,7 +56,7 @@ int ensure_workspace(fpcg_plan* p) {
   if (p->ws) return FPCG_OK;
   int64_t a = 0, b = 0;
   for (auto& c : p->cls) {
-    if (!fpcg::two_pass_capable(c.k, c.L, &p->prec)) continue;
+    if (!fpcg::two_pass_capable(c.k, c.L, &c.prec)) continue;
     c.a0 = a;
     c.b0 = b;
     a += c.count * (int64_t)c.k * c.k;
@@ -79,17 +82,17 @@ int run_class(fpcg_plan* p, const fpcg_plan::Class& c, int path, const void* H, 
   if (path == FPCG_PATH_TWO_PASS) {
     float2* A = p->ws + c.a0;
     float2* bv = p->ws + p->ws_a + c.b0;
-    int rc = fpcg_gram(Hc, yc, sigma2 + c.first, c.n, c.k, c.count, p->prec.gram, A, bv,
+    int rc = fpcg_gram(Hc, yc, sigma2 + c.first, c.n, c.k, c.count, c.prec.gram, A, bv,
                        status ? status + c.first : nullptr, s);
     if (rc) return rc;
     return fpcg::run_uniform(nullptr, nullptr, nullptr, qam ? qam + c.first : nullptr, A, bv, c.k, c.k, c.count,
-                             p->iters, c.L, &p->prec, xc, sym ? sym + c.x0 : nullptr,
+                             p->iters, c.L, &c.prec, xc, sym ? sym + c.x0 : nullptr,
                              rel_res ? rel_res + c.first : nullptr, nullptr, tx ? tx + c.x0 : nullptr, bits,
                              status ? status + c.first : nullptr, s, FPCG_PATH_TENSOR_CORE, false,
                              true);  // keep a Gram-pass FPCG_ST_TIMEOUT
   }
   return fpcg::run_uniform(Hc, yc, sigma2 + c.first, qam ? qam + c.first : nullptr, nullptr, nullptr, c.n, c.k,
-                           c.count, p->iters, c.L, &p->prec, xc, sym ? sym + c.x0 : nullptr,
+                           c.count, p->iters, c.L, &c.prec, xc, sym ? sym + c.x0 : nullptr,
                            rel_res ? rel_res + c.first : nullptr, nullptr, tx ? tx + c.x0 : nullptr, bits,
                            status ? status + c.first : nullptr, s, path, false);
 }
@@ -152,6 +155,7 @@ int fpcg_plan_create(const fpcg_batch_desc* d, fpcg_plan** out) {
         c.n = n;
         c.k = k;
         c.L = d->block_L > 0 ? std::min(d->block_L, k) : 0;
+        c.prec = d->prec;
         c.path = -1;
         c.first = pos;
         c.count = 0;
@@ -205,6 +209,9 @@ int fpcg_plan_classes(const fpcg_plan* p, int32_t* n_classes, fpcg_class_info* i
       info[c].path = path_of(p, k);
       info[c].first = k.first;
       info[c].count = k.count;
+      info[c].mv = k.prec.mv;
+      info[c].reserved = 0;
+      info[c].kappa = k.kappa;
     }
   }
   return FPCG_OK;
@@ -227,8 +234,8 @@ int fpcg_plan_autotune(fpcg_plan* p, const void* H, const void* y, const double*
   for (auto& c : p->cls) {
     if (rc) break;
     int cand[2] = {-1, FPCG_PATH_SIMT};
-    if (fpcg::two_pass_capable(c.k, c.L, &p->prec)) cand[0] = FPCG_PATH_TWO_PASS;
-    else if (fpcg::tc_capable(c.k, c.L, &p->prec) && c.n % 2 == 0) cand[0] = FPCG_PATH_TENSOR_CORE;
+    if (fpcg::two_pass_capable(c.k, c.L, &c.prec)) cand[0] = FPCG_PATH_TWO_PASS;
+    else if (fpcg::tc_capable(c.k, c.L, &c.prec) && c.n % 2 == 0) cand[0] = FPCG_PATH_TENSOR_CORE;
     if (cand[0] < 0) {
       c.path = FPCG_PATH_SIMT;
       continue;
@@ -263,6 +270,81 @@ int fpcg_plan_autotune(fpcg_plan* p, const void* H, const void* y, const double*
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  return rc;
+}
+
+int fpcg_plan_autoprec(fpcg_plan* p, const void* H, const void* y, const double* sigma2, double tol, void* stream) {
+  if (!p || !H || !y || !sigma2 || !(tol > 0.0 && tol < 1.0)) return FPCG_EINVAL;
+  constexpr int64_t kSample = 64;
+  constexpr int kMaxIters = 32;
+  cudaStream_t s = (cudaStream_t)stream;
+  drop_graph(p);
+  if (p->ws) {  // two-pass eligibility may change with the precisions: the workspace is laid out again
+    cudaStreamSynchronize(s);
+    cudaFree(p->ws);
+    p->ws = nullptr;
+  }
+  int kmax = 1;
+  for (const auto& c : p->cls) kmax = std::max(kmax, c.k);
+  float* coeffs = nullptr;
+  float2* xs = nullptr;
+  cudaError_t e = cudaMalloc(&coeffs, sizeof(float) * 2 * kMaxIters * kSample);
+  if (e == cudaSuccess) e = cudaMalloc(&xs, sizeof(float2) * (size_t)kmax * kSample);
+  if (e != cudaSuccess) {
+    cudaFree(coeffs);
+    return e == cudaErrorMemoryAllocation ? FPCG_ENOMEM : fpcg::cuda_error(e);
+  }
+  std::vector<float> host((size_t)2 * kMaxIters * kSample);
+  std::vector<double> kap((size_t)kSample);
+  int rc = FPCG_OK;
+  // the estimate of kappa (FP-CG) or kappa_bar (FP-BJ-CG, block L): median over
+  // the first systems of the class of the Ritz-value estimate from fp32 CG step sizes
+  auto estimate = [&](const fpcg_plan::Class& c, int L, double* out) -> int {
+    const int64_t n = std::min<int64_t>(c.count, kSample);
+    const int m = std::min(c.k, kMaxIters);
+    fpcg_precision pe = p->prec;
+    pe.gram = pe.mv = pe.ip = pe.w = pe.resid = FPCG_FP32;
+    pe.refine_steps = 0;
+    int r = fpcg::run_uniform(static_cast<const float2*>(H) + c.h0, static_cast<const float2*>(y) + c.y0,
+                              sigma2 + c.first, nullptr, nullptr, nullptr, c.n, c.k, n, m, L, &pe, xs, nullptr,
+                              nullptr, nullptr, nullptr, nullptr, nullptr, s, -1, true, false, coeffs);
+    if (r) return r;
+    cudaError_t ce = cudaMemcpyAsync(host.data(), coeffs, sizeof(float) * 2 * m * n, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return fpcg::cuda_error(ce);
+    fpcg_kappa_cg_batch(host.data(), m, m, n, kap.data());
+    std::vector<double> v;
+    for (int64_t i = 0; i < n; ++i)
+      if (kap[(size_t)i] >= 1.0) v.push_back(kap[(size_t)i]);
+    if (v.empty()) {
+      *out = 1.0;
+      return FPCG_OK;
+    }
+    std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+    *out = v[v.size() / 2];
+    return FPCG_OK;
+  };
+  for (auto& c : p->cls) {
+    double kappa = 1.0, kappa_bar = 1.0;
+    rc = estimate(c, 0, &kappa);
+    if (!rc && c.L > 0) rc = estimate(c, c.L, &kappa_bar);
+    if (rc) break;
+    // eq. heuristic / eq. heuristic_bj; the matvec never goes above the fp32 working precision
+    auto pick = [&](double k) {
+      const int f = fpcg_choose_precision(c.k, k, nullptr);
+      return f == FPCG_FP64 || f < 0 ? FPCG_FP32 : f;
+    };
+    const int mv_cg = pick(kappa), mv_bj = pick(kappa_bar);
+    int L = 0;
+    if (c.L > 0) L = fpcg_choose_method(c.k, c.L, kappa, kappa_bar, tol, mv_cg, mv_bj, FPCG_FP32, nullptr, nullptr);
+    if (L < 0) L = c.L;
+    c.L = L;
+    c.prec.mv = L ? mv_bj : mv_cg;
+    c.kappa = L ? kappa_bar : kappa;
+    c.path = -1;
+  }
+  cudaFree(coeffs);
+  cudaFree(xs);
   return rc;
 }
 

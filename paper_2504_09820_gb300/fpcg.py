@@ -67,7 +67,8 @@ class BatchDesc(ctypes.Structure):
 
 class ClassInfo(ctypes.Structure):
     _fields_ = [("n_rx", ctypes.c_int32), ("k", ctypes.c_int32), ("block_L", ctypes.c_int32),
-                ("path", ctypes.c_int32), ("first", ctypes.c_int64), ("count", ctypes.c_int64)]
+                ("path", ctypes.c_int32), ("first", ctypes.c_int64), ("count", ctypes.c_int64),
+                ("mv", ctypes.c_int32), ("reserved", ctypes.c_int32), ("kappa", ctypes.c_double)]
 
 
 PLAN_GRAPH = 1
@@ -129,6 +130,15 @@ def lib():
         L.fpcg_plan_run.restype = ctypes.c_int
         L.fpcg_plan_destroy.argtypes = [_P]
         L.fpcg_plan_destroy.restype = ctypes.c_int
+        L.fpcg_plan_autoprec.argtypes = [_P, _P, _P, _P, ctypes.c_double, _P]
+        L.fpcg_plan_autoprec.restype = ctypes.c_int
+        L.fpcg_detect_coeffs.argtypes = det + [_I32, ctypes.POINTER(Precision)] + [_P, _P, _P, _P, _P, _P, _P, _P]
+        L.fpcg_detect_coeffs.restype = ctypes.c_int
+        L.fpcg_kappa_cg_batch.argtypes = [_P, _I32, _I32, _I64, _P]
+        L.fpcg_kappa_cg_batch.restype = ctypes.c_int
+        L.fpcg_choose_method.argtypes = [_I32, _I32, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I32, _I32,
+                                         _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
+        L.fpcg_choose_method.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -165,6 +175,38 @@ def fpcg_kappa_cg(alpha, beta):
     _check(lib().fpcg_kappa_cg(a.ctypes.data, b.ctypes.data if b.size else None, int(a.size), ctypes.byref(out)),
            "fpcg_kappa_cg")
     return out.value
+
+
+def fpcg_kappa_cg_batch(coeffs, m=None):
+    """kappa estimates of every system from a host [batch][2][iters] float32
+    coefficient array (fpcg_detect_coeffs's layout) using the first m steps."""
+    import numpy as np
+    c = np.ascontiguousarray(coeffs, dtype=np.float32)
+    batch, two, iters = c.shape
+    out = np.empty(batch, dtype=np.float64)
+    _check(lib().fpcg_kappa_cg_batch(c.ctypes.data, int(iters), int(m or iters), int(batch), out.ctypes.data),
+           "fpcg_kappa_cg_batch")
+    return out
+
+
+def fpcg_choose_method(K, L, kappa, kappa_bar, tol, mv_cg="fp16", mv_bj="fp16", w="fp32"):
+    """(block size to use: L or 0 for FP-CG, k_cg, k_pcg): Remark 4's break-even (host only)."""
+    kc, kp = _I32(), _I32()
+    rc = lib().fpcg_choose_method(int(K), int(L), float(kappa), float(kappa_bar), float(tol), FORMAT[mv_cg],
+                                  FORMAT[mv_bj], FORMAT[w], ctypes.byref(kc), ctypes.byref(kp))
+    if rc < 0:
+        raise FpcgError(-rc, "fpcg_choose_method")
+    return rc, kc.value, kp.value
+
+
+def fpcg_detect_coeffs(H, y, sigma2, qam_order, iters, block_L, prec, x_hat, coeffs, sym_idx=None, rel_res=None,
+                       tx_idx=None, bit_errors=None, status=None, stream=None):
+    """Marshal a call to fpcg_detect_coeffs (coeffs: float32 [batch][2][iters] on the device)."""
+    a, b = _detect_args(H, y, sigma2, qam_order, iters, prec, x_hat, sym_idx, rel_res, None,
+                        tx_idx, bit_errors, status)
+    b = [b[0], b[1], b[2], b[3], b[5], b[6], b[7]]   # no res_hist
+    _check(lib().fpcg_detect_coeffs(*a, int(block_L or 0), *b, _ptr(coeffs, torch.float32, "coeffs"),
+                                    _stream(stream)), "fpcg_detect_coeffs")
 
 
 def fpcg_strerror(code):
@@ -399,8 +441,14 @@ class Plan:
         _check(lib().fpcg_plan_classes(self._h, ctypes.byref(n), None), "fpcg_plan_classes")
         info = (ClassInfo * n.value)()
         _check(lib().fpcg_plan_classes(self._h, ctypes.byref(n), info), "fpcg_plan_classes")
-        return [dict(n_rx=c.n_rx, k=c.k, block_L=c.block_L, path=c.path, first=c.first, count=c.count)
-                for c in info]
+        return [dict(n_rx=c.n_rx, k=c.k, block_L=c.block_L, path=c.path, first=c.first, count=c.count,
+                     mv=FORMAT_NAME[c.mv], kappa=c.kappa) for c in info]
+
+    def autoprec(self, H, y, sigma2, tol=1e-3, stream=None):
+        """Per-class matvec format and FP-CG / FP-BJ-CG choice (fpcg_plan_autoprec)."""
+        _check(lib().fpcg_plan_autoprec(self._h, _ptr(H, torch.complex64, "H"), _ptr(y, torch.complex64, "y"),
+                                        _ptr(sigma2, torch.float64, "sigma2"), float(tol), _stream(stream)),
+               "fpcg_plan_autoprec")
 
     def _bufs(self, H, y, sigma2, qam_order, x_hat, sym_idx, rel_res, status):
         return [_ptr(H, torch.complex64, "H"), _ptr(y, torch.complex64, "y"),
