@@ -18,18 +18,31 @@ namespace {
 
 // ---- one system slot in shared memory -----------------------------------------
 struct Slot {
-  uint8_t* A16;     // [2K][K] 16-bit, row r at r*2K bytes, 16-byte chunk c at (c ^ swz(r))
+  uint8_t* A16;     // [2K][K] 16-bit, row r at r*2K bytes, 16-byte chunk c at (c ^ swz(r));
+                    // e4m3 matvec: [K][2K] bytes in the same row geometry (rows 0..K-1)
+  float* sA;        // e4m3 matvec: scale of row k, k-tile kt at k * (K/16) + kt
+  uint8_t* stg;     // e4m3 matvec: the drain's staging of 16-bit pieces, 1 KB per m-tile
   float2* Md;       // diagonal blocks of A (fp32), inverted in place (md_*_stride layout)
   float2* b;        // [K]
   float2* W;        // [K] matvec result, redistributed
   uint32_t* Pk;     // [3K] packed B fragments
 };
 
-__device__ inline Slot slot_carve(uint8_t* base, int K, int L) {
+__device__ inline Slot slot_carve(uint8_t* base, int K, int L, bool f8 = false) {
   Slot s;
   uint8_t* p = base;
   s.A16 = p;
-  p += 4 * K * K;
+  if (f8) {
+    p += 2 * K * K;
+    s.sA = (float*)p;
+    p += sizeof(float) * K * (K / 16);
+    s.stg = p;
+    p += 64 * K;
+  } else {
+    s.sA = nullptr;
+    s.stg = nullptr;
+    p += 4 * K * K;
+  }
   s.Md = (float2*)p;
   p += sizeof(float2) * (L > 0 ? (K / L) * md_block_stride(L) : 2);
   s.b = (float2*)p;
@@ -59,6 +72,14 @@ __device__ __forceinline__ uint32_t a16_offset(int r, int chunk) {
 template <int K>
 __device__ __forceinline__ uint32_t rem_block(int pc, int pr, int mt, int kt) {
   return (uint32_t)((((pc * 2 + pr) * (K / 16) + mt) * (K / 16) + kt) * 512);
+}
+
+// Byte offset of row r (0..31: 16 rows of Re A, then 16 of Im A, of one
+// m-tile) and 16-byte chunk c (columns 8c..8c+7 of one k-tile) in a 1 KB
+// staging block of 16-bit values: the chunk swaps every four rows, so the
+// eight rows of one ldmatrix phase fall on eight different 16-byte bank groups.
+__device__ __forceinline__ uint32_t stg_offset(int r, int c) {
+  return (uint32_t)(r * 32 + ((c ^ ((r >> 2) & 1)) << 4));
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -172,7 +193,15 @@ __device__ __noinline__ float round_ip(float v, int fmt) { return round_to(v, fm
 // matrix (tc_rem_pieces 16-bit pieces, fragment order, at `rem`; skipped while
 // rem is null), so that b - A x is formed against the fp32 Gram to within
 // about 2^-22 of |A||x| (fp16) instead of against A16.
-template <int K, bool BF, int LT, int KR = K, int NV = 1, int NS = 1, int RM = 0>
+//
+// F8 = 1 (with BF, RM = 1, NV = NS = 1): the matvec of a CG iteration runs in
+// e4m3 (mma.sync m16n8k32) on the slot's A8 = A / s_A with one power-of-two
+// scale s_A per row and 16-column block, against p quantised with one scale
+// s_p per 16-entry block (the blocks of 32 interleaved real components of
+// quant_e4m3); each block's fp32 partial sum is scaled by s_A s_p (exact) and
+// accumulated in fp32.  A residual trip forms b - A x from rem_np bf16 pieces
+// in the scratch alone: A_mv (= s_A A8, exact in bf16) or the fp32 Gram.
+template <int K, bool BF, int LT, int KR = K, int NV = 1, int NS = 1, int RM = 0, int F8 = 0>
 struct CgWarp {
   static constexpr int KT = K / 16;          // k-tiles (16 users)
   static constexpr int MT = K / 16;          // m-tiles of Re A (and of Im A)
@@ -180,6 +209,7 @@ struct CgWarp {
   static constexpr int NCOL = 6;             // B columns (re, im) x (hi, mid, lo)
   static_assert(NV == 1 || (NV == 8 && MT <= 8), "cooperative mode: eight warps");
   static_assert(NS == 1 || (NV == 1 && E % NS == 0 && MT % NS == 0), "split mode: rows and m-tiles per warp");
+  static_assert(!F8 || (BF && RM == 1 && NV == 1 && NS == 1), "e4m3 matvec: one warp per slot, bf16 residual pieces");
   const DetectTcParams& P;
   Slot S;
   int lane, g, t;
@@ -190,6 +220,8 @@ struct CgWarp {
   int sj = 0, bar_id = 0;    // NS > 1: this warp's index in its system's group, the group's barrier
   float2* rst = nullptr;     // NS > 1: warp-private staging of r for the preconditioner
   const uint8_t* rem = nullptr;  // RM = 1: this slot's remainder pieces (global scratch)
+  int rem_np = 0;                // F8: pieces of the residual's matrix at rem
+  float sp[KT];                  // F8: scales of the k-tiles of the last packed p
 
   // NS > 1: rows lane + 32e this warp writes (packs, outputs)
   __device__ __forceinline__ bool mine(int e) const { return NS == 1 || e % NS == sj; }
@@ -236,6 +268,12 @@ struct CgWarp {
   // remainders when `split` (three pieces carry all 24 bits of an fp32 value;
   // zeros otherwise).
   __device__ __forceinline__ void pack(const float2 (&v)[E], bool split) {
+    if constexpr (F8) {
+      if (!split) {
+        pack8(v);
+        return;
+      }
+    }
     if constexpr (NS > 1 && NS == E) {  // split mode: only rows lane + 32 sj
       float2 vs = v[0];
 #pragma unroll
@@ -280,6 +318,96 @@ struct CgWarp {
         }
       }
     }
+    __syncwarp();
+  }
+
+  // F8: v as e4m3 B fragments.  k-tile kt holds entries 16kt..16kt+15 (the
+  // real components 32kt..32kt+31 of v, Re and Im interleaved), divided by
+  // their block's scale sp[kt] (e4m3_scale of the block's largest |component|)
+  // and rounded to e4m3.  Column 0 holds (Re v_l, -Im v_l) pairs and column 1
+  // (Im v_l, Re v_l), so that a row of A8 (Re, Im interleaved) times them gives
+  // Re and Im of (A v)_k.  Word ((kt*2 + col)*4 + tt)*2 + h holds rows
+  // 16h + 4tt .. 16h + 4tt + 3 of the k-tile: entries 16kt + 8h + 2tt and + 1.
+  __device__ __forceinline__ void pack8(const float2 (&v)[E]) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      float m = vact() ? fmaxf(fabsf(v[e].x), fabsf(v[e].y)) : 0.f;
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));  // 16-entry block
+      const float s = e4m3_scale(m), inv = __frcp_rn(s);  // powers of two: v * inv is exact
+      sp[2 * e] = __shfl_sync(0xffffffffu, s, 0);  // k-tiles 2e (lanes 0-15), 2e + 1 (lanes 16-31)
+      if (2 * e + 1 < KT) sp[2 * e + 1] = __shfl_sync(0xffffffffu, s, 16);
+      const float qx = v[e].x * inv, qy = v[e].y * inv;
+      const float nx = __shfl_down_sync(0xffffffffu, qx, 1);
+      const float ny = __shfl_down_sync(0xffffffffu, qy, 1);
+      const int rl = lane + 32 * e;
+      if (vact() && (rl & 1) == 0) {
+        const int kt = rl >> 4, j = rl & 15, tt = (j & 7) >> 1, h = j >> 3;
+        uint32_t* w = S.Pk + ((kt * 2) * 4 + tt) * 2 + h;
+        w[0] = tc::cvt_e4m3x4(qx, -qy, nx, -ny);
+        w[8] = tc::cvt_e4m3x4(qy, qx, ny, nx);
+      }
+    }
+    __syncwarp();
+  }
+
+  // F8: W = A8 v with the block scales, one m-tile (16 rows of A8) pair at a
+  // time; every k-tile's mma starts from zero and its fp32 partial sums are
+  // scaled by s_A s_p and added.  Lane (g, t = 0) holds rows g, g + 8 of the
+  // columns Re, Im.
+  __device__ __forceinline__ void apply8(float2 (&w)[E]) {
+    uint32_t b0[KT], b1[KT];
+#pragma unroll
+    for (int kt = 0; kt < KT; ++kt) {
+      b0[kt] = b1[kt] = 0u;
+      if (g < 2) {
+        const uint2 pw = *reinterpret_cast<const uint2*>(S.Pk + ((kt * 2 + g) * 4 + t) * 2);
+        b0[kt] = pw.x;
+        b1[kt] = pw.y;
+      }
+    }
+    const uint32_t abase = tc::smem_u32(S.A16);
+    const int lr = lane & 15, lc = lane >> 4;
+    constexpr int MP = MT >= 2 ? 2 : 1;
+    const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int mt0 = 0; mt0 < MT; mt0 += MP) {
+      float acc[MP][4];
+      float sa[MP][2][KT];
+#pragma unroll
+      for (int j = 0; j < MP; ++j) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int kt = 0; kt < KT; ++kt) sa[j][h][kt] = S.sA[(16 * (mt0 + j) + g + 8 * h) * KT + kt] * sp[kt];
+      }
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) {
+#pragma unroll
+        for (int j = 0; j < MP; ++j) {
+          uint32_t a[4];
+          float c[4];
+          tc::ldmatrix_x4(a, abase + a16_offset<K>(16 * (mt0 + j) + lr, 2 * kt + lc));
+          tc::mma_m16n8k32_e4m3(c, a, b0[kt], b1[kt], zero);
+          acc[j][0] = fmaf(c[0], sa[j][0][kt], acc[j][0]);
+          acc[j][1] = fmaf(c[1], sa[j][0][kt], acc[j][1]);
+          acc[j][2] = fmaf(c[2], sa[j][1][kt], acc[j][2]);
+          acc[j][3] = fmaf(c[3], sa[j][1][kt], acc[j][3]);
+        }
+      }
+      if (t == 0) {
+#pragma unroll
+        for (int j = 0; j < MP; ++j) {
+          S.W[16 * (mt0 + j) + g] = make_float2(acc[j][0], acc[j][1]);
+          S.W[16 * (mt0 + j) + g + 8] = make_float2(acc[j][2], acc[j][3]);
+        }
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; ++e) w[e] = vact() ? S.W[lane + 32 * e] : make_float2(0.f, 0.f);
     __syncwarp();
   }
 
@@ -369,7 +497,7 @@ struct CgWarp {
   // that wrote them.
   __device__ __forceinline__ void rem_apply(const uint8_t* src, const uint32_t (&b0)[KT], const uint32_t (&b1)[KT],
                                             uint4 (&q)[2][KT]) {
-    constexpr int NR = tc_rem_pieces(BF) * MT;
+    const int NR = (F8 ? rem_np : tc_rem_pieces(BF)) * MT;
 #pragma unroll 1
     for (int i = 0; i < NR; ++i) {
       float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
@@ -406,6 +534,12 @@ struct CgWarp {
       apply_cta(res, w);
       return;
     }
+    if constexpr (F8) {
+      if (!res) {
+        apply8(w);
+        return;
+      }
+    }
     gsync();  // NS > 1: every warp's rows are packed
     uint32_t b0[KT], b1[KT];
 #pragma unroll
@@ -417,7 +551,15 @@ struct CgWarp {
         b1[kt] = pw.y;
       }
     }
-    if constexpr (NS > 1) {  // this warp's m-tiles interleaved along k
+    if constexpr (F8) {  // residual: W = b, then W -= (each piece) x
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (vact()) S.W[lane + 32 * e] = S.b[lane + 32 * e];
+      uint4 q[2][KT];
+      rem_load(rem, 0, q);
+      __syncwarp();
+      rem_apply(rem, b0, b1, q);
+    } else if constexpr (NS > 1) {  // this warp's m-tiles interleaved along k
       apply_mtiles<MT / NS>(sj * (MT / NS), res, b0, b1);
     } else {  // m-tiles in pairs: more independent chains, a rolled loop keeps the code small
       constexpr int MP = MT >= 2 ? 2 : 1;

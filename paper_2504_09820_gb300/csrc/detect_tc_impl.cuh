@@ -76,13 +76,18 @@ __device__ int g_rem_busy[kTcScratchRegions];
 
 template <int K>
 __device__ __forceinline__ uint8_t* rem_slot(int region, int slot) {
-  return g_rem<K> + (size_t)region * tc_rem_region_bytes(K) + (size_t)slot * 2 * tc_rem_piece_bytes(K);
+  return g_rem<K> + (size_t)region * tc_rem_region_bytes(K) + (size_t)slot * kTcRemMaxPieces * tc_rem_piece_bytes(K);
 }
 
 // Drain warpgroup: tile j of this CTA (TMEM buffer j & 1) holds systems
 // seq = j*P + p, p < P, which go to slots seq % nslots.  Thread = TMEM lane =
 // row 2k + odd of its system's block.
-template <int K, bool BF, int LT, int RG>
+// F8: each 16-column block of row k (Re from thread 2k, Im from 2k + 1) is
+// quantised with its own scale (e4m3_scale of the block's largest |component|)
+// into 32 interleaved bytes of A8, and the residual's matrix goes to the
+// scratch as rem_pieces bf16 pieces: A_mv = s_A A8 (exact in bf16) or the fp32
+// Gram (hi, mid, lo).
+template <int K, bool BF, int LT, int RG, int F8>
 __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem, int64_t tile0, int64_t tstep) {
   const tcp::Pipe& pp = P.pipe;
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -94,7 +99,8 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
   const int ps = row / twoK, k = (row % twoK) >> 1, odd = row & 1;
   const int blk0 = ps * twoK;
   const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
-  const size_t slot_bytes = tc_slot_bytes(K, LT);
+  const size_t slot_bytes = tc_slot_bytes(K, LT, F8);
+  const int npieces = F8 ? P.rem_pieces : tc_rem_pieces(BF);
   const uint64_t keep = tc::policy_evict_last();  // remainder pieces: read back by the CG warps
   int64_t j = 0;
   for (int64_t tile = tile0; tile < pp.ntiles; tile += tstep, ++j) {
@@ -115,7 +121,7 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
     tc::tc_fence_after();
     const uint32_t tb = lane_base + b * (uint32_t)tcp::kAccCols;
     const int slot = (int)((j * PP + ps) % ns);
-    Slot sl = slot_carve(S.slots + slot * slot_bytes, K, LT);
+    Slot sl = slot_carve(S.slots + slot * slot_bytes, K, LT, F8);
     uint8_t* rem = (RG && *S.region >= 0) ? rem_slot<K>(*S.region, slot) : nullptr;
     const int arow = odd ? K + k : k;           // row of [Re A; Im A]
     const int kb0 = (k / (LT > 0 ? LT : 1)) * LT;  // first column of k's diagonal block
@@ -139,19 +145,60 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
           a[u][m] = val;
         }
       }
-      if (RG && rem) {
-        // A - A16 in 16-bit pieces, in mma A-fragment order (rem_block): the warp
-        // owns one m-tile (16 rows of Re A and of Im A); each piece of this
-        // k-tile goes row-major through the slot's A16 area (rewritten below)
-        // and comes back by ldmatrix as fragments, one 16-byte store per lane.
-        const int kt = (cg - blk0) >> 5, mt = (k & (K - 1)) >> 4;
-        float lo[2][8];
+      const int kt = (cg - blk0) >> 5, mt = (k & (K - 1)) >> 4;
+      float lo[2][8];  // the first piece for the scratch
+      if constexpr (F8) {
+        float m = 0.f;
 #pragma unroll
         for (int u = 0; u < 2; ++u)
 #pragma unroll
-          for (int m = 0; m < 8; ++m) lo[u][m] = a[u][m] - round16<BF>(a[u][m]);  // exact
+          for (int mm = 0; mm < 8; ++mm) m = fmaxf(m, fabsf(a[u][mm]));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));  // Re and Im of the block
+        const float sc = e4m3_scale(m), inv = __frcp_rn(sc);  // powers of two
+        uint32_t wq[4];  // e4m3 bytes of columns 4i .. 4i + 3 of this thread's part
 #pragma unroll
-        for (int pc = 0; pc < tc_rem_pieces(BF); ++pc) {
+        for (int i = 0; i < 4; ++i) {
+          const float* src = &a[i >> 1][4 * (i & 1)];
+          wq[i] = tc::cvt_e4m3x4(src[0] * inv, src[1] * inv, src[2] * inv, src[3] * inv);
+          if (npieces == 1) {  // A_mv = sc * e4m3 value, exact in bf16
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(wq[i] >> (16 * h)), __NV_E4M3);
+              const float2 f = __half22float2(__half2(hr));
+              lo[i >> 1][4 * (i & 1) + 2 * h] = f.x * sc;
+              lo[i >> 1][4 * (i & 1) + 2 * h + 1] = f.y * sc;
+            }
+          } else {
+#pragma unroll
+            for (int h = 0; h < 4; ++h) lo[i >> 1][4 * (i & 1) + h] = src[h];
+          }
+        }
+        // thread 2k (Re) writes columns 0-7 of the block, thread 2k + 1 (Im) columns 8-15
+        const uint32_t s0 = __shfl_xor_sync(0xffffffffu, odd ? wq[0] : wq[2], 1);
+        const uint32_t s1 = __shfl_xor_sync(0xffffffffu, odd ? wq[1] : wq[3], 1);
+        const uint32_t re0 = odd ? s0 : wq[0], re1 = odd ? s1 : wq[1];
+        const uint32_t im0 = odd ? wq[2] : s0, im1 = odd ? wq[3] : s1;
+        *reinterpret_cast<uint4*>(sl.A16 + a16_offset<K>(k, 2 * kt + odd)) =
+            make_uint4(__byte_perm(re0, im0, 0x5140), __byte_perm(re0, im0, 0x7362), __byte_perm(re1, im1, 0x5140),
+                       __byte_perm(re1, im1, 0x7362));
+        if (!odd) sl.sA[k * (K / 16) + kt] = sc;
+      } else if (RG) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int mm = 0; mm < 8; ++mm) lo[u][mm] = a[u][mm] - round16<BF>(a[u][mm]);  // exact
+      }
+      if (RG && rem) {
+        // The scratch pieces in mma A-fragment order (rem_block): the warp owns
+        // one m-tile (16 rows of Re A and of Im A); each piece of this k-tile
+        // goes row-major through shared memory (the slot's A16 area, rewritten
+        // below, or the e4m3 slot's staging block) and comes back by ldmatrix
+        // as fragments, one 16-byte store per lane.
+        const uint32_t abase = tc::smem_u32(F8 ? sl.stg + mt * 1024 : sl.A16);
+        const int lr = lane & 15, lc = lane >> 4;
+        const int srow = odd * 16 + (k & 15);
+#pragma unroll 1
+        for (int pc = 0; pc < npieces; ++pc) {
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             uint4 q;
@@ -159,17 +206,17 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
             q.y = pk2<BF>(lo[u][2], lo[u][3]);
             q.z = pk2<BF>(lo[u][4], lo[u][5]);
             q.w = pk2<BF>(lo[u][6], lo[u][7]);
-            *reinterpret_cast<uint4*>(sl.A16 + a16_offset<K>(arow, 2 * kt + u)) = q;
+            if (F8) *reinterpret_cast<uint4*>(sl.stg + mt * 1024 + stg_offset(srow, u)) = q;
+            else *reinterpret_cast<uint4*>(sl.A16 + a16_offset<K>(arow, 2 * kt + u)) = q;
 #pragma unroll
-            for (int m = 0; m < 8; ++m) lo[u][m] -= round16<BF>(lo[u][m]);  // exact
+            for (int mm = 0; mm < 8; ++mm) lo[u][mm] -= round16<BF>(lo[u][mm]);  // exact
           }
           __syncwarp();
-          const uint32_t abase = tc::smem_u32(sl.A16);
-          const int lr = lane & 15, lc = lane >> 4;
 #pragma unroll
           for (int pr = 0; pr < 2; ++pr) {
             uint32_t f[4];
-            tc::ldmatrix_x4(f, abase + a16_offset<K>(pr * K + 16 * mt + lr, 2 * kt + lc));
+            tc::ldmatrix_x4(f, abase + (F8 ? stg_offset(pr * 16 + lr, lc)
+                                           : a16_offset<K>(pr * K + 16 * mt + lr, 2 * kt + lc)));
             tc::st_global_hint(rem + rem_block<K>(pc, pr, mt, kt) + 16 * lane, make_uint4(f[0], f[1], f[2], f[3]),
                                keep);
           }
@@ -179,13 +226,14 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int l0 = (cg + 16 * u - blk0) >> 1;
-        // 8 columns -> one 16-byte chunk of row arow
-        uint4 pkd;
-        pkd.x = pk2<BF>(a[u][0], a[u][1]);
-        pkd.y = pk2<BF>(a[u][2], a[u][3]);
-        pkd.z = pk2<BF>(a[u][4], a[u][5]);
-        pkd.w = pk2<BF>(a[u][6], a[u][7]);
-        *reinterpret_cast<uint4*>(sl.A16 + a16_offset<K>(arow, l0 >> 3)) = pkd;
+        if constexpr (!F8) {  // 8 columns -> one 16-byte chunk of row arow
+          uint4 pkd;
+          pkd.x = pk2<BF>(a[u][0], a[u][1]);
+          pkd.y = pk2<BF>(a[u][2], a[u][3]);
+          pkd.z = pk2<BF>(a[u][4], a[u][5]);
+          pkd.w = pk2<BF>(a[u][6], a[u][7]);
+          *reinterpret_cast<uint4*>(sl.A16 + a16_offset<K>(arow, l0 >> 3)) = pkd;
+        }
         if constexpr (LT > 0) {
 #pragma unroll
           for (int m = 0; m < 8; ++m) {
@@ -213,16 +261,17 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
 }
 
 // CG warp c: every system whose slot is c, in order.
-template <int K, bool BF, int LT, int RG>
+template <int K, bool BF, int LT, int RG, int F8>
 __device__ void cg_role(const DetectTcParams& P, const Smem& S, int c, int64_t tile0, int64_t tstep) {
   const tcp::Pipe& pp = P.pipe;
   const int lane = threadIdx.x & 31;
   constexpr int PP = 64 / K;
   const int ns = P.nslots;
   const int64_t nloc = tile0 < pp.ntiles ? (pp.ntiles - tile0 + tstep - 1) / tstep : 0;
-  CgWarp<K, BF, LT, K, 1, 1, RG> W(P, slot_carve(S.slots + c * tc_slot_bytes(K, LT), K, LT), lane);
+  CgWarp<K, BF, LT, K, 1, 1, RG, F8> W(P, slot_carve(S.slots + c * tc_slot_bytes(K, LT, F8), K, LT, F8), lane);
   if constexpr (RG == 1)
     if (*S.region >= 0) W.rem = rem_slot<K>(*S.region, c);
+  W.rem_np = P.rem_pieces;
   int64_t seq = c;
   for (; seq / PP < nloc; seq += ns) {
     const uint32_t use = (uint32_t)(seq / ns);
@@ -246,8 +295,9 @@ __device__ void cg_role(const DetectTcParams& P, const Smem& S, int c, int64_t t
 
 // RG = 1: residuals against the fp32 Gram matrix (resid_gram), with the
 // remainder pieces in a scratch region; RG = 0: against A16 alone (none of
-// that code is compiled in).
-template <int K, bool BF, int LT, int RG>
+// that code is compiled in).  F8 = 1 (with BF = RG = 1): the e4m3 matvec, and
+// the residual's matrix all in the scratch (rem_pieces bf16 pieces).
+template <int K, bool BF, int LT, int RG, int F8>
 __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_constant__ DetectTcParams P) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   Smem S;
@@ -307,9 +357,9 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
   } else if (warp >= kConv0) {
     tcp::converter_role<kConv, kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, warp - kConv0, lane);
   } else if (warp >= kCg0) {
-    if (warp - kCg0 < P.nslots) cg_role<K, BF, LT, RG>(P, S, warp - kCg0, tile0, tstep);
+    if (warp - kCg0 < P.nslots) cg_role<K, BF, LT, RG, F8>(P, S, warp - kCg0, tile0, tstep);
   } else {
-    drain_role<K, BF, LT, RG>(P, S, tmem, tile0, tstep);
+    drain_role<K, BF, LT, RG, F8>(P, S, tmem, tile0, tstep);
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -323,24 +373,38 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
   }
 }
 
-template <int K, bool BF, int LT, int RG>
+template <int K, bool BF, int LT, int RG, int F8 = 0>
 cudaError_t launch_k(DetectTcParams P, int num_sms, cudaStream_t stream) {
-  const size_t smem = detect_tc_smem_bytes(K, P.L);
-  P.nslots = tc_num_slots(K, P.L);
+  const size_t smem = detect_tc_smem_bytes(K, P.L, F8);
+  P.nslots = tc_num_slots(K, P.L, F8);
   P.pipe.s32b = tc_stage32_bytes(K);
-  cudaError_t e =
-      cudaFuncSetAttribute(detect_tc_kernel<K, BF, LT, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!F8) P.rem_pieces = tc_rem_pieces(BF);
+  if (F8 && P.rem_pieces != 1 && P.rem_pieces != 3) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(detect_tc_kernel<K, BF, LT, RG, F8>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t grid = P.pipe.ntiles < num_sms ? P.pipe.ntiles : num_sms;
   if (grid <= 0) return cudaSuccess;
-  detect_tc_kernel<K, BF, LT, RG><<<(unsigned)grid, kThreads, smem, stream>>>(P);
+  detect_tc_kernel<K, BF, LT, RG, F8><<<(unsigned)grid, kThreads, smem, stream>>>(P);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 template <int K>
-cudaError_t launch_detect_tc_k(const DetectTcParams& P, int num_sms, int mv_bf16, cudaStream_t stream) {
+cudaError_t launch_detect_tc_k(const DetectTcParams& P, int num_sms, int mv, cudaStream_t stream) {
+  if (mv == E4M3) {  // residual pieces: the fp32 Gram (3) or A_mv (1)
+    DetectTcParams Q = P;
+    Q.rem_pieces = P.resid_gram ? 3 : 1;
+    switch (P.L) {
+      case 0: return launch_k<K, true, 0, 1, 1>(Q, num_sms, stream);
+      case 4: return launch_k<K, true, 4, 1, 1>(Q, num_sms, stream);
+      case 8: return launch_k<K, true, 8, 1, 1>(Q, num_sms, stream);
+      case 16: return launch_k<K, true, 16, 1, 1>(Q, num_sms, stream);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  const int mv_bf16 = mv == BF16;
   switch ((P.L * 2 + (mv_bf16 ? 1 : 0)) * 2 + (P.resid_gram ? 1 : 0)) {
     case 0: return launch_k<K, false, 0, 0>(P, num_sms, stream);
     case 1: return launch_k<K, false, 0, 1>(P, num_sms, stream);

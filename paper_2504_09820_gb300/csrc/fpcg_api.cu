@@ -152,12 +152,13 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
     rc = device_sms(&sms_tc);
     if (rc) return rc;
   }
-  // the Gram residual's scratch pool has one region per SM (kTcScratchRegions of them)
-  const bool scratch_ok = prec->resid != FPCG_FP64 || sms_tc <= fpcg::kTcScratchRegions;
+  // the Gram residual's (and the e4m3 matvec's) scratch pool has one region per SM
+  const bool f8 = prec->mv == FPCG_FP8E4M3;
+  const bool scratch_ok = (prec->resid != FPCG_FP64 && !f8) || sms_tc <= fpcg::kTcScratchRegions;
   if (path == FPCG_PATH_TENSOR_CORE && tc_ok && !Ain && !scratch_ok) return FPCG_ENOTSUP;
   if (tc_ok && scratch_ok) {
     const int sms = sms_tc;
-    rc = check_device_smem(fpcg::detect_tc_smem_bytes(k, block_L));
+    rc = check_device_smem(fpcg::detect_tc_smem_bytes(k, block_L, f8));
     if (rc) return rc;
     fpcg::DetectTcParams T;
     memset(&T, 0, sizeof(T));
@@ -167,7 +168,7 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
     cg_params(T, qam_order, iters, block_L, prec, refine_iters, x_hat, sym_idx, rel_res, res_hist, tx_idx,
               bit_errors, status);
     T.resid_gram = prec->resid == FPCG_FP64;
-    cudaError_t e = fpcg::launch_detect_tc(T, sms, prec->mv == FPCG_BF16, s);
+    cudaError_t e = fpcg::launch_detect_tc(T, sms, prec->mv, s);
     return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
   }
   rc = check_device_smem(fpcg::simt_smem_bytes(fp64, k, block_L, prec->mv));
@@ -226,7 +227,8 @@ bool two_pass_capable(int k, int block_L, const fpcg_precision* prec) {
 
 bool tc_capable(int k, int block_L, const fpcg_precision* prec) {
   return prec->w == FPCG_FP32 && (prec->gram == FPCG_BF16 || prec->gram == FPCG_FP16) &&
-         (prec->mv == FPCG_BF16 || prec->mv == FPCG_FP16) && fpcg::detect_tc_supported(k, block_L);
+         (prec->mv == FPCG_BF16 || prec->mv == FPCG_FP16 || (prec->mv == FPCG_FP8E4M3 && prec->fp8_block == 32)) &&
+         fpcg::detect_tc_supported(k, block_L);
 }
 
 }  // namespace fpcg

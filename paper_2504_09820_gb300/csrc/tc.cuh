@@ -303,5 +303,34 @@ __device__ __forceinline__ void mma_m16n8k16_f16(float (&d)[4], const uint32_t (
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// D(16x8, f32) = A(16x32, e4m3 row) * B(32x8, e4m3 col) + C.  Lane (g, t) =
+// (lane / 4, lane % 4) holds A bytes (row g, cols 4t..4t+3), (g+8, 4t..),
+// (g, 16+4t..), (g+8, 16+4t..) in a[0..3], B bytes (rows 4t..4t+3, col g) and
+// (rows 16+4t.., col g) in b0, b1, and D (g, 2t), (g, 2t+1), (g+8, 2t),
+// (g+8, 2t+1).  The byte geometry of A is that of an m16n8k16 16-bit A
+// fragment, so ldmatrix_x4 loads it the same way.
+__device__ __forceinline__ void mma_m16n8k32_e4m3(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1,
+                                                  const float (&c)[4]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%10,%11,%12,%13};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]), "f"(c[2]),
+        "f"(c[3]));
+}
+
+// Two fp32 values to e4m3 (round to nearest even, saturating to +-448), lo in
+// byte 0 and hi in byte 1 of the result.
+__device__ __forceinline__ uint32_t cvt_e4m3x2(float lo, float hi) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// Four fp32 values to four e4m3 bytes (v0 in byte 0).
+__device__ __forceinline__ uint32_t cvt_e4m3x4(float v0, float v1, float v2, float v3) {
+  return cvt_e4m3x2(v0, v1) | (cvt_e4m3x2(v2, v3) << 16);
+}
+
 }  // namespace tc
 }  // namespace fpcg

@@ -81,7 +81,8 @@ def test_routing_to_simt():
     assert F.fpcg_path(64, 8, 4, F.precision(**bf)) == F.PATH_SIMT           # K < 16
     assert F.fpcg_path(256, 64, 8, F.precision(**bf, resid="fp64")) == F.PATH_TENSOR_CORE  # Gram residual
     assert F.fpcg_path(256, 64, 8, F.precision(gram="fp32", mv="bf16")) == F.PATH_SIMT  # fp32 Gram
-    assert F.fpcg_path(256, 64, 8, F.precision(gram="bf16", mv="e4m3")) == F.PATH_SIMT
+    assert F.fpcg_path(256, 64, 8, F.precision(gram="bf16", mv="e4m3")) == F.PATH_TENSOR_CORE  # e4m3 A p
+    assert F.fpcg_path(256, 128, 8, F.precision(gram="bf16", mv="e4m3")) == F.PATH_SIMT
     assert F.fpcg_path(255, 64, 8, F.precision(**bf)) == F.PATH_SIMT          # odd N (no TMA)
     assert F.fpcg_path(256, 64, 8, F.precision(**bf)) == F.PATH_TENSOR_CORE
 
