@@ -21,11 +21,12 @@ struct Slot {
   uint8_t* A16;     // [2K][K] 16-bit, row r at r*2K bytes, 16-byte chunk c at (c ^ swz(r));
                     // e4m3 matvec: [K][2K] bytes in the same row geometry (rows 0..K-1)
   float* sA;        // e4m3 matvec: scale of row k, k-tile kt at k * (K/16) + kt
-  uint8_t* stg;     // e4m3 matvec: the drain's staging of 16-bit pieces, 1 KB per m-tile
   float2* Md;       // diagonal blocks of A (fp32), inverted in place (md_*_stride layout)
   float2* b;        // [K]
   float2* W;        // [K] matvec result, redistributed
   uint32_t* Pk;     // [3K] packed B fragments
+  uint32_t* Pk8;    // e4m3 matvec: [6K] B fragments of x in six e4m3 pieces
+  float* sv;        // e4m3 matvec: [K/16] block scales of the vector last packed
 };
 
 __device__ inline Slot slot_carve(uint8_t* base, int K, int L, bool f8 = false) {
@@ -36,11 +37,8 @@ __device__ inline Slot slot_carve(uint8_t* base, int K, int L, bool f8 = false) 
     p += 2 * K * K;
     s.sA = (float*)p;
     p += sizeof(float) * K * (K / 16);
-    s.stg = p;
-    p += 64 * K;
   } else {
     s.sA = nullptr;
-    s.stg = nullptr;
     p += 4 * K * K;
   }
   s.Md = (float2*)p;
@@ -50,6 +48,8 @@ __device__ inline Slot slot_carve(uint8_t* base, int K, int L, bool f8 = false) 
   s.W = (float2*)p;
   p += sizeof(float2) * K;
   s.Pk = (uint32_t*)p;
+  s.Pk8 = f8 ? s.Pk + 3 * K : nullptr;
+  s.sv = f8 ? reinterpret_cast<float*>(s.Pk + 9 * K) : nullptr;
   return s;
 }
 
@@ -194,13 +194,14 @@ __device__ __noinline__ float round_ip(float v, int fmt) { return round_to(v, fm
 // rem is null), so that b - A x is formed against the fp32 Gram to within
 // about 2^-22 of |A||x| (fp16) instead of against A16.
 //
-// F8 = 1 (with BF, RM = 1, NV = NS = 1): the matvec of a CG iteration runs in
-// e4m3 (mma.sync m16n8k32) on the slot's A8 = A / s_A with one power-of-two
-// scale s_A per row and 16-column block, against p quantised with one scale
-// s_p per 16-entry block (the blocks of 32 interleaved real components of
+// F8 = 1 (with BF, NV = NS = 1): the matvec of a CG iteration runs in e4m3
+// (mma.sync m16n8k32) on the slot's A8 = A / s_A with one power-of-two scale
+// s_A per row and 16-column block, against p quantised with one scale s_p per
+// 16-entry block (the blocks of 32 interleaved real components of
 // quant_e4m3); each block's fp32 partial sum is scaled by s_A s_p (exact) and
-// accumulated in fp32.  A residual trip forms b - A x from rem_np bf16 pieces
-// in the scratch alone: A_mv (= s_A A8, exact in bf16) or the fp32 Gram.
+// accumulated in fp32.  A residual trip forms b - A_mv x on the same A8 with x
+// in six e4m3 pieces (pack8x), and with RM = 1 subtracts (A - A_mv) x from
+// the two bf16 remainder pieces in the scratch.
 template <int K, bool BF, int LT, int KR = K, int NV = 1, int NS = 1, int RM = 0, int F8 = 0>
 struct CgWarp {
   static constexpr int KT = K / 16;          // k-tiles (16 users)
@@ -209,7 +210,7 @@ struct CgWarp {
   static constexpr int NCOL = 6;             // B columns (re, im) x (hi, mid, lo)
   static_assert(NV == 1 || (NV == 8 && MT <= 8), "cooperative mode: eight warps");
   static_assert(NS == 1 || (NV == 1 && E % NS == 0 && MT % NS == 0), "split mode: rows and m-tiles per warp");
-  static_assert(!F8 || (BF && RM == 1 && NV == 1 && NS == 1), "e4m3 matvec: one warp per slot, bf16 residual pieces");
+  static_assert(!F8 || (BF && NV == 1 && NS == 1), "e4m3 matvec: one warp per slot, bf16 remainder pieces");
   const DetectTcParams& P;
   Slot S;
   int lane, g, t;
@@ -220,8 +221,6 @@ struct CgWarp {
   int sj = 0, bar_id = 0;    // NS > 1: this warp's index in its system's group, the group's barrier
   float2* rst = nullptr;     // NS > 1: warp-private staging of r for the preconditioner
   const uint8_t* rem = nullptr;  // RM = 1: this slot's remainder pieces (global scratch)
-  int rem_np = 0;                // F8: pieces of the residual's matrix at rem
-  float sp[KT];                  // F8: scales of the k-tiles of the last packed p
 
   // NS > 1: rows lane + 32e this warp writes (packs, outputs)
   __device__ __forceinline__ bool mine(int e) const { return NS == 1 || e % NS == sj; }
@@ -273,6 +272,8 @@ struct CgWarp {
         pack8(v);
         return;
       }
+      pack8x(v);
+      if constexpr (RM == 0) return;  // the bf16 split feeds the remainder pieces only
     }
     if constexpr (NS > 1 && NS == E) {  // split mode: only rows lane + 32 sj
       float2 vs = v[0];
@@ -328,24 +329,68 @@ struct CgWarp {
   // (Im v_l, Re v_l), so that a row of A8 (Re, Im interleaved) times them gives
   // Re and Im of (A v)_k.  Word ((kt*2 + col)*4 + tt)*2 + h holds rows
   // 16h + 4tt .. 16h + 4tt + 3 of the k-tile: entries 16kt + 8h + 2tt and + 1.
+  // The scales go to S.sv.
   __device__ __forceinline__ void pack8(const float2 (&v)[E]) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      float m = vact() ? fmaxf(fabsf(v[e].x), fabsf(v[e].y)) : 0.f;
+      float inv;
+      const float s = block_scale(v[e], inv);
+      if ((lane & 15) == 0 && 2 * e + (lane >> 4) < KT) S.sv[2 * e + (lane >> 4)] = s;  // k-tile 2e + lane / 16
+      put8(S.Pk, lane + 32 * e, 0, e4m3_pairs(tc::cvt_e4m3x2(v[e].x * inv, v[e].y * inv)));
+    }
+    __syncwarp();
+  }
+
+  // The e4m3 scale of the 16-entry block (16 lanes) holding this lane's entry v.
+  __device__ __forceinline__ float block_scale(float2 v, float& inv) const {
+    float m = vact() ? fmaxf(fabsf(v.x), fabsf(v.y)) : 0.f;
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));  // 16-entry block
-      const float s = e4m3_scale(m), inv = __frcp_rn(s);  // powers of two: v * inv is exact
-      sp[2 * e] = __shfl_sync(0xffffffffu, s, 0);  // k-tiles 2e (lanes 0-15), 2e + 1 (lanes 16-31)
-      if (2 * e + 1 < KT) sp[2 * e + 1] = __shfl_sync(0xffffffffu, s, 16);
-      const float qx = v[e].x * inv, qy = v[e].y * inv;
-      const float nx = __shfl_down_sync(0xffffffffu, qx, 1);
-      const float ny = __shfl_down_sync(0xffffffffu, qy, 1);
-      const int rl = lane + 32 * e;
-      if (vact() && (rl & 1) == 0) {
-        const int kt = rl >> 4, j = rl & 15, tt = (j & 7) >> 1, h = j >> 3;
-        uint32_t* w = S.Pk + ((kt * 2) * 4 + tt) * 2 + h;
-        w[0] = tc::cvt_e4m3x4(qx, -qy, nx, -ny);
-        w[8] = tc::cvt_e4m3x4(qy, qx, ny, nx);
+    for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return e4m3_scale_inv(m, inv);
+  }
+
+  // The two B-column byte pairs of one entry from its e4m3 bytes (Re in byte
+  // 0, Im in byte 1): (Re, -Im) in the low half, (Im, Re) in the high half.
+  __device__ __forceinline__ static uint32_t e4m3_pairs(uint32_t q) {
+    const uint32_t c0 = (q & 0xffu) | ((q ^ 0x8000u) & 0xff00u);
+    const uint32_t c1 = ((q >> 8) & 0xffu) | ((q & 0xffu) << 8);
+    return c0 | (c1 << 16);
+  }
+
+  // Row rl's pairs (and row rl + 1's, from the next lane) into the words of
+  // piece pc: word ((((kt * NP + pc) * 2 + col) * 4 + tt) * 2 + h, NP the
+  // pieces of the array (1 for p, 6 for x).
+  template <int NP = 1>
+  __device__ __forceinline__ void put8(uint32_t* base, int rl, int pc, uint32_t mine) {
+    const uint32_t nb = __shfl_down_sync(0xffffffffu, mine, 1);
+    if (vact() && (rl & 1) == 0) {
+      const int kt = rl >> 4, j = rl & 15, tt = (j & 7) >> 1, h = j >> 3;
+      uint32_t* w = base + ((((kt * NP + pc) * 2) * 4 + tt) * 2 + h);
+      w[0] = (mine & 0xffffu) | (nb << 16);
+      w[8] = (mine >> 16) | (nb & 0xffff0000u);
+    }
+  }
+
+  // F8 residual: x = s0 sum_i 2^(-4i) q_i, q_i in e4m3, six pieces per entry:
+  // s0 = sp[kt] is the e4m3 scale of the block, and piece i + 1 quantises the
+  // exact remainder of piece i in units 16 times smaller.  The remainder of an
+  // e4m3 rounding is at most 2^-4 of the value (subnormals: 2^-10), so no
+  // piece saturates, and what is left after six is below 2^-24 of the block's
+  // largest entry.  Pieces go to S.Pk8 (put8 with NP = 6), s0 to S.sv.
+  __device__ __forceinline__ void pack8x(const float2 (&v)[E]) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      float inv;
+      const float s = block_scale(v[e], inv);
+      if ((lane & 15) == 0 && 2 * e + (lane >> 4) < KT) S.sv[2 * e + (lane >> 4)] = s;
+      float rx = v[e].x * inv, ry = v[e].y * inv;  // exact: inv is a power of two
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const uint32_t q = tc::cvt_e4m3x2(rx, ry);
+        const float2 dq = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)q, __NV_E4M3)));
+        rx = (rx - dq.x) * 16.f;  // exact
+        ry = (ry - dq.y) * 16.f;
+        put8<6>(S.Pk8, lane + 32 * e, i, e4m3_pairs(q));
       }
     }
     __syncwarp();
@@ -381,7 +426,7 @@ struct CgWarp {
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int kt = 0; kt < KT; ++kt) sa[j][h][kt] = S.sA[(16 * (mt0 + j) + g + 8 * h) * KT + kt] * sp[kt];
+          for (int kt = 0; kt < KT; ++kt) sa[j][h][kt] = S.sA[(16 * (mt0 + j) + g + 8 * h) * KT + kt] * S.sv[kt];
       }
 #pragma unroll
       for (int kt = 0; kt < KT; ++kt) {
@@ -405,6 +450,90 @@ struct CgWarp {
         }
       }
     }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; ++e) w[e] = vact() ? S.W[lane + 32 * e] : make_float2(0.f, 0.f);
+    __syncwarp();
+  }
+
+  // F8 residual: S.W = b - A_mv x on A8, x from its six pieces in S.Pk8.
+  // n-tile 0 holds pieces 0-3 and n-tile 1 pieces 4, 5 (column 2i + c: piece
+  // i, column c of pack8), so lane (g, t) accumulates pieces t and 4 + t, each
+  // in its own units; they are scaled by 2^(-4 piece) and summed over the
+  // quad, smallest first.
+  __device__ __forceinline__ void res8() {
+    const uint32_t abase = tc::smem_u32(S.A16);
+    const int lr = lane & 15, lc = lane >> 4;
+    const float f0 = __uint_as_float((uint32_t)(127 - 4 * t) << 23);       // 2^(-4t)
+    const float f1 = __uint_as_float((uint32_t)(127 - 16 - 4 * t) << 23);  // 2^(-4(4 + t))
+    const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int mt = 0; mt < MT; ++mt) {
+      float acc[2][4], sa[2][KT];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[0][q] = acc[1][q] = 0.f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt) sa[h][kt] = S.sA[(16 * mt + g + 8 * h) * KT + kt] * S.sv[kt];
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) {
+        uint32_t a[4];
+        tc::ldmatrix_x4(a, abase + a16_offset<K>(16 * mt + lr, 2 * kt + lc));
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int pc = 4 * nt + (g >> 1);  // pieces 6, 7: zero columns
+          const uint2 pw = pc < 6 ? *reinterpret_cast<const uint2*>(
+                                        S.Pk8 + ((((kt * 6 + pc) * 2 + (g & 1)) * 4 + t) * 2))
+                                  : make_uint2(0u, 0u);
+          float c[4];
+          tc::mma_m16n8k32_e4m3(c, a, pw.x, pw.y, zero);
+          acc[nt][0] = fmaf(c[0], sa[0][kt], acc[nt][0]);
+          acc[nt][1] = fmaf(c[1], sa[0][kt], acc[nt][1]);
+          acc[nt][2] = fmaf(c[2], sa[1][kt], acc[nt][2]);
+          acc[nt][3] = fmaf(c[3], sa[1][kt], acc[nt][3]);
+        }
+      }
+      float v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v[q] = fmaf(acc[0][q], f0, acc[1][q] * f1);
+        v[q] += __shfl_xor_sync(0xffffffffu, v[q], 2);
+        v[q] += __shfl_xor_sync(0xffffffffu, v[q], 1);
+      }
+      if (t == 0) {
+        const float2 bb0 = S.b[16 * mt + g], bb8 = S.b[16 * mt + g + 8];
+        S.W[16 * mt + g] = make_float2(bb0.x - v[0], bb0.y - v[1]);
+        S.W[16 * mt + g + 8] = make_float2(bb8.x - v[2], bb8.y - v[3]);
+      }
+    }
+  }
+
+  // F8: a CG iteration's A p (apply8) or a residual (res8, then the
+  // remainder pieces with RM = 1), then w = W.
+  __device__ __forceinline__ void apply_f8(bool res, float2 (&w)[E]) {
+    if (!res) {
+      apply8(w);
+      return;
+    }
+    res8();
+    if constexpr (RM == 1)
+      if (rem != nullptr) {
+        uint32_t b0[KT], b1[KT];
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt) {
+          b0[kt] = b1[kt] = 0u;
+          if (g < NCOL) {
+            const uint2 pw = *reinterpret_cast<const uint2*>(S.Pk + ((kt * NCOL + g) * 4 + t) * 2);
+            b0[kt] = pw.x;
+            b1[kt] = pw.y;
+          }
+        }
+        uint4 q[2][KT];
+        rem_load(rem, 0, q);
+        __syncwarp();
+        rem_apply(rem, b0, b1, q);
+      }
     __syncwarp();
 #pragma unroll
     for (int e = 0; e < E; ++e) w[e] = vact() ? S.W[lane + 32 * e] : make_float2(0.f, 0.f);
@@ -497,7 +626,7 @@ struct CgWarp {
   // that wrote them.
   __device__ __forceinline__ void rem_apply(const uint8_t* src, const uint32_t (&b0)[KT], const uint32_t (&b1)[KT],
                                             uint4 (&q)[2][KT]) {
-    const int NR = (F8 ? rem_np : tc_rem_pieces(BF)) * MT;
+    constexpr int NR = tc_rem_pieces(BF) * MT;
 #pragma unroll 1
     for (int i = 0; i < NR; ++i) {
       float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
@@ -535,10 +664,8 @@ struct CgWarp {
       return;
     }
     if constexpr (F8) {
-      if (!res) {
-        apply8(w);
-        return;
-      }
+      apply_f8(res, w);
+      return;
     }
     gsync();  // NS > 1: every warp's rows are packed
     uint32_t b0[KT], b1[KT];
@@ -551,15 +678,7 @@ struct CgWarp {
         b1[kt] = pw.y;
       }
     }
-    if constexpr (F8) {  // residual: W = b, then W -= (each piece) x
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (vact()) S.W[lane + 32 * e] = S.b[lane + 32 * e];
-      uint4 q[2][KT];
-      rem_load(rem, 0, q);
-      __syncwarp();
-      rem_apply(rem, b0, b1, q);
-    } else if constexpr (NS > 1) {  // this warp's m-tiles interleaved along k
+    if constexpr (NS > 1) {  // this warp's m-tiles interleaved along k
       apply_mtiles<MT / NS>(sj * (MT / NS), res, b0, b1);
     } else {  // m-tiles in pairs: more independent chains, a rolled loop keeps the code small
       constexpr int MP = MT >= 2 ? 2 : 1;

@@ -46,6 +46,23 @@ __device__ __forceinline__ float e4m3_scale(float amax) {
   return ldexpf(1.f, k);
 }
 
+// e4m3_scale(amax) and its reciprocal from the bits of amax (both exact powers
+// of two); amax outside [2^-118, 2^127) takes e4m3_scale itself.  amax = 1.f *
+// 2^E = m 2^(E+1) with m = 1.f / 2, and m <= 0.875 is 1.f <= 1.75, i.e. a
+// fraction field of at most 0x600000.
+__device__ __forceinline__ float e4m3_scale_inv(float amax, float& inv) {
+  const uint32_t b = __float_as_uint(amax);
+  if (b - 0x04800000u < 0x7f000000u - 0x04800000u) {
+    const int E = (int)(b >> 23) - 127;
+    const int k = (b & 0x7fffffu) <= 0x600000u ? E - 8 : E - 7;
+    inv = __uint_as_float((uint32_t)(127 - k) << 23);
+    return __uint_as_float((uint32_t)(127 + k) << 23);
+  }
+  const float s = e4m3_scale(amax);
+  inv = 1.f / s;
+  return s;
+}
+
 // ---- error-free transformations (Knuth TwoSum, FMA-based TwoProd) ---------
 // The _rn intrinsics are never contracted into FMAs, which these rely on.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

@@ -16,7 +16,6 @@ struct DetectTcParams {
   int iters, L, refine_steps, refine_iters, alpha_num, ip;
   int nslots;      // systems in flight per CTA (tc_num_slots)
   int resid_gram;  // fused kernel: residuals against the fp32 Gram (remainder pieces in global scratch)
-  int rem_pieces;  // fused e4m3 kernel: 16-bit pieces of the residual's matrix in the scratch (1 or 3)
   int status_or;   // OR the status bits into status[] instead of storing them (a Gram pass wrote it first)
   float2* x_hat;
   uint8_t* sym;
@@ -41,15 +40,20 @@ __host__ __device__ constexpr int md_block_stride(int L) { return L == 4 ? 18 : 
 // the matvec format, the fp32 diagonal blocks M_d, b and the matvec result [K]
 // (c64) and the packed B fragments (3K words).  16-bit matvec: [Re A; Im A]
 // (2K x K).  e4m3 matvec (f8): A as K rows of 2K bytes (Re, Im interleaved),
-// its per-(row, 16-column block) fp32 scales [K][K/16] and a 1 KB staging
-// area per 16 rows, used by the drain only.
+// its per-(row, 16-column block) fp32 scales [K][K/16], 6K more words of
+// B fragments (x in six e4m3 pieces for the residual) and the K/16 block
+// scales of the vector last packed.
 __host__ __device__ inline size_t tc_slot_bytes(int K, int L, bool f8 = false) {
-  size_t s = f8 ? 2 * (size_t)K * K + sizeof(float) * (size_t)K * (K / 16) + 64 * (size_t)K : 4 * (size_t)K * K;
+  size_t s = f8 ? 2 * (size_t)K * K + sizeof(float) * (size_t)K * (K / 16) : 4 * (size_t)K * K;
   s += sizeof(float2) * (L > 0 ? (size_t)(K / L) * md_block_stride(L) : 2);
   s += sizeof(float2) * K * 2;
-  s += sizeof(uint32_t) * 3 * K;
+  s += sizeof(uint32_t) * (f8 ? 9 : 3) * K + (f8 ? sizeof(float) * (K / 16) : 0);
   return (s + 127) & ~size_t(127);
 }
+
+// e4m3 kernel: the drain's staging of 16-bit remainder pieces, 1 KB per drain
+// warp, after the slots.
+constexpr size_t kTcF8StageBytes = 4 * 1024;
 
 constexpr int kTcCgWarps = 6;       // CG warps, one slot each (at most)
 
@@ -58,15 +62,14 @@ constexpr int kTcCgWarps = 6;       // CG warps, one slot each (at most)
 // (fp16: 11 + 11 significant bits of the 24) or two (bf16: 8 + 8 + 8), in
 // mma.sync A-fragment order, kept in a device scratch pool (one region per
 // resident CTA, at most one CTA per SM) instead of shared memory.  With an
-// e4m3 matvec the slot holds no 16-bit copy, and the residual's matrix is all
-// in the scratch: A_mv exactly as one bf16 piece, or the fp32 Gram as three
-// (8 + 8 + 8 significant bits).
+// e4m3 matvec the remainder is A - A_mv, as two bf16 pieces (the first within
+// 2^-4 of an entry, so 4 + 8 + 8 significant bits and a last error of
+// 2^-22 of the entry).
 constexpr int kTcScratchRegions = 160;  // >= SMs of the GPU (checked at launch)
-constexpr int kTcRemMaxPieces = 3;
 __host__ __device__ constexpr int tc_rem_pieces(bool bf16) { return bf16 ? 2 : 1; }
 __host__ __device__ constexpr size_t tc_rem_piece_bytes(int K) { return 4 * (size_t)K * K; }
 __host__ __device__ constexpr size_t tc_rem_region_bytes(int K) {
-  return (size_t)kTcCgWarps * kTcRemMaxPieces * tc_rem_piece_bytes(K);
+  return (size_t)kTcCgWarps * 2 * tc_rem_piece_bytes(K);
 }
 constexpr int kTcStages32 = 4;      // FP32 TMA ring depth of the fused kernel
 constexpr size_t kTcSmemMax = 227 * 1024;
@@ -83,13 +86,14 @@ __host__ __device__ inline size_t tc_slots_offset(int K) {
 
 // Systems in flight per CTA: as many slots as fit beside the pipeline, one per CG warp.
 inline int tc_num_slots(int K, int L, bool f8 = false) {
-  const size_t avail = kTcSmemMax - 1024 - tc_slots_offset(K);
+  const size_t avail = kTcSmemMax - 1024 - tc_slots_offset(K) - (f8 ? kTcF8StageBytes : 0);
   const size_t n = avail / tc_slot_bytes(K, L, f8);
   return n < (size_t)kTcCgWarps ? (int)n : kTcCgWarps;
 }
 
 inline size_t detect_tc_smem_bytes(int K, int L, bool f8 = false) {
-  const size_t s = 1024 + tc_slots_offset(K) + tc_num_slots(K, L, f8) * tc_slot_bytes(K, L, f8);
+  const size_t s =
+      1024 + tc_slots_offset(K) + tc_num_slots(K, L, f8) * tc_slot_bytes(K, L, f8) + (f8 ? kTcF8StageBytes : 0);
   return s < 120 * 1024 ? 120 * 1024 : s;  // one CTA (one 512-column TMEM allocation) per SM
 }
 

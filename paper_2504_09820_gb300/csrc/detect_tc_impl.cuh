@@ -62,6 +62,7 @@ struct Smem {
   volatile int* abort;
   int* region;       // this CTA's scratch region (-1: none)
   uint8_t* slots;
+  uint8_t* f8stage;  // e4m3 kernel: the drain's staging, 1 KB per drain warp
 };
 
 // Scratch pool of the remainder pieces: one region per resident CTA.  The
@@ -76,7 +77,7 @@ __device__ int g_rem_busy[kTcScratchRegions];
 
 template <int K>
 __device__ __forceinline__ uint8_t* rem_slot(int region, int slot) {
-  return g_rem<K> + (size_t)region * tc_rem_region_bytes(K) + (size_t)slot * kTcRemMaxPieces * tc_rem_piece_bytes(K);
+  return g_rem<K> + (size_t)region * tc_rem_region_bytes(K) + (size_t)slot * 2 * tc_rem_piece_bytes(K);
 }
 
 // Drain warpgroup: tile j of this CTA (TMEM buffer j & 1) holds systems
@@ -84,9 +85,8 @@ __device__ __forceinline__ uint8_t* rem_slot(int region, int slot) {
 // row 2k + odd of its system's block.
 // F8: each 16-column block of row k (Re from thread 2k, Im from 2k + 1) is
 // quantised with its own scale (e4m3_scale of the block's largest |component|)
-// into 32 interleaved bytes of A8, and the residual's matrix goes to the
-// scratch as rem_pieces bf16 pieces: A_mv = s_A A8 (exact in bf16) or the fp32
-// Gram (hi, mid, lo).
+// into 32 interleaved bytes of A8; with RG, the exact remainder A - A_mv goes
+// to the scratch as two bf16 pieces.
 template <int K, bool BF, int LT, int RG, int F8>
 __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem, int64_t tile0, int64_t tstep) {
   const tcp::Pipe& pp = P.pipe;
@@ -100,7 +100,6 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
   const int blk0 = ps * twoK;
   const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
   const size_t slot_bytes = tc_slot_bytes(K, LT, F8);
-  const int npieces = F8 ? P.rem_pieces : tc_rem_pieces(BF);
   const uint64_t keep = tc::policy_evict_last();  // remainder pieces: read back by the CG warps
   int64_t j = 0;
   for (int64_t tile = tile0; tile < pp.ntiles; tile += tstep, ++j) {
@@ -154,23 +153,21 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
 #pragma unroll
           for (int mm = 0; mm < 8; ++mm) m = fmaxf(m, fabsf(a[u][mm]));
         m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));  // Re and Im of the block
-        const float sc = e4m3_scale(m), inv = __frcp_rn(sc);  // powers of two
+        float inv;
+        const float sc = e4m3_scale_inv(m, inv);  // powers of two
         uint32_t wq[4];  // e4m3 bytes of columns 4i .. 4i + 3 of this thread's part
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const float* src = &a[i >> 1][4 * (i & 1)];
           wq[i] = tc::cvt_e4m3x4(src[0] * inv, src[1] * inv, src[2] * inv, src[3] * inv);
-          if (npieces == 1) {  // A_mv = sc * e4m3 value, exact in bf16
+          if constexpr (RG) {  // a - sc q: exact (q sc is within a factor of two of a, or 0)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(wq[i] >> (16 * h)), __NV_E4M3);
               const float2 f = __half22float2(__half2(hr));
-              lo[i >> 1][4 * (i & 1) + 2 * h] = f.x * sc;
-              lo[i >> 1][4 * (i & 1) + 2 * h + 1] = f.y * sc;
+              lo[i >> 1][4 * (i & 1) + 2 * h] = src[2 * h] - f.x * sc;
+              lo[i >> 1][4 * (i & 1) + 2 * h + 1] = src[2 * h + 1] - f.y * sc;
             }
-          } else {
-#pragma unroll
-            for (int h = 0; h < 4; ++h) lo[i >> 1][4 * (i & 1) + h] = src[h];
           }
         }
         // thread 2k (Re) writes columns 0-7 of the block, thread 2k + 1 (Im) columns 8-15
@@ -192,13 +189,14 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
         // The scratch pieces in mma A-fragment order (rem_block): the warp owns
         // one m-tile (16 rows of Re A and of Im A); each piece of this k-tile
         // goes row-major through shared memory (the slot's A16 area, rewritten
-        // below, or the e4m3 slot's staging block) and comes back by ldmatrix
-        // as fragments, one 16-byte store per lane.
-        const uint32_t abase = tc::smem_u32(F8 ? sl.stg + mt * 1024 : sl.A16);
+        // below, or the e4m3 kernel's staging block of this warp) and comes
+        // back by ldmatrix as fragments, one 16-byte store per lane.
+        uint8_t* stg = F8 ? S.f8stage + q * 1024 : nullptr;
+        const uint32_t abase = tc::smem_u32(F8 ? stg : sl.A16);
         const int lr = lane & 15, lc = lane >> 4;
         const int srow = odd * 16 + (k & 15);
-#pragma unroll 1
-        for (int pc = 0; pc < npieces; ++pc) {
+#pragma unroll
+        for (int pc = 0; pc < tc_rem_pieces(BF); ++pc) {
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             uint4 q;
@@ -206,7 +204,7 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
             q.y = pk2<BF>(lo[u][2], lo[u][3]);
             q.z = pk2<BF>(lo[u][4], lo[u][5]);
             q.w = pk2<BF>(lo[u][6], lo[u][7]);
-            if (F8) *reinterpret_cast<uint4*>(sl.stg + mt * 1024 + stg_offset(srow, u)) = q;
+            if (F8) *reinterpret_cast<uint4*>(stg + stg_offset(srow, u)) = q;
             else *reinterpret_cast<uint4*>(sl.A16 + a16_offset<K>(arow, 2 * kt + u)) = q;
 #pragma unroll
             for (int mm = 0; mm < 8; ++mm) lo[u][mm] -= round16<BF>(lo[u][mm]);  // exact
@@ -271,7 +269,6 @@ __device__ void cg_role(const DetectTcParams& P, const Smem& S, int c, int64_t t
   CgWarp<K, BF, LT, K, 1, 1, RG, F8> W(P, slot_carve(S.slots + c * tc_slot_bytes(K, LT, F8), K, LT, F8), lane);
   if constexpr (RG == 1)
     if (*S.region >= 0) W.rem = rem_slot<K>(*S.region, c);
-  W.rem_np = P.rem_pieces;
   int64_t seq = c;
   for (; seq / PP < nloc; seq += ns) {
     const uint32_t use = (uint32_t)(seq / ns);
@@ -295,8 +292,8 @@ __device__ void cg_role(const DetectTcParams& P, const Smem& S, int c, int64_t t
 
 // RG = 1: residuals against the fp32 Gram matrix (resid_gram), with the
 // remainder pieces in a scratch region; RG = 0: against A16 alone (none of
-// that code is compiled in).  F8 = 1 (with BF = RG = 1): the e4m3 matvec, and
-// the residual's matrix all in the scratch (rem_pieces bf16 pieces).
+// that code is compiled in).  F8 = 1 (with BF): the e4m3 matvec; RG then
+// makes the residual's remainder A - A_mv.
 template <int K, bool BF, int LT, int RG, int F8>
 __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_constant__ DetectTcParams P) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -311,6 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
     S.abort = reinterpret_cast<volatile int*>(S.tmem_slot + 1);
     S.region = const_cast<int*>(reinterpret_cast<volatile int*>(S.abort + 1));
     S.slots = base + tc_slots_offset(K);
+    S.f8stage = S.slots + (size_t)P.nslots * tc_slot_bytes(K, LT, F8);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const tcp::Pipe& pp = P.pipe;
@@ -378,8 +376,6 @@ cudaError_t launch_k(DetectTcParams P, int num_sms, cudaStream_t stream) {
   const size_t smem = detect_tc_smem_bytes(K, P.L, F8);
   P.nslots = tc_num_slots(K, P.L, F8);
   P.pipe.s32b = tc_stage32_bytes(K);
-  if (!F8) P.rem_pieces = tc_rem_pieces(BF);
-  if (F8 && P.rem_pieces != 1 && P.rem_pieces != 3) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(detect_tc_kernel<K, BF, LT, RG, F8>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -393,14 +389,16 @@ cudaError_t launch_k(DetectTcParams P, int num_sms, cudaStream_t stream) {
 
 template <int K>
 cudaError_t launch_detect_tc_k(const DetectTcParams& P, int num_sms, int mv, cudaStream_t stream) {
-  if (mv == E4M3) {  // residual pieces: the fp32 Gram (3) or A_mv (1)
-    DetectTcParams Q = P;
-    Q.rem_pieces = P.resid_gram ? 3 : 1;
-    switch (P.L) {
-      case 0: return launch_k<K, true, 0, 1, 1>(Q, num_sms, stream);
-      case 4: return launch_k<K, true, 4, 1, 1>(Q, num_sms, stream);
-      case 8: return launch_k<K, true, 8, 1, 1>(Q, num_sms, stream);
-      case 16: return launch_k<K, true, 16, 1, 1>(Q, num_sms, stream);
+  if (mv == E4M3) {  // the residual against A_mv, or with the remainder against the fp32 Gram
+    switch (P.L * 2 + (P.resid_gram ? 1 : 0)) {
+      case 0: return launch_k<K, true, 0, 0, 1>(P, num_sms, stream);
+      case 1: return launch_k<K, true, 0, 1, 1>(P, num_sms, stream);
+      case 8: return launch_k<K, true, 4, 0, 1>(P, num_sms, stream);
+      case 9: return launch_k<K, true, 4, 1, 1>(P, num_sms, stream);
+      case 16: return launch_k<K, true, 8, 0, 1>(P, num_sms, stream);
+      case 17: return launch_k<K, true, 8, 1, 1>(P, num_sms, stream);
+      case 32: return launch_k<K, true, 16, 0, 1>(P, num_sms, stream);
+      case 33: return launch_k<K, true, 16, 1, 1>(P, num_sms, stream);
       default: return cudaErrorInvalidValue;
     }
   }
