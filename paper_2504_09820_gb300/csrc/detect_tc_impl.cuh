@@ -4,9 +4,10 @@
 // persistent launch (one CTA per SM, 16 warps).
 //
 //   warps 0-3    drain warpgroup: TMEM accumulator -> system slots
-//   warps 4-9    CG warps: warp 4+c runs every system that lands in slot c
-//                (as many slots as shared memory holds, up to six)
-//   warps 10-13  converters: FP32 stages -> bf16/fp16 swizzled operand stages
+//   warps 4-9    CG warps (4-11 for K <= 32): warp 4+c runs every system that
+//                lands in slot c (as many slots as shared memory holds)
+//   warps 10-13  converters (12-13 for K <= 32): FP32 stages -> bf16/fp16
+//                swizzled operand stages
 //   warp 14      TMA producer of the FP32 stages
 //   warp 15      TMEM allocation and the UMMA-issuing thread
 //
@@ -45,9 +46,7 @@ namespace {
 constexpr int kThreads = 16 * 32;
 constexpr int kMmaWarp = 15;
 constexpr int kProdWarp = 14;
-constexpr int kCg0 = 4;                     // CG warps 4-9
-constexpr int kConv0 = kCg0 + kTcCgWarps;   // converter warps 10-13
-constexpr int kConv = kProdWarp - kConv0;
+constexpr int kCg0 = 4;                     // CG warps 4 .. 3 + tc_cg_warps(K), then the converters
 
 struct Bars2 {
   uint64_t slot_full[kTcCgWarps];    // drain -> CG warp
@@ -315,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
   for (int i = threadIdx.x; i < tcp::kStages * tcp::kStageBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(tcp::stage16(S.pipe, 0))[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
-    tcp::init_bars(*S.bars, kConv, kTcStages32);
+    tcp::init_bars(*S.bars, kProdWarp - kCg0 - tc_cg_warps(K), kTcStages32);
     for (int i = 0; i < kTcCgWarps; ++i) {
       tc::mbar_init(&S.sbars->slot_full[i], 1);
       tc::mbar_init(&S.sbars->slot_empty[i], 1);
@@ -352,8 +351,10 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
   } else if (warp == kProdWarp) {
     if (lane == 0) tcp::producer_role<kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep);
     __syncwarp();
-  } else if (warp >= kConv0) {
-    tcp::converter_role<kConv, kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, warp - kConv0, lane);
+  } else if (warp >= kCg0 + tc_cg_warps(K)) {
+    constexpr int kConv0 = kCg0 + tc_cg_warps(K);
+    tcp::converter_role<kProdWarp - kConv0, kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, warp - kConv0,
+                                                         lane);
   } else if (warp >= kCg0) {
     if (warp - kCg0 < P.nslots) cg_role<K, BF, LT, RG, F8>(P, S, warp - kCg0, tile0, tstep);
   } else {
