@@ -43,6 +43,48 @@ HEAD = dict(name="FP-BJ-CG", L=4, iters=7,
 SOLVER_PREC = dict(HEAD["prec"], resid="fp32")
 COMP = dict(name="FP32 plain CG", L=None, iters=20,
             prec=dict(gram="fp32", mv="fp32", ip="fp32", w="fp32", refine_steps=0))
+# e4m3 A p (per-block power-of-two scales, fp32 accumulation) with the residual
+# against the fp32 Gram: the head's path with the matvec in FP8, 6 + 6
+# iterations, block-Jacobi L = 4 and 8.
+FP8 = [dict(name=f"FP-BJ-CG e4m3 L={L}", L=L, iters=6,
+            prec=dict(gram="bf16", mv="e4m3", ip="fp32", w="fp32", refine_steps=1, refine_iters=6, resid="fp64"))
+       for L in (4, 8)]
+
+
+def comparator_flops(N, K, iters):
+    """Floating-point operations of one detection by the fp32 comparator
+    (8 per complex multiply-add): the Hermitian half of the Gram matrix and
+    the matched filter, then per CG iteration the matvec (K^2 complex
+    multiply-adds), two inner products and three axpys (about 24 K)."""
+    return 8 * N * K * (K + 1) // 2 + 8 * N * K + iters * (8 * K * K + 24 * K)
+
+
+def gram_half_flops(N, K):
+    """The Hermitian half of one Gram matrix: K (K + 1) / 2 entries of N
+    complex multiply-adds."""
+    return 8 * N * K * (K + 1) // 2
+
+
+def simt_peaks(dev):
+    """fp32 and fp64 FMA rates of the CUDA cores (fpcg_fma_probe, best of
+    three launches timed by CUDA events), TFLOP/s."""
+    import torch
+    from paper_2504_09820_gb300 import fpcg as F
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {}
+    for fp64, name, iters in ((0, "fp32_tflops", 65536), (1, "fp64_tflops", 4096)):
+        buf = torch.empty(sms * 8 * 256, dtype=torch.float64 if fp64 else torch.float32, device=dev)
+        best = 0.0
+        for _ in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fl = F.fpcg_fma_probe(fp64, iters, buf)
+            b.record()
+            torch.cuda.synchronize(dev)
+            best = max(best, fl / (a.elapsed_time(b) / 1e3) / 1e12)
+        out[name] = best
+    out["method"] = "fpcg_fma_probe: 8 independent FMA chains per thread, 8 CTAs of 256 threads per SM"
+    return out
 
 
 def workload_spec(rank=0):
@@ -79,7 +121,7 @@ def bytes_per_detection(N, K):
 # by the hash of the head kernel's sources (kernel_source_hash) it was taken
 # on; a launch moves the same bytes per system, so it scales with the batch.
 # None once the kernel changed.
-KERNEL_TRAFFIC = {"09c401d2fdb9": 135245.0}
+KERNEL_TRAFFIC = {"44fc45ae5cbb": 135168.4}
 
 
 def kernel_source_hash(tu="detect_tc_k64.cu"):
@@ -528,6 +570,17 @@ def main():
     comp = make_call(COMP, o_comp, g)
     c_total, _ = timed(comp, max(2, args.steps // 2), 1)
     comp_det_s = job_rate(world, B, max(2, args.steps // 2), c_total)
+    # its Gram phase alone: the same call with no CG iteration
+    comp_gram = make_call(dict(COMP, iters=0), outputs(), g)
+    cg_total, _ = timed(comp_gram, 2, 1)
+    comp_gram_s = cg_total / 2
+
+    # e4m3 A p on the same batch
+    o_fp8 = [outputs() for _ in FP8]
+    fp8_t = []
+    for cfg, o in zip(FP8, o_fp8):
+        t8, _ = timed(make_call(cfg, o, g), max(2, args.steps // 2), 1)
+        fp8_t.append(t8 / max(2, args.steps // 2))
 
     # BER of both paths vs fp64 LMMSE on a sample.  The LMMSE estimate is the
     # library's own fp64 path: CG in fp64 for 2K iterations (exact after K in
@@ -555,12 +608,14 @@ def main():
         e_head = Q.bit_errors(o_head["sym"][:ns].cpu().numpy(), d["tx"][:ns])
         e_comp = Q.bit_errors(o_comp["sym"][:ns].cpu().numpy(), d["tx"][:ns])
         nbits = ns * K * bps
+        fp8_ber = [Q.bit_errors(o["sym"][:ns].cpu().numpy(), d["tx"][:ns]) / e_ref - 1 for o in o_fp8]
         ber = {"sample_systems": ns, "lmmse": e_ref / nbits, "head": e_head / nbits,
                "comparator": e_comp / nbits, "head_rel_to_lmmse": e_head / e_ref - 1,
                "comparator_rel_to_lmmse": e_comp / e_ref - 1,
                "lmmse_reference": "oracle: float64 Gram of the stored H, Cholesky solve (CPU)",
                "gpu_fp64_cg_rel_to_lmmse": e_cg64 / e_ref - 1,
-               "head_full_batch": int(o_head["be"][0]) / (B * K * bps)}
+               "head_full_batch": int(o_head["be"][0]) / (B * K * bps),
+               "fp8_rel_to_lmmse": fp8_ber}
 
     # end to end through the public API from pinned host buffers
     hst = {k: g[k].cpu().pin_memory() for k in g}
@@ -606,6 +661,11 @@ def main():
                                     "launches_per_step", "systems_per_path", "graph", "roofline", "ber_total",
                                     "status_max")}
 
+    sp = simt_peaks(dev)
+    fp8 = [{"name": cfg["name"], "iters": [cfg["iters"], cfg["prec"]["refine_iters"]], "value": B / t,
+            "unit": UNIT, "ms_per_step": 1e3 * t,
+            "ber_rel_to_lmmse": (ber["fp8_rel_to_lmmse"][i] if ber else None)} for i, (cfg, t) in
+           enumerate(zip(FP8, fp8_t))]
     pk = peaks()
     algo_bytes = B * bytes_per_detection(N, K)
     tpsys = KERNEL_TRAFFIC.get(kernel_source_hash())
@@ -635,7 +695,16 @@ def main():
         "e2e": {"value": job_rate(world, B, e_steps, e_total), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "comparator": {"name": COMP["name"], "iters": COMP["iters"], "value": comp_det_s, "unit": UNIT,
-                       "speedup_of_head": det_s / comp_det_s},
+                       "speedup_of_head": det_s / comp_det_s,
+                       "flops_per_detection": comparator_flops(N, K, COMP["iters"]),
+                       "tflops": comparator_flops(N, K, COMP["iters"]) * comp_det_s / 1e12,
+                       "gram_phase_ms": 1e3 * comp_gram_s,
+                       "gram_tflops": B * gram_half_flops(N, K) / comp_gram_s / 1e12,
+                       "gram_frac_of_fp32_peak": B * gram_half_flops(N, K) / comp_gram_s / 1e12 / sp["fp32_tflops"],
+                       "gram_at_fp32_peak_ms": 1e3 * B * gram_half_flops(N, K) / (sp["fp32_tflops"] * 1e12),
+                       "head_speedup_over_gram_at_fp32_peak":
+                           B * gram_half_flops(N, K) / (sp["fp32_tflops"] * 1e12) / (ms_step / 1e3)},
+        "simt_peaks": sp, "fp8": fp8,
         "ber": ber, "clocks": clocks, "gpu_launches": args.steps, "breakdown": breakdown,
         "serving": serving, "mixed": mixed,
     }

@@ -495,6 +495,20 @@ FPCG_API int fpcg_kappa_cg_batch(const float* coeffs, int32_t iters, int32_t m, 
 FPCG_API int fpcg_choose_method(int32_t k, int32_t block_L, double kappa, double kappa_bar, double tol,
                                 int32_t mv_cg, int32_t mv_bj, int32_t w, int32_t* k_cg, int32_t* k_pcg);
 
+/*
+ * fpcg_fma_probe -- a throughput probe of the CUDA cores, with no counterpart
+ * in the paper: it states the fp32 and fp64 FMA rates that bound the SIMT
+ * kernels (the fp32 plain-CG comparator's Gram runs on these units).  Launches
+ * out_len / 256 blocks of 256 threads on `stream`; every thread runs eight
+ * independent FMA chains for `iters` steps in fp64 (fp64 != 0) or fp32 and
+ * writes one value to out (device, out_len doubles or floats, caller-owned;
+ * its contents mean nothing).  *flops (host, nullable) receives the launch's
+ * floating-point operations (2 per FMA); the caller times the launch.
+ * Asynchronous.  FPCG_EINVAL for out_len not a positive multiple of 256,
+ * iters not a positive multiple of 4, or a null or misaligned out.
+ */
+FPCG_API int fpcg_fma_probe(int32_t fp64, int64_t iters, void* out, int64_t out_len, double* flops, void* stream);
+
 /* Human-readable text for a return code (static storage). */
 FPCG_API const char* fpcg_strerror(int code);
 

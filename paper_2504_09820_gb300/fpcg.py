@@ -139,6 +139,8 @@ def lib():
         L.fpcg_choose_method.argtypes = [_I32, _I32, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I32, _I32,
                                          _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
         L.fpcg_choose_method.restype = ctypes.c_int
+        L.fpcg_fma_probe.argtypes = [_I32, _I64, _P, _I64, ctypes.POINTER(ctypes.c_double), _P]
+        L.fpcg_fma_probe.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -215,6 +217,16 @@ def fpcg_strerror(code):
 
 def fpcg_last_cuda_error():
     return lib().fpcg_last_cuda_error().decode()
+
+
+def fpcg_fma_probe(fp64, iters, out, stream=None):
+    """Launch the FMA throughput probe on `out` (a CUDA float32 or float64
+    tensor, a multiple of 256 elements); returns the launch's flop count."""
+    f = ctypes.c_double(0.0)
+    dt = torch.float64 if fp64 else torch.float32
+    _check(lib().fpcg_fma_probe(1 if fp64 else 0, int(iters), _ptr(out, dt, "out"), int(out.numel()),
+                                ctypes.byref(f), _stream(stream)), "fpcg_fma_probe")
+    return f.value
 
 
 def fpcg_version():
