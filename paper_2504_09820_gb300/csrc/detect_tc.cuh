@@ -15,6 +15,7 @@ struct DetectTcParams {
   const int32_t* qam;
   int iters, L, refine_steps, refine_iters, alpha_num, ip;
   int nslots;      // systems in flight per CTA (tc_num_slots)
+  int ncg;         // CG warps (tc_cg_warps); the converters are the 10 - ncg warps after them
   int resid_gram;  // fused kernel: residuals against the fp32 Gram (remainder pieces in global scratch)
   int status_or;   // OR the status bits into status[] instead of storing them (a Gram pass wrote it first)
   float2* x_hat;
@@ -57,12 +58,16 @@ constexpr size_t kTcF8StageBytes = 4 * 1024;
 
 constexpr int kTcCgWarps = 8;       // CG warps, one slot each (at most)
 
-// CG warps of the fused kernel for K, of its 16 warps: 4 drain the
-// accumulator, 2 feed the pipeline, the rest convert the FP32 stages.  For
-// K = 64 a system brings four times the H of K = 32 (N = 4K), which two
-// converter warps do not keep up with: 6 CG warps and 4 converters there,
-// 8 and 2 below (more systems in flight; the CG warps are latency-bound).
-__host__ __device__ constexpr int tc_cg_warps(int K) { return K >= 64 ? 6 : 8; }
+// CG warps of the fused kernel, of its 16 warps: 4 drain the accumulator, 2
+// feed the pipeline, the rest convert the FP32 stages.  A tile brings 64 x N
+// complex entries of H whatever K is, and two converter warps keep up with
+// N <= 128 only: 8 CG warps and 2 converters there for K <= 32 (more systems
+// in flight; the CG warps are latency-bound), 6 and 4 otherwise (K = 64 has at
+// most six slots).  Measured on GB300, 7 + 7 iterations, L = 4: K = 32,
+// N = 128: 0.58 -> 0.47 ms for 32768 systems; N = 256: 0.62 -> 0.80 ms.
+__host__ __device__ constexpr int tc_cg_warps(int K, int N) { return K <= 32 && N <= 128 ? 8 : 6; }
+// The most CG warps (and slots) a CTA of this K can run.
+__host__ __device__ constexpr int tc_cg_warps_max(int K) { return K <= 32 ? 8 : 6; }
 
 // Remainder of the fp32 Gram matrix beyond its matvec-format copy, for the
 // residual b - A x of the fused kernel: A - A16 as one more 16-bit piece
@@ -76,7 +81,7 @@ constexpr int kTcScratchRegions = 160;  // >= SMs of the GPU (checked at launch)
 __host__ __device__ constexpr int tc_rem_pieces(bool bf16) { return bf16 ? 2 : 1; }
 __host__ __device__ constexpr size_t tc_rem_piece_bytes(int K) { return 4 * (size_t)K * K; }
 __host__ __device__ constexpr size_t tc_rem_region_bytes(int K) {
-  return (size_t)tc_cg_warps(K) * 2 * tc_rem_piece_bytes(K);
+  return (size_t)tc_cg_warps_max(K) * 2 * tc_rem_piece_bytes(K);
 }
 constexpr int kTcStages32 = 4;      // FP32 TMA ring depth of the fused kernel
 constexpr size_t kTcSmemMax = 227 * 1024;
@@ -95,7 +100,7 @@ __host__ __device__ inline size_t tc_slots_offset(int K) {
 inline int tc_num_slots(int K, int L, bool f8 = false) {
   const size_t avail = kTcSmemMax - 1024 - tc_slots_offset(K) - (f8 ? kTcF8StageBytes : 0);
   const size_t n = avail / tc_slot_bytes(K, L, f8);
-  return n < (size_t)tc_cg_warps(K) ? (int)n : tc_cg_warps(K);
+  return n < (size_t)tc_cg_warps_max(K) ? (int)n : tc_cg_warps_max(K);
 }
 
 inline size_t detect_tc_smem_bytes(int K, int L, bool f8 = false) {

@@ -4,10 +4,11 @@
 // persistent launch (one CTA per SM, 16 warps).
 //
 //   warps 0-3    drain warpgroup: TMEM accumulator -> system slots
-//   warps 4-9    CG warps (4-11 for K <= 32): warp 4+c runs every system that
-//                lands in slot c (as many slots as shared memory holds)
-//   warps 10-13  converters (12-13 for K <= 32): FP32 stages -> bf16/fp16
-//                swizzled operand stages
+//   warps 4-9    CG warps (4-11 for K <= 32 and N <= 128: tc_cg_warps): warp
+//                4+c runs every system that lands in slot c (as many slots as
+//                shared memory holds)
+//   warps 10-13  converters (12-13 with eight CG warps): FP32 stages ->
+//                bf16/fp16 swizzled operand stages
 //   warp 14      TMA producer of the FP32 stages
 //   warp 15      TMEM allocation and the UMMA-issuing thread
 //
@@ -46,7 +47,7 @@ namespace {
 constexpr int kThreads = 16 * 32;
 constexpr int kMmaWarp = 15;
 constexpr int kProdWarp = 14;
-constexpr int kCg0 = 4;                     // CG warps 4 .. 3 + tc_cg_warps(K), then the converters
+constexpr int kCg0 = 4;                     // CG warps 4 .. 3 + ncg, then the converters
 
 struct Bars2 {
   uint64_t slot_full[kTcCgWarps];    // drain -> CG warp
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
   for (int i = threadIdx.x; i < tcp::kStages * tcp::kStageBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(tcp::stage16(S.pipe, 0))[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
-    tcp::init_bars(*S.bars, kProdWarp - kCg0 - tc_cg_warps(K), kTcStages32);
+    tcp::init_bars(*S.bars, kProdWarp - kCg0 - P.ncg, kTcStages32);
     for (int i = 0; i < kTcCgWarps; ++i) {
       tc::mbar_init(&S.sbars->slot_full[i], 1);
       tc::mbar_init(&S.sbars->slot_empty[i], 1);
@@ -351,10 +352,10 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
   } else if (warp == kProdWarp) {
     if (lane == 0) tcp::producer_role<kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep);
     __syncwarp();
-  } else if (warp >= kCg0 + tc_cg_warps(K)) {
-    constexpr int kConv0 = kCg0 + tc_cg_warps(K);
-    tcp::converter_role<kProdWarp - kConv0, kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, warp - kConv0,
-                                                         lane);
+  } else if (warp >= kCg0 + P.ncg) {
+    const int cw = warp - kCg0 - P.ncg;
+    if (P.ncg == 8) tcp::converter_role<2, kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, cw, lane);
+    else tcp::converter_role<4, kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, cw, lane);
   } else if (warp >= kCg0) {
     if (warp - kCg0 < P.nslots) cg_role<K, BF, LT, RG, F8>(P, S, warp - kCg0, tile0, tstep);
   } else {
@@ -375,7 +376,9 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
 template <int K, bool BF, int LT, int RG, int F8 = 0>
 cudaError_t launch_k(DetectTcParams P, int num_sms, cudaStream_t stream) {
   const size_t smem = detect_tc_smem_bytes(K, P.L, F8);
+  P.ncg = tc_cg_warps(K, P.pipe.N);
   P.nslots = tc_num_slots(K, P.L, F8);
+  if (P.nslots > P.ncg) P.nslots = P.ncg;
   P.pipe.s32b = tc_stage32_bytes(K);
   cudaError_t e = cudaFuncSetAttribute(detect_tc_kernel<K, BF, LT, RG, F8>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -70,3 +70,9 @@ def test_argument_validation_needs_no_gpu(so):
     assert L.fpcg_detect(1, 1, 1, 1, 64, 16, 1, 4, ctypes.byref(p8), 1, nul, nul, nul, nul, nul, nul, nul) == F.ENOTSUP
     # tx without a counter
     assert L.fpcg_detect(1, 1, 1, 1, 64, 16, 1, 4, ctypes.byref(p), 1, 1, nul, nul, 1, nul, nul, nul) == F.EINVAL
+    # FMA probe: a length that is not a multiple of 256, too few iterations, no buffer
+    f = ctypes.c_double(0.0)
+    assert L.fpcg_fma_probe(0, 64, 256, 255, ctypes.byref(f), nul) == F.EINVAL
+    assert L.fpcg_fma_probe(0, 2, 256, 256, ctypes.byref(f), nul) == F.EINVAL
+    assert L.fpcg_fma_probe(1, 64, nul, 256, ctypes.byref(f), nul) == F.EINVAL
+    assert L.fpcg_fma_probe(1, 64, 4, 256, ctypes.byref(f), nul) == F.EINVAL   # misaligned for fp64
