@@ -253,10 +253,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def mixed_measure(dev, steps, warmup, batch=None, both=True):
+def mixed_measure(dev, steps, warmup, batch=None, both=True, autotune=True):
     """Uneven batch through a plan: every system draws K in {8,...,128}, N = K x
-    {2, 4, 8} (at most 512), rho and the QAM order; one CUDA graph of one
-    persistent launch per (N, K) class, kernels chosen by the autotuner.
+    {2, 4, 8} (at most 512), rho and the QAM order; one CUDA graph of the
+    plan's launches (one fused launch for the K in {16, 32, 64} classes, the
+    Gram pass and the solver of each two-pass class), kernels chosen by the
+    autotuner (autotune=False: the plan's default choice, e.g. for profiling,
+    where the profiler distorts the autotuner's timings).
     Returns the measurement as a dict (both: also time it without the graph)."""
     import torch
     from paper_2504_09820_gb300 import fpcg as F
@@ -274,7 +277,9 @@ def mixed_measure(dev, steps, warmup, batch=None, both=True):
              "st": torch.empty(plan.batch, dtype=torch.int32, device=dev),
              "be": torch.zeros(1, dtype=torch.int64, device=dev)}
         t0 = time.perf_counter()
-        plan.autotune(g["H"], g["y"], g["sigma2"], g["qam"], o["x"], o["sym"], o["rel"], o["st"], stream=stream)
+        if autotune:
+            plan.autotune(g["H"], g["y"], g["sigma2"], g["qam"], o["x"], o["sym"], o["rel"], o["st"],
+                          stream=stream)
         t_tune = time.perf_counter() - t0
 
         def call():
@@ -300,11 +305,13 @@ def mixed_measure(dev, steps, warmup, batch=None, both=True):
     pk = peaks()
     achieved = algo / r["t"] / 1e9
     nbits = float(sum(int(k) * int(round(math.log2(q))) for k, q in zip(d["k"], d["qam"])))
-    paths, launches = {}, 0
+    paths = {}
     for c in r["classes"]:
         key = {F.PATH_TENSOR_CORE: "tensor_core", F.PATH_TWO_PASS: "two_pass"}.get(c["path"], "simt")
         paths[key] = paths.get(key, 0) + c["count"]
-        launches += 2 if c["path"] == F.PATH_TWO_PASS else 1
+    # one launch per launch index (the fused classes share one), plus the Gram
+    # pass of every two-pass class
+    launches = len({c["launch"] for c in r["classes"]}) + sum(c["path"] == F.PATH_TWO_PASS for c in r["classes"])
     out = {"value": B / r["t"], "unit": UNIT, "ms_per_step": 1e3 * r["t"], "steps": steps, "warmup": warmup,
            "workload": f"uneven batch of {B}: K in {spec.ks}, N = K x {spec.ratios} capped at {spec.n_cap}, "
                        f"rho in {spec.rhos}, QAM in {spec.qams}, {spec.snr_db} dB",
@@ -326,9 +333,9 @@ def run_mixed(args):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     F.lib()
-    m = mixed_measure(dev, args.steps, args.warmup, args.batch)
+    m = mixed_measure(dev, args.steps, args.warmup, args.batch, autotune=not args.no_autotune)
     print(json.dumps({
-        "metric": "detections/s, uneven batch (one CUDA graph, one launch per (N, K) class)",
+        "metric": "detections/s, uneven batch (one CUDA graph; one fused launch for the K in {16, 32, 64} classes)",
         "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": m["ms_per_step"], "higher_is_better": True, "dtype": DTYPE, "data": "synthetic",
         "config": {"workload": m["workload"], "method": m["method"], "block_L": m["block_L"], "iters": m["iters"],
@@ -458,6 +465,8 @@ def main():
     ap.add_argument("--workload", default="kron256x64", choices=["kron256x64", "mixed", "serve"],
                     help="mixed: the uneven batch through a plan; serve: the serving loop "
                          "(each prints its own JSON line)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="--workload mixed: keep the plan's default kernel choice (profiling runs)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the serving and uneven-batch sub-measurements of the headline line")
     ap.add_argument("--breakdown", action="store_true",

@@ -342,13 +342,17 @@ typedef struct fpcg_batch_desc {
 } fpcg_batch_desc;
 
 #define FPCG_PLAN_GRAPH 1
+#define FPCG_PLAN_PER_CLASS 2 /* one launch per class (by default the fused-kernel classes of the same
+                               * block size and precisions share one launch: up to ten per launch) */
 
 typedef struct fpcg_class_info {
   int32_t n_rx, k, block_L; /* the class's N, K and block size (0: FP-CG) */
   int32_t path;             /* FPCG_PATH_SIMT, FPCG_PATH_TENSOR_CORE or FPCG_PATH_TWO_PASS */
   int64_t first, count;     /* its systems: plan positions [first, first + count) */
   int32_t mv;               /* its matvec format (the plan's, or fpcg_plan_autoprec's choice) */
-  int32_t reserved;
+  int32_t launch;           /* index of the launch that detects its systems within one run: classes
+                             * that share a fused launch share it (a two-pass class's Gram pass is a
+                             * launch of its own before it) */
   double kappa;             /* fpcg_plan_autoprec's condition-number estimate, 0 before */
 } fpcg_class_info;
 

@@ -22,6 +22,39 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
                 unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits,
                 bool status_or = false, float* coeffs = nullptr);
 
+// One class of a fused multi-class launch: its inputs and outputs (device
+// pointers at the class's first system), N, K and batch size.
+struct FusedClass {
+  const void* H;
+  const void* y;
+  const double* sigma2;
+  const int32_t* qam;
+  int32_t n, k;
+  int64_t batch;
+  void* x_hat;
+  uint8_t* sym;
+  double* rel_res;
+  const uint8_t* tx;
+  int32_t* status;
+};
+
+// Whether a class can join a fused multi-class launch: the fused kernel's
+// K (16, 32, 64), a 16-bit matvec, an even N (the TMA views), aligned data.
+bool fused_multi_capable(const FusedClass& c, int32_t block_L, const fpcg_precision* prec);
+
+constexpr int kFusedMultiMax = 10;  // classes per fused multi-class launch
+
+// Detection of n classes (n <= kFusedMultiMax, every one fused_multi_capable, the same
+// iterations, block size and precisions) in one launch of the fused kernel;
+// bit_errors (nullable) is accumulated into, not zeroed.
+int run_fused_multi(const FusedClass* cls, int n, int32_t iters, int32_t block_L, const fpcg_precision* prec,
+                    unsigned long long* bit_errors, void* stream);
+
+// Device addresses of the fused kernel's scratch pools on the current device,
+// looked up now (call outside a stream capture before capturing a launch
+// that needs them).
+int prepare_fused_pools(void* stream);
+
 // Checks of the arguments common to every detection entry point (no GPU
 // work): FPCG_OK or FPCG_EINVAL.
 int check_detect_args(int32_t k, int64_t batch, int32_t iters, int32_t block_L, const void* x_hat,

@@ -114,6 +114,50 @@ inline bool detect_tc_supported(int K, int L) {
   return (K == 16 || K == 32 || K == 64) && (L == 0 || L == 4 || L == 8 || L == 16) && tc_num_slots(K, L) >= 2;
 }
 
+// Up to kTcMultiMax classes of one fused launch (detect_tc_multi_kernel):
+// each class's own parameters (tensor maps of its H and y, outputs, slots),
+// the number of the class's first tile in the launch's running tile count,
+// and the scratch pools of K = 16, 32, 64 (device addresses, tc_rem_pool).
+constexpr int kTcMultiMax = 10;
+struct MultiTcParams {
+  int nclass;
+  int64_t tile_base[kTcMultiMax];
+  uint8_t* pool[3];
+  int* busy[3];
+  DetectTcParams cls[kTcMultiMax];
+};
+
+// Device address of the scratch pool of K (and its busy flags) on the
+// current device.  Looked up outside stream captures and remembered per
+// device: during a capture the address found earlier is used (a capture that
+// comes first fails with the lookup's error).
+template <int K>
+cudaError_t tc_rem_pool(cudaStream_t stream, uint8_t** pool, int** busy);
+extern template cudaError_t tc_rem_pool<16>(cudaStream_t, uint8_t**, int**);
+extern template cudaError_t tc_rem_pool<32>(cudaStream_t, uint8_t**, int**);
+extern template cudaError_t tc_rem_pool<64>(cudaStream_t, uint8_t**, int**);
+
+// One launch over the classes of M (every class: K in {16, 32, 64}, the
+// given block size L, matvec format and residual mode; cls[c] filled as for
+// launch_detect_tc, pools set).  Instantiated per L in detect_tc_multi_l*.cu.
+template <int LT>
+cudaError_t launch_detect_tc_multi_l(MultiTcParams& M, int num_sms, int mv_bf16, int resid_gram, cudaStream_t s);
+extern template cudaError_t launch_detect_tc_multi_l<0>(MultiTcParams&, int, int, int, cudaStream_t);
+extern template cudaError_t launch_detect_tc_multi_l<4>(MultiTcParams&, int, int, int, cudaStream_t);
+extern template cudaError_t launch_detect_tc_multi_l<8>(MultiTcParams&, int, int, int, cudaStream_t);
+extern template cudaError_t launch_detect_tc_multi_l<16>(MultiTcParams&, int, int, int, cudaStream_t);
+
+inline cudaError_t launch_detect_tc_multi(MultiTcParams& M, int num_sms, int L, int mv_bf16, int resid_gram,
+                                          cudaStream_t s) {
+  switch (L) {
+    case 0: return launch_detect_tc_multi_l<0>(M, num_sms, mv_bf16, resid_gram, s);
+    case 4: return launch_detect_tc_multi_l<4>(M, num_sms, mv_bf16, resid_gram, s);
+    case 8: return launch_detect_tc_multi_l<8>(M, num_sms, mv_bf16, resid_gram, s);
+    case 16: return launch_detect_tc_multi_l<16>(M, num_sms, mv_bf16, resid_gram, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // mv: the matvec format (FPCG_BF16, FPCG_FP16 or FPCG_FP8E4M3 codes).
 template <int K>
 cudaError_t launch_detect_tc_k(const DetectTcParams& P, int num_sms, int mv, cudaStream_t stream);

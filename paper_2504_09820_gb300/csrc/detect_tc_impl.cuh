@@ -35,6 +35,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "cg_warp.cuh"
 #include "common.cuh"
 #include "detect_tc.cuh"
@@ -61,6 +63,8 @@ struct Smem {
   uint32_t* tmem_slot;
   volatile int* abort;
   int* region;       // this CTA's scratch region (-1: none)
+  uint8_t* pool;     // the scratch pool of this K and its busy flags
+  int* busy;
   uint8_t* slots;
   uint8_t* f8stage;  // e4m3 kernel: the drain's staging, 1 KB per drain warp
 };
@@ -76,8 +80,8 @@ template <int K>
 __device__ int g_rem_busy[kTcScratchRegions];
 
 template <int K>
-__device__ __forceinline__ uint8_t* rem_slot(int region, int slot) {
-  return g_rem<K> + (size_t)region * tc_rem_region_bytes(K) + (size_t)slot * 2 * tc_rem_piece_bytes(K);
+__device__ __forceinline__ uint8_t* rem_slot(uint8_t* pool, int region, int slot) {
+  return pool + (size_t)region * tc_rem_region_bytes(K) + (size_t)slot * 2 * tc_rem_piece_bytes(K);
 }
 
 // Drain warpgroup: tile j of this CTA (TMEM buffer j & 1) holds systems
@@ -121,7 +125,7 @@ __device__ void drain_role(const DetectTcParams& P, const Smem& S, uint32_t tmem
     const uint32_t tb = lane_base + b * (uint32_t)tcp::kAccCols;
     const int slot = (int)((j * PP + ps) % ns);
     Slot sl = slot_carve(S.slots + slot * slot_bytes, K, LT, F8);
-    uint8_t* rem = (RG && *S.region >= 0) ? rem_slot<K>(*S.region, slot) : nullptr;
+    uint8_t* rem = (RG && *S.region >= 0) ? rem_slot<K>(S.pool, *S.region, slot) : nullptr;
     const int arow = odd ? K + k : k;           // row of [Re A; Im A]
     const int kb0 = (k / (LT > 0 ? LT : 1)) * LT;  // first column of k's diagonal block
 #pragma unroll 1
@@ -268,7 +272,7 @@ __device__ void cg_role(const DetectTcParams& P, const Smem& S, int c, int64_t t
   const int64_t nloc = tile0 < pp.ntiles ? (pp.ntiles - tile0 + tstep - 1) / tstep : 0;
   CgWarp<K, BF, LT, K, 1, 1, RG, F8> W(P, slot_carve(S.slots + c * tc_slot_bytes(K, LT, F8), K, LT, F8), lane);
   if constexpr (RG == 1)
-    if (*S.region >= 0) W.rem = rem_slot<K>(*S.region, c);
+    if (*S.region >= 0) W.rem = rem_slot<K>(S.pool, *S.region, c);
   int64_t seq = c;
   for (; seq / PP < nloc; seq += ns) {
     const uint32_t use = (uint32_t)(seq / ns);
@@ -290,26 +294,30 @@ __device__ void cg_role(const DetectTcParams& P, const Smem& S, int c, int64_t t
   }
 }
 
+// One batch of one (N, K) class by the whole CTA: barriers, scratch region,
+// the roles over tiles tile0, tile0 + tstep, ... of P, and on the way out the
+// region released and the barriers invalidated (the next class of a
+// multi-class launch lays shared memory out anew).  `base` is the 1024-byte
+// aligned start of dynamic shared memory, `tmem` the CTA's 512 TMEM columns,
+// `pool` / `busy` the scratch pool of this K.
 // RG = 1: residuals against the fp32 Gram matrix (resid_gram), with the
 // remainder pieces in a scratch region; RG = 0: against A16 alone (none of
 // that code is compiled in).  F8 = 1 (with BF): the e4m3 matvec; RG then
 // makes the residual's remainder A - A_mv.
 template <int K, bool BF, int LT, int RG, int F8>
-__global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_constant__ DetectTcParams P) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
+__device__ __forceinline__ void detect_tc_body(const DetectTcParams& P, uint8_t* base, uint32_t tmem, int64_t tile0,
+                                               int64_t tstep, uint8_t* pool, int* busy) {
   Smem S;
-  {
-    const uint32_t a = tc::smem_u32(smem_raw);
-    uint8_t* base = smem_raw + ((1024u - (a & 1023u)) & 1023u);
-    S.pipe = base;
-    S.bars = reinterpret_cast<tcp::Bars*>(base + tcp::pipe_bytes(kTcStages32, tc_stage32_bytes(K)));
-    S.sbars = reinterpret_cast<Bars2*>(S.bars + 1);
-    S.tmem_slot = reinterpret_cast<uint32_t*>(S.sbars + 1);
-    S.abort = reinterpret_cast<volatile int*>(S.tmem_slot + 1);
-    S.region = const_cast<int*>(reinterpret_cast<volatile int*>(S.abort + 1));
-    S.slots = base + tc_slots_offset(K);
-    S.f8stage = S.slots + (size_t)P.nslots * tc_slot_bytes(K, LT, F8);
-  }
+  S.pipe = base;
+  S.bars = reinterpret_cast<tcp::Bars*>(base + tcp::pipe_bytes(kTcStages32, tc_stage32_bytes(K)));
+  S.sbars = reinterpret_cast<Bars2*>(S.bars + 1);
+  S.tmem_slot = reinterpret_cast<uint32_t*>(S.sbars + 1);
+  S.abort = reinterpret_cast<volatile int*>(S.tmem_slot + 1);
+  S.region = const_cast<int*>(reinterpret_cast<volatile int*>(S.abort + 1));
+  S.pool = pool;
+  S.busy = busy;
+  S.slots = base + tc_slots_offset(K);
+  S.f8stage = S.slots + (size_t)P.nslots * tc_slot_bytes(K, LT, F8);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const tcp::Pipe& pp = P.pipe;
   for (int i = threadIdx.x; i < tcp::kStages * tcp::kStageBytes / 16; i += kThreads)
@@ -325,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
     if (RG) {
       for (int t = 0; t < 2 * kTcScratchRegions && got < 0; ++t) {
         const int c = (int)((blockIdx.x + t) % kTcScratchRegions);
-        if (atomicCAS(&g_rem_busy<K>[c], 0, 1) == 0) got = c;
+        if (atomicCAS(&busy[c], 0, 1) == 0) got = c;
       }
       __threadfence();  // the previous holder's accesses happen before ours
       if (got < 0) *S.abort = 1;  // not expected (one CTA per SM): no work, status FPCG_ST_TIMEOUT
@@ -333,13 +341,10 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
     *S.region = got;
     tc::fence_mbar_init();
   }
-  if (warp == kMmaWarp) tc::tmem_alloc(S.tmem_slot, 2 * tcp::kAccCols);
   tc::fence_proxy_async();
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = *S.tmem_slot;
-  const int64_t tile0 = blockIdx.x, tstep = gridDim.x;
 
   if (*S.abort) {  // no scratch region: nothing was started; this CTA's systems are reported
     if (warp == kCg0 && P.status)
@@ -363,23 +368,87 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
   }
   tc::tc_fence_before();
   __syncthreads();
+  if (threadIdx.x == 0) {
+    if (RG && *S.region >= 0) {  // every access of this CTA to its region is done
+      __threadfence();
+      atomicExch(&busy[*S.region], 0);
+    }
+    tcp::inval_bars(*S.bars, kTcStages32);
+    for (int i = 0; i < kTcCgWarps; ++i) {
+      tc::mbar_inval(&S.sbars->slot_full[i]);
+      tc::mbar_inval(&S.sbars->slot_empty[i]);
+    }
+  }
+  __syncthreads();
+}
+
+// The fused detector for one class: one CTA per SM, tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...
+template <int K, bool BF, int LT, int RG, int F8>
+__global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_constant__ DetectTcParams P) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ uint32_t s_tmem;
+  const uint32_t a = tc::smem_u32(smem_raw);
+  uint8_t* base = smem_raw + ((1024u - (a & 1023u)) & 1023u);
+  const int warp = threadIdx.x >> 5;
+  if (warp == kMmaWarp) tc::tmem_alloc(&s_tmem, 2 * tcp::kAccCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  detect_tc_body<K, BF, LT, RG, F8>(P, base, tmem, blockIdx.x, gridDim.x, g_rem<K>, g_rem_busy<K>);
   if (warp == kMmaWarp) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, 2 * tcp::kAccCols);
   }
-  if (RG && threadIdx.x == 0 && *S.region >= 0) {  // every access of this CTA to its region is done
-    __threadfence();
-    atomicExch(&g_rem_busy<K>[*S.region], 0);
+}
+
+// The fused detector for up to kTcMultiMax classes (K in {16, 32, 64}, the
+// same matvec format, residual and block size) in one persistent launch.  The
+// classes' tiles are numbered on, class after class, and dealt round-robin
+// over the CTAs, so a CTA whose share of one class ends early starts on the
+// next while the last tiles of the first still run elsewhere.
+template <bool BF, int LT, int RG>
+__global__ void __launch_bounds__(kThreads, 1) detect_tc_multi_kernel(const __grid_constant__ MultiTcParams M) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ uint32_t s_tmem;
+  const uint32_t a = tc::smem_u32(smem_raw);
+  uint8_t* base = smem_raw + ((1024u - (a & 1023u)) & 1023u);
+  const int warp = threadIdx.x >> 5;
+  if (warp == kMmaWarp) tc::tmem_alloc(&s_tmem, 2 * tcp::kAccCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const int64_t g = gridDim.x;
+  for (int c = 0; c < M.nclass; ++c) {
+    const DetectTcParams& P = M.cls[c];
+    const int64_t tile0 = (((int64_t)blockIdx.x - M.tile_base[c]) % g + g) % g;
+    switch (P.pipe.K) {
+      case 16: detect_tc_body<16, BF, LT, RG, 0>(P, base, tmem, tile0, g, M.pool[0], M.busy[0]); break;
+      case 32: detect_tc_body<32, BF, LT, RG, 0>(P, base, tmem, tile0, g, M.pool[1], M.busy[1]); break;
+      case 64: detect_tc_body<64, BF, LT, RG, 0>(P, base, tmem, tile0, g, M.pool[2], M.busy[2]); break;
+      default: break;
+    }
   }
+  if (warp == kMmaWarp) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 2 * tcp::kAccCols);
+  }
+}
+
+// The launch settings of one class: CG warps, slots, FP32 stage size.
+inline void class_settings(DetectTcParams& P, int K, bool f8) {
+  P.ncg = tc_cg_warps(K, P.pipe.N);
+  P.nslots = tc_num_slots(K, P.L, f8);
+  if (P.nslots > P.ncg) P.nslots = P.ncg;
+  P.pipe.s32b = tc_stage32_bytes(K);
 }
 
 template <int K, bool BF, int LT, int RG, int F8 = 0>
 cudaError_t launch_k(DetectTcParams P, int num_sms, cudaStream_t stream) {
   const size_t smem = detect_tc_smem_bytes(K, P.L, F8);
-  P.ncg = tc_cg_warps(K, P.pipe.N);
-  P.nslots = tc_num_slots(K, P.L, F8);
-  if (P.nslots > P.ncg) P.nslots = P.ncg;
-  P.pipe.s32b = tc_stage32_bytes(K);
+  class_settings(P, K, F8);
   cudaError_t e = cudaFuncSetAttribute(detect_tc_kernel<K, BF, LT, RG, F8>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -389,7 +458,67 @@ cudaError_t launch_k(DetectTcParams P, int num_sms, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+template <bool BF, int LT, int RG>
+cudaError_t launch_multi(MultiTcParams& M, int num_sms, cudaStream_t stream) {
+  size_t smem = 0;
+  int64_t tiles = 0;
+  for (int c = 0; c < M.nclass; ++c) {
+    DetectTcParams& P = M.cls[c];
+    const int K = P.pipe.K;
+    if ((K != 16 && K != 32 && K != 64) || P.L != LT) return cudaErrorInvalidValue;
+    class_settings(P, K, false);
+    const size_t sm = detect_tc_smem_bytes(K, LT);
+    smem = sm > smem ? sm : smem;
+    M.tile_base[c] = tiles;
+    tiles += P.pipe.ntiles;
+  }
+  cudaError_t e =
+      cudaFuncSetAttribute(detect_tc_multi_kernel<BF, LT, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t grid = tiles < num_sms ? tiles : num_sms;
+  if (grid <= 0) return cudaSuccess;
+  detect_tc_multi_kernel<BF, LT, RG><<<(unsigned)grid, kThreads, smem, stream>>>(M);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+template <int LT>
+cudaError_t launch_detect_tc_multi_l(MultiTcParams& M, int num_sms, int mv_bf16, int resid_gram, cudaStream_t s) {
+  if (M.nclass < 1 || M.nclass > kTcMultiMax) return cudaErrorInvalidValue;
+  switch ((mv_bf16 ? 2 : 0) + (resid_gram ? 1 : 0)) {
+    case 0: return launch_multi<false, LT, 0>(M, num_sms, s);
+    case 1: return launch_multi<false, LT, 1>(M, num_sms, s);
+    case 2: return launch_multi<true, LT, 0>(M, num_sms, s);
+    default: return launch_multi<true, LT, 1>(M, num_sms, s);
+  }
+}
+
+template <int K>
+cudaError_t tc_rem_pool(cudaStream_t stream, uint8_t** pool, int** busy) {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static void* addr[kMaxDev][2] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cap == cudaStreamCaptureStatusNone || !addr[dev][0]) {
+    e = cudaGetSymbolAddress(&addr[dev][0], g_rem<K>);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&addr[dev][1], g_rem_busy<K>);
+    if (e != cudaSuccess) {
+      addr[dev][0] = addr[dev][1] = nullptr;
+      return e;
+    }
+  }
+  *pool = static_cast<uint8_t*>(addr[dev][0]);
+  *busy = static_cast<int*>(addr[dev][1]);
+  return cudaSuccess;
+}
 
 template <int K>
 cudaError_t launch_detect_tc_k(const DetectTcParams& P, int num_sms, int mv, cudaStream_t stream) {

@@ -4,6 +4,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <new>
+
 #include "../../include/fpcg.h"
 #include "api_internal.cuh"
 #include "detect_simt.cuh"
@@ -206,6 +208,75 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
 }
 
 int cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+bool fused_multi_capable(const FusedClass& c, int32_t block_L, const fpcg_precision* prec) {
+  return (c.k == 16 || c.k == 32 || c.k == 64) && (prec->mv == FPCG_BF16 || prec->mv == FPCG_FP16) &&
+         !force_simt() && tc_capable(c.k, block_L, prec) && c.batch > 0 && c.x_hat &&
+         fpcg::tma_pipe_ok(c.H, c.y, c.n) && !check_detect_args(c.k, c.batch, 0, block_L, c.x_hat, c.sym, c.qam,
+                                                                c.tx, c.tx ? (const unsigned long long*)1 : nullptr);
+}
+
+int prepare_fused_pools(void* stream) {
+  uint8_t* pool;
+  int* busy;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = fpcg::tc_rem_pool<16>(s, &pool, &busy);
+  if (e == cudaSuccess) e = fpcg::tc_rem_pool<32>(s, &pool, &busy);
+  if (e == cudaSuccess) e = fpcg::tc_rem_pool<64>(s, &pool, &busy);
+  return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+}
+
+static_assert(kFusedMultiMax == fpcg::kTcMultiMax, "one limit on the classes of a fused launch");
+
+int run_fused_multi(const FusedClass* cls, int n, int32_t iters, int32_t block_L, const fpcg_precision* prec,
+                    unsigned long long* bit_errors, void* stream) {
+  if (n < 1 || n > kFusedMultiMax || iters < 0) return FPCG_EINVAL;
+  int rc = check_prec(prec);
+  if (rc) return rc;
+  for (int c = 0; c < n; ++c)
+    if (!fused_multi_capable(cls[c], block_L, prec)) return FPCG_ENOTSUP;
+  int sms = 0;
+  rc = device_sms(&sms);
+  if (rc) return rc;
+  if (prec->resid == FPCG_FP64 && sms > fpcg::kTcScratchRegions) return FPCG_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the parameter block is large (up to ten tensor-map pairs): built on the heap
+  fpcg::MultiTcParams* M = new (std::nothrow) fpcg::MultiTcParams;
+  if (!M) return FPCG_ENOMEM;
+  memset(M, 0, sizeof(*M));
+  M->nclass = n;
+  cudaError_t e = fpcg::tc_rem_pool<16>(s, &M->pool[0], &M->busy[0]);
+  if (e == cudaSuccess) e = fpcg::tc_rem_pool<32>(s, &M->pool[1], &M->busy[1]);
+  if (e == cudaSuccess) e = fpcg::tc_rem_pool<64>(s, &M->pool[2], &M->busy[2]);
+  if (e != cudaSuccess) {
+    delete M;
+    return cuda_fail(e);
+  }
+  const int refine_iters = prec->refine_iters < 0 ? iters : prec->refine_iters;
+  size_t smem = 0;
+  for (int c = 0; c < n; ++c) {
+    const FusedClass& f = cls[c];
+    fpcg::DetectTcParams& T = M->cls[c];
+    if (!fpcg::make_pipe(&T.pipe, (const float2*)f.H, (const float2*)f.y, f.n, f.k, f.batch,
+                         prec->gram == FPCG_BF16)) {
+      delete M;
+      return FPCG_ENOTSUP;
+    }
+    T.sigma2 = f.sigma2;
+    cg_params(T, f.qam, iters, block_L, prec, refine_iters, f.x_hat, f.sym, f.rel_res, nullptr, f.tx,
+              f.tx ? bit_errors : nullptr, f.status);
+    T.resid_gram = prec->resid == FPCG_FP64;
+    const size_t sm = fpcg::detect_tc_smem_bytes(f.k, block_L);
+    smem = sm > smem ? sm : smem;
+  }
+  rc = check_device_smem(smem);
+  if (!rc) {
+    e = fpcg::launch_detect_tc_multi(*M, sms, block_L, prec->mv == FPCG_BF16, prec->resid == FPCG_FP64, s);
+    rc = e == cudaSuccess ? FPCG_OK : cuda_fail(e);
+  }
+  delete M;
+  return rc;
+}
 
 int check_detect_args(int32_t k, int64_t batch, int32_t iters, int32_t block_L, const void* x_hat,
                       const uint8_t* sym_idx, const int32_t* qam_order, const uint8_t* tx_idx,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -97,7 +98,61 @@ int run_class(fpcg_plan* p, const fpcg_plan::Class& c, int path, const void* H, 
                            status ? status + c.first : nullptr, s, path, false);
 }
 
-// Issues every class on `s`; bit_errors is zeroed once.
+// A class that may share one launch of the fused kernel with others: the
+// fused kernel's path and K, a 16-bit matvec.
+bool groupable(const fpcg_plan* p, const fpcg_plan::Class& c) {
+  return !(p->flags & FPCG_PLAN_PER_CLASS) && path_of(p, c) == FPCG_PATH_TENSOR_CORE &&
+         (c.k == 16 || c.k == 32 || c.k == 64) && (c.prec.mv == FPCG_BF16 || c.prec.mv == FPCG_FP16);
+}
+
+bool same_launch(const fpcg_plan::Class& a, const fpcg_plan::Class& b) {
+  return a.L == b.L && std::memcmp(&a.prec, &b.prec, sizeof(fpcg_precision)) == 0;
+}
+
+fpcg::FusedClass fused_class(const fpcg_plan::Class& c, const void* H, const void* y, const double* sigma2,
+                             const int32_t* qam, void* x_hat, uint8_t* sym, double* rel_res, const uint8_t* tx,
+                             int32_t* status) {
+  fpcg::FusedClass f;
+  f.H = static_cast<const float2*>(H) + c.h0;
+  f.y = static_cast<const float2*>(y) + c.y0;
+  f.sigma2 = sigma2 + c.first;
+  f.qam = qam ? qam + c.first : nullptr;
+  f.n = c.n;
+  f.k = c.k;
+  f.batch = c.count;
+  f.x_hat = static_cast<float2*>(x_hat) + c.x0;
+  f.sym = sym ? sym + c.x0 : nullptr;
+  f.rel_res = rel_res ? rel_res + c.first : nullptr;
+  f.tx = tx ? tx + c.x0 : nullptr;
+  f.status = status ? status + c.first : nullptr;
+  return f;
+}
+
+// Launch index of every class within one run: the fused classes of the same
+// block size and precisions share one (up to ten per launch), every other
+// class has its own.
+std::vector<int32_t> launch_ids(const fpcg_plan* p) {
+  std::vector<int32_t> id(p->cls.size(), -1);
+  int32_t next = 0;
+  for (size_t i = 0; i < p->cls.size(); ++i) {
+    if (id[i] >= 0) continue;
+    id[i] = next;
+    if (groupable(p, p->cls[i])) {
+      int members = 1;
+      for (size_t j = i + 1; j < p->cls.size() && members < fpcg::kFusedMultiMax; ++j)
+        if (id[j] < 0 && groupable(p, p->cls[j]) && same_launch(p->cls[i], p->cls[j])) {
+          id[j] = next;
+          ++members;
+        }
+    }
+    ++next;
+  }
+  return id;
+}
+
+// Issues every class on `s`; bit_errors is zeroed once.  Classes that share a
+// launch index run in one launch of the fused kernel (each class on its own if
+// the data of one of them does not allow it).
 int enqueue(fpcg_plan* p, const void* H, const void* y, const double* sigma2, const int32_t* qam,
             void* x_hat, uint8_t* sym, double* rel_res, const uint8_t* tx, unsigned long long* bits,
             int32_t* status, cudaStream_t s) {
@@ -105,9 +160,31 @@ int enqueue(fpcg_plan* p, const void* H, const void* y, const double* sigma2, co
     cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return fpcg::cuda_error(e);
   }
-  for (const auto& c : p->cls) {
+  const std::vector<int32_t> id = launch_ids(p);
+  std::vector<bool> done(p->cls.size(), false);
+  for (size_t i = 0; i < p->cls.size(); ++i) {
+    if (done[i]) continue;
+    const auto& c = p->cls[i];
+    std::vector<size_t> members;
+    for (size_t j = i; j < p->cls.size(); ++j)
+      if (id[j] == id[i]) members.push_back(j);
+    if (members.size() >= 2) {
+      std::vector<fpcg::FusedClass> f;
+      bool ok = true;
+      for (size_t j : members) {
+        f.push_back(fused_class(p->cls[j], H, y, sigma2, qam, x_hat, sym, rel_res, tx, status));
+        ok = ok && fpcg::fused_multi_capable(f.back(), c.L, &c.prec);
+      }
+      if (ok) {
+        const int rc = fpcg::run_fused_multi(f.data(), (int)f.size(), p->iters, c.L, &c.prec, bits, s);
+        if (rc) return rc;
+        for (size_t j : members) done[j] = true;
+        continue;
+      }
+    }
     const int rc = run_class(p, c, path_of(p, c), H, y, sigma2, qam, x_hat, sym, rel_res, tx, bits, status, s);
     if (rc) return rc;
+    done[i] = true;
   }
   return FPCG_OK;
 }
@@ -201,6 +278,7 @@ int fpcg_plan_classes(const fpcg_plan* p, int32_t* n_classes, fpcg_class_info* i
   if (!p || !n_classes) return FPCG_EINVAL;
   *n_classes = (int32_t)p->cls.size();
   if (info) {
+    const std::vector<int32_t> ids = launch_ids(p);
     for (size_t c = 0; c < p->cls.size(); ++c) {
       const auto& k = p->cls[c];
       info[c].n_rx = k.n;
@@ -210,7 +288,7 @@ int fpcg_plan_classes(const fpcg_plan* p, int32_t* n_classes, fpcg_class_info* i
       info[c].first = k.first;
       info[c].count = k.count;
       info[c].mv = k.prec.mv;
-      info[c].reserved = 0;
+      info[c].launch = ids[c];
       info[c].kappa = k.kappa;
     }
   }
@@ -363,6 +441,8 @@ int fpcg_plan_run(fpcg_plan* p, const void* H, const void* y, const double* sigm
   }
   const int wrc = ensure_workspace(p);
   if (wrc) return wrc;
+  const int prc = fpcg::prepare_fused_pools(s);  // the capture below uses the addresses found now
+  if (prc) return prc;
   const void* key[10] = {H, y, sigma2, qam, x_hat, sym, rel_res, tx, bits, status};
   if (p->exec && !std::equal(key, key + 10, p->key)) drop_graph(p);
   if (!p->exec) {

@@ -132,6 +132,9 @@ __device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B,
       tc::tma_load_2d_hint(st + kStage32HBytes, &p.tmY, 64 * c, (int)(tile * p.P), &B.full32[s], once);
     }
   }
+  // the last loads have landed before this role ends, even where the consumers
+  // left early (an abort raised after the last issue)
+  wait_issued_loads<S32>(B.full32, u);
 }
 
 // Converter warp `cw` of NC: columns cl = cw + NC m of the tile and y of
@@ -192,7 +195,7 @@ __device__ inline void converter_role(const Pipe& p, uint8_t* pipe_base, Bars& B
 __device__ inline void mma_role(const Pipe& p, uint8_t* pipe_base, Bars& B, volatile int* abort, uint32_t tmem,
                                 int64_t tile0, int64_t tstep) {
   const uint32_t idesc = tc::idesc_f16(128, kMmaN, p.bf16 != 0);
-  uint32_t u = 0;
+  uint32_t u = 0, nacc = 0;
   int64_t j = 0;
   for (int64_t tile = tile0; tile < p.ntiles; tile += tstep, ++j) {
     const uint32_t b = (uint32_t)(j & 1), qa = (uint32_t)(j >> 1);
@@ -220,10 +223,15 @@ __device__ inline void mma_role(const Pipe& p, uint8_t* pipe_base, Bars& B, vola
     }
     if (*abort) break;
     tc::mma_commit(&B.acc_full[b]);
+    ++nacc;
   }
-  // make sure nothing is in flight before the TMEM is released
+  // make sure nothing is in flight before the TMEM is released, and that the
+  // last commits' arrivals (stages nobody waits for again, tiles an aborting
+  // drain did not take) have landed before the barriers can be invalidated
   tc::mma_commit(&B.done);
   tc::mbar_wait_issued(&B.done, 0);
+  wait_issued_loads<kStages>(B.empty, u);
+  wait_issued_loads<2>(B.acc_full, nacc);
 }
 
 // Initialise the pipeline's barriers (one thread).
@@ -241,6 +249,24 @@ __device__ inline void init_bars(Bars& B, int nconv, int stages32 = kStages32) {
     tc::mbar_init(&B.acc_empty[b], 1);
   }
   tc::mbar_init(&B.done, 1);
+}
+
+// Invalidate the pipeline's barriers (one thread, every phase complete), so
+// that their memory can be laid out anew.
+__device__ inline void inval_bars(Bars& B, int stages32 = kStages32) {
+  for (int s = 0; s < stages32; ++s) {
+    tc::mbar_inval(&B.full32[s]);
+    tc::mbar_inval(&B.empty32[s]);
+  }
+  for (int s = 0; s < kStages; ++s) {
+    tc::mbar_inval(&B.full[s]);
+    tc::mbar_inval(&B.empty[s]);
+  }
+  for (int b = 0; b < 2; ++b) {
+    tc::mbar_inval(&B.acc_full[b]);
+    tc::mbar_inval(&B.acc_empty[b]);
+  }
+  tc::mbar_inval(&B.done);
 }
 
 // Drain helper: for the calling thread (TMEM lane `row` of the tile) combine

@@ -68,10 +68,11 @@ class BatchDesc(ctypes.Structure):
 class ClassInfo(ctypes.Structure):
     _fields_ = [("n_rx", ctypes.c_int32), ("k", ctypes.c_int32), ("block_L", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("first", ctypes.c_int64), ("count", ctypes.c_int64),
-                ("mv", ctypes.c_int32), ("reserved", ctypes.c_int32), ("kappa", ctypes.c_double)]
+                ("mv", ctypes.c_int32), ("launch", ctypes.c_int32), ("kappa", ctypes.c_double)]
 
 
 PLAN_GRAPH = 1
+PLAN_PER_CLASS = 2
 
 _lib = None
 _P = ctypes.c_void_p
@@ -390,7 +391,7 @@ class Plan:
     ``run`` and ``autotune`` take packed device buffers in that layout.
     """
 
-    def __init__(self, n_rx, k, iters, prec, block_L=0, graph=False):
+    def __init__(self, n_rx, k, iters, prec, block_L=0, graph=False, per_class=False):
         import numpy as np
         self._n = np.ascontiguousarray(n_rx, dtype=np.int32)
         self._k = np.ascontiguousarray(k, dtype=np.int32)
@@ -398,7 +399,7 @@ class Plan:
             raise ValueError("n_rx and k must be 1-D and of equal length")
         self.batch = int(self._n.size)
         d = BatchDesc(self.batch, self._n.ctypes.data, self._k.ctypes.data, int(iters),
-                      int(block_L or 0), prec, PLAN_GRAPH if graph else 0)
+                      int(block_L or 0), prec, (PLAN_GRAPH if graph else 0) | (PLAN_PER_CLASS if per_class else 0))
         h = ctypes.c_void_p()
         _check(lib().fpcg_plan_create(ctypes.byref(d), ctypes.byref(h)), "fpcg_plan_create")
         self._h = h
@@ -454,7 +455,7 @@ class Plan:
         info = (ClassInfo * n.value)()
         _check(lib().fpcg_plan_classes(self._h, ctypes.byref(n), info), "fpcg_plan_classes")
         return [dict(n_rx=c.n_rx, k=c.k, block_L=c.block_L, path=c.path, first=c.first, count=c.count,
-                     mv=FORMAT_NAME[c.mv], kappa=c.kappa) for c in info]
+                     mv=FORMAT_NAME[c.mv], kappa=c.kappa, launch=c.launch) for c in info]
 
     def autoprec(self, H, y, sigma2, tol=1e-3, stream=None):
         """Per-class matvec format and FP-CG / FP-BJ-CG choice (fpcg_plan_autoprec)."""

@@ -58,3 +58,33 @@ def test_gram_timeout_reported(monkeypatch):
     F.fpcg_gram(H, y, s2, "bf16", A, b, status=st)
     torch.cuda.synchronize()
     assert torch.all(st == 0) and torch.isfinite(torch.view_as_real(A)).all()
+
+
+def test_timeout_in_a_multi_class_launch(monkeypatch):
+    """The fused launch over several classes: with the one-cycle budget every
+    class's systems report FPCG_ST_TIMEOUT (each class's CTAs abort and the
+    next class starts from fresh barriers); with the default budget the
+    results are the earlier ones."""
+    d = wl.generate_mixed(wl.MixedSpec(batch=300, seed=63))
+    prec = F.precision(gram="bf16", mv="fp16", refine_steps=1, resid="fp64")
+    p = F.Plan(d["n"], d["k"], 6, prec, block_L=4)
+    g = p.pack(d["H"], d["y"], d["sigma2"], d["qam"], d["tx"])
+    fused = [c for c in p.classes() if c["path"] == F.PATH_TENSOR_CORE and c["k"] in (16, 32, 64)]
+    assert len(fused) >= 2 and len({c["launch"] for c in fused}) == 1
+
+    def run():
+        n = p.totals[2]
+        x = torch.zeros(n, dtype=torch.complex64, device="cuda")
+        st = torch.zeros(p.batch, dtype=torch.int32, device="cuda")
+        p.run(g["H"], g["y"], g["sigma2"], g["qam"], x, status=st)
+        torch.cuda.synchronize()
+        return x.cpu(), st.cpu()
+
+    x0, st0 = run()
+    monkeypatch.setenv("FPCG_TC_WAIT_CYCLES", "1")
+    _, st1 = run()
+    monkeypatch.delenv("FPCG_TC_WAIT_CYCLES")
+    for c in fused:
+        assert torch.all(st1[c["first"]:c["first"] + c["count"]] & F.ST_TIMEOUT != 0), c
+    x2, st2 = run()
+    assert torch.equal(x2, x0) and torch.equal(st2, st0)

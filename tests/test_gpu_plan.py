@@ -133,3 +133,50 @@ def test_two_pass_class_equals_gram_then_solve(mixed):
         F.fpcg_solve_gram(A, b, ITERS, c["block_L"], F.precision(**PREC), xs)
         torch.cuda.synchronize()
         assert np.array_equal(xs.cpu().numpy(), np.stack([x[i] for i in idx])), c
+
+
+def test_fused_classes_share_one_launch(mixed):
+    """The one-pass classes of K in {16, 32, 64} (one block size, one set of
+    precisions) run in one launch of the fused kernel; the results are those
+    of one launch per class (FPCG_PLAN_PER_CLASS), bit for bit."""
+    d, p, g = mixed
+    cls = p.classes()
+    fused = [c for c in cls if c["path"] == F.PATH_TENSOR_CORE and c["k"] in (16, 32, 64)]
+    assert len(fused) >= 2
+    assert len({c["launch"] for c in fused}) == 1
+    others = [c["launch"] for c in cls if c not in fused]
+    assert fused[0]["launch"] not in others and len(set(others)) == len(others)
+    q = F.Plan(d["n"], d["k"], ITERS, F.precision(**PREC), block_L=L, graph=False, per_class=True)
+    assert len({c["launch"] for c in q.classes()}) == len(cls)
+    a = _run(p, g)
+    b = _run(q, g)
+    for k in ("x", "sym", "rel", "st", "bits"):
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_fused_launch_with_ten_classes_and_a_split():
+    """More fused classes than one launch holds (ten): the plan splits them
+    into launches of at most ten, and every class still equals its uniform call."""
+    pairs = [(n, k) for k in (16, 32, 64) for n in (2 * k, 3 * k, 4 * k, 6 * k) if n <= 384]
+    rng = np.random.default_rng(5)
+    parts = [wl.generate(wl.Spec(N=n, K=k, batch=int(rng.integers(3, 40)), rho=0.3, qam=16, snr_db=15.0,
+                                 seed=900 + i)) for i, (n, k) in enumerate(pairs)]
+    nn = np.concatenate([[pt["H"].shape[2]] * pt["H"].shape[0] for pt in parts])
+    kk = np.concatenate([[pt["H"].shape[1]] * pt["H"].shape[0] for pt in parts])
+    d = {"n": nn, "k": kk, "H": [h for pt in parts for h in pt["H"]], "y": [v for pt in parts for v in pt["y"]],
+         "sigma2": np.concatenate([pt["sigma2"] for pt in parts]), "qam": np.concatenate([pt["qam"] for pt in parts]),
+         "tx": [t for pt in parts for t in pt["tx"]]}
+    p = F.Plan(d["n"], d["k"], 5, F.precision(**PREC), block_L=4)
+    g = p.pack(d["H"], d["y"], d["sigma2"], d["qam"], d["tx"])
+    cls = p.classes()
+    assert len(cls) == len(pairs) and all(c["path"] == F.PATH_TENSOR_CORE for c in cls)
+    ids = [c["launch"] for c in cls]
+    assert len(set(ids)) == 2 and max(ids.count(i) for i in set(ids)) == 10
+    out = _run(p, g)
+    x = p.unpack(out["x"], d["k"])
+    for c in cls:
+        idx = np.sort(p.order[c["first"]:c["first"] + c["count"]])
+        cd = _class_data(d, idx)
+        t = {k: torch.from_numpy(v).cuda() for k, v in cd.items()}
+        res = F.detect(t["H"], t["y"], t["sigma2"], t["qam"], 5, F.precision(**PREC), L=4)
+        assert np.array_equal(res["x"].cpu().numpy(), np.stack([x[i] for i in idx])), c

@@ -63,3 +63,24 @@ def test_descriptor_checks():
     e = F.Plan([], [], 4, pr)                     # empty batch
     assert e.totals == (0, 0, 0) and e.classes() == []
     e.close()
+
+
+def test_launch_indices():
+    """The fused-kernel classes (K in {16, 32, 64}) share one launch index,
+    up to ten classes per launch; every other class has its own; with
+    per_class every class has its own."""
+    n, k, _, _ = wl.mixed_params(wl.MixedSpec(batch=500, seed=7))
+    p = F.Plan(n, k, 6, F.precision(**PREC), block_L=8)
+    cls = p.classes()
+    fused = [c for c in cls if c["path"] == F.PATH_TENSOR_CORE]
+    rest = [c for c in cls if c["path"] != F.PATH_TENSOR_CORE]
+    assert 2 <= len(fused) <= 10 and len({c["launch"] for c in fused}) == 1
+    ids = [c["launch"] for c in rest] + [fused[0]["launch"]]
+    assert len(set(ids)) == len(ids) and sorted(set(c["launch"] for c in cls)) == list(range(len(ids)))
+    q = F.Plan(n, k, 6, F.precision(**PREC), block_L=8, per_class=True)
+    assert sorted(c["launch"] for c in q.classes()) == list(range(len(cls)))
+    # e4m3 classes and the SIMT path are not grouped
+    r = F.Plan(n, k, 6, F.precision(gram="bf16", mv="e4m3", refine_steps=1), block_L=8)
+    assert len({c["launch"] for c in r.classes()}) == len(cls)
+    for x in (p, q, r):
+        x.close()
