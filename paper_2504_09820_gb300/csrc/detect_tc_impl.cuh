@@ -296,15 +296,18 @@ __device__ void cg_role(const DetectTcParams& P, const Smem& S, int c, int64_t t
 
 // One batch of one (N, K) class by the whole CTA: barriers, scratch region,
 // the roles over tiles tile0, tile0 + tstep, ... of P, and on the way out the
-// region released and the barriers invalidated (the next class of a
-// multi-class launch lays shared memory out anew).  `base` is the 1024-byte
+// region released.  MULTI (a class of a multi-class launch): the producer and
+// the MMA thread also wait for their last TMA loads and commits, and the
+// barriers are invalidated, since the next class lays shared memory out anew
+// (a single-class launch ends with the CTA, and its abort path already waits
+// for what it issued).  `base` is the 1024-byte
 // aligned start of dynamic shared memory, `tmem` the CTA's 512 TMEM columns,
 // `pool` / `busy` the scratch pool of this K.
 // RG = 1: residuals against the fp32 Gram matrix (resid_gram), with the
 // remainder pieces in a scratch region; RG = 0: against A16 alone (none of
 // that code is compiled in).  F8 = 1 (with BF): the e4m3 matvec; RG then
 // makes the residual's remainder A - A_mv.
-template <int K, bool BF, int LT, int RG, int F8>
+template <int K, bool BF, int LT, int RG, int F8, bool MULTI>
 __device__ __forceinline__ void detect_tc_body(const DetectTcParams& P, uint8_t* base, uint32_t tmem, int64_t tile0,
                                                int64_t tstep, uint8_t* pool, int* busy) {
   Smem S;
@@ -352,14 +355,14 @@ __device__ __forceinline__ void detect_tc_body(const DetectTcParams& P, uint8_t*
         for (int p = lane; p < 64 / K; p += 32)
           if (tile * (64 / K) + p < pp.batch) P.status[tile * (64 / K) + p] = 32;
   } else if (warp == kMmaWarp) {
-    if (lane == 0) tcp::mma_role(pp, S.pipe, *S.bars, S.abort, tmem, tile0, tstep);
+    if (lane == 0) tcp::mma_role<MULTI>(pp, S.pipe, *S.bars, S.abort, tmem, tile0, tstep);
     __syncwarp();
   } else if (warp == kProdWarp) {
-    if (lane == 0) tcp::producer_role<kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep);
+    if (lane == 0) tcp::producer_role<kTcStages32, MULTI>(pp, S.pipe, *S.bars, S.abort, tile0, tstep);
     __syncwarp();
   } else if (warp >= kCg0 + P.ncg) {
     const int cw = warp - kCg0 - P.ncg;
-    if (P.ncg == 8) tcp::converter_role<2, kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, cw, lane);
+    if (K <= 32 && P.ncg == 8) tcp::converter_role<2, kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, cw, lane);
     else tcp::converter_role<4, kTcStages32>(pp, S.pipe, *S.bars, S.abort, tile0, tstep, cw, lane);
   } else if (warp >= kCg0) {
     if (warp - kCg0 < P.nslots) cg_role<K, BF, LT, RG, F8>(P, S, warp - kCg0, tile0, tstep);
@@ -373,13 +376,15 @@ __device__ __forceinline__ void detect_tc_body(const DetectTcParams& P, uint8_t*
       __threadfence();
       atomicExch(&busy[*S.region], 0);
     }
-    tcp::inval_bars(*S.bars, kTcStages32);
-    for (int i = 0; i < kTcCgWarps; ++i) {
-      tc::mbar_inval(&S.sbars->slot_full[i]);
-      tc::mbar_inval(&S.sbars->slot_empty[i]);
+    if constexpr (MULTI) {
+      tcp::inval_bars(*S.bars, kTcStages32);
+      for (int i = 0; i < kTcCgWarps; ++i) {
+        tc::mbar_inval(&S.sbars->slot_full[i]);
+        tc::mbar_inval(&S.sbars->slot_empty[i]);
+      }
     }
   }
-  __syncthreads();
+  if constexpr (MULTI) __syncthreads();
 }
 
 // The fused detector for one class: one CTA per SM, tiles blockIdx.x,
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_kernel(const __grid_con
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = s_tmem;
-  detect_tc_body<K, BF, LT, RG, F8>(P, base, tmem, blockIdx.x, gridDim.x, g_rem<K>, g_rem_busy<K>);
+  detect_tc_body<K, BF, LT, RG, F8, false>(P, base, tmem, blockIdx.x, gridDim.x, g_rem<K>, g_rem_busy<K>);
   if (warp == kMmaWarp) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, 2 * tcp::kAccCols);
@@ -425,9 +430,9 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_multi_kernel(const __gr
     const DetectTcParams& P = M.cls[c];
     const int64_t tile0 = (((int64_t)blockIdx.x - M.tile_base[c]) % g + g) % g;
     switch (P.pipe.K) {
-      case 16: detect_tc_body<16, BF, LT, RG, 0>(P, base, tmem, tile0, g, M.pool[0], M.busy[0]); break;
-      case 32: detect_tc_body<32, BF, LT, RG, 0>(P, base, tmem, tile0, g, M.pool[1], M.busy[1]); break;
-      case 64: detect_tc_body<64, BF, LT, RG, 0>(P, base, tmem, tile0, g, M.pool[2], M.busy[2]); break;
+      case 16: detect_tc_body<16, BF, LT, RG, 0, true>(P, base, tmem, tile0, g, M.pool[0], M.busy[0]); break;
+      case 32: detect_tc_body<32, BF, LT, RG, 0, true>(P, base, tmem, tile0, g, M.pool[1], M.busy[1]); break;
+      case 64: detect_tc_body<64, BF, LT, RG, 0, true>(P, base, tmem, tile0, g, M.pool[2], M.busy[2]); break;
       default: break;
     }
   }

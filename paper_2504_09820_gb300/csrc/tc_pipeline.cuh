@@ -108,8 +108,9 @@ __device__ __forceinline__ uint8_t* stage16(uint8_t* pipe_base, int t) {
 }
 
 // Producer role (one thread): tiles this CTA owns are tile0, tile0 + tstep, ...
-// S32 = FP32 stages in the ring (2..kStages32).
-template <int S32 = kStages32>
+// S32 = FP32 stages in the ring (2..kStages32).  DRAIN: also wait for the last
+// loads at the end (the shared memory is reused after the role ends).
+template <int S32 = kStages32, bool DRAIN = false>
 __device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B, volatile int* abort,
                                      int64_t tile0, int64_t tstep) {
   const uint32_t tx = kStage32HBytes + 64 * 4 * p.P;
@@ -134,7 +135,7 @@ __device__ inline void producer_role(const Pipe& p, uint8_t* pipe_base, Bars& B,
   }
   // the last loads have landed before this role ends, even where the consumers
   // left early (an abort raised after the last issue)
-  wait_issued_loads<S32>(B.full32, u);
+  if constexpr (DRAIN) wait_issued_loads<S32>(B.full32, u);
 }
 
 // Converter warp `cw` of NC: columns cl = cw + NC m of the tile and y of
@@ -191,7 +192,9 @@ __device__ inline void converter_role(const Pipe& p, uint8_t* pipe_base, Bars& B
   }
 }
 
-// MMA role (one thread).
+// MMA role (one thread).  DRAIN: also wait for the arrivals of the last
+// commits at the end (the shared memory is reused after the role ends).
+template <bool DRAIN = false>
 __device__ inline void mma_role(const Pipe& p, uint8_t* pipe_base, Bars& B, volatile int* abort, uint32_t tmem,
                                 int64_t tile0, int64_t tstep) {
   const uint32_t idesc = tc::idesc_f16(128, kMmaN, p.bf16 != 0);
@@ -230,8 +233,10 @@ __device__ inline void mma_role(const Pipe& p, uint8_t* pipe_base, Bars& B, vola
   // drain did not take) have landed before the barriers can be invalidated
   tc::mma_commit(&B.done);
   tc::mbar_wait_issued(&B.done, 0);
-  wait_issued_loads<kStages>(B.empty, u);
-  wait_issued_loads<2>(B.acc_full, nacc);
+  if constexpr (DRAIN) {
+    wait_issued_loads<kStages>(B.empty, u);
+    wait_issued_loads<2>(B.acc_full, nacc);
+  }
 }
 
 // Initialise the pipeline's barriers (one thread).
