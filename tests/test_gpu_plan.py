@@ -154,6 +154,23 @@ def test_fused_classes_share_one_launch(mixed):
         assert torch.equal(a[k], b[k]), k
 
 
+def test_fused_launch_with_the_gram_residual():
+    """The multi-class launch with the residual against the fp32 Gram matrix:
+    each class's remainder pieces in the scratch pool of its K (passed to the
+    kernel as device addresses), results bit-identical to one launch per class."""
+    d = wl.generate_mixed(wl.MixedSpec(batch=360, seed=12))
+    pk = dict(PREC, resid="fp64")
+    p = F.Plan(d["n"], d["k"], ITERS, F.precision(**pk), block_L=4, graph=True)
+    q = F.Plan(d["n"], d["k"], ITERS, F.precision(**pk), block_L=4, graph=False, per_class=True)
+    g = p.pack(d["H"], d["y"], d["sigma2"], d["qam"], d["tx"])
+    fused = [c for c in p.classes() if c["path"] == F.PATH_TENSOR_CORE and c["k"] in (16, 32, 64)]
+    assert len(fused) >= 2 and len({c["launch"] for c in fused}) == 1
+    a = _run(p, g)
+    b = _run(q, g)
+    for k in ("x", "sym", "rel", "st", "bits"):
+        assert torch.equal(a[k], b[k]), k
+
+
 def test_fused_launch_with_ten_classes_and_a_split():
     """More fused classes than one launch holds (ten): the plan splits them
     into launches of at most ten, and every class still equals its uniform call."""
