@@ -59,7 +59,7 @@ extern "C" {
 enum {
   FPCG_OK = 0,
   FPCG_EINVAL = 1,   /* bad argument: null pointer, size out of range, K > N, K % L != 0, ... */
-  FPCG_ENOTSUP = 2,  /* valid but not supported here (e.g. fp64 mode with K > 64) */
+  FPCG_ENOTSUP = 2,  /* valid but not supported here (e.g. the fp64 mode with K > 64 on a given Gram matrix) */
   FPCG_ECUDA = 3,    /* a CUDA call or kernel launch failed; see fpcg_last_cuda_error() */
   FPCG_ENOMEM = 4    /* reserved for entry points that allocate */
 };
@@ -164,8 +164,11 @@ typedef struct fpcg_precision {
  *              which sym_idx differs from tx_idx over the batch; nullable
  *   status     [batch] int32 FPCG_ST_* bits; nullable
  *   stream     cudaStream_t
- * Errors: FPCG_EINVAL for a bad argument (nothing is launched),
- * FPCG_ENOTSUP for the fp64 mode with K > 64, FPCG_ECUDA if a launch fails.
+ * Errors: FPCG_EINVAL for a bad argument (nothing is launched), FPCG_ECUDA
+ * if a launch fails.  The fp64 mode with K > 64 never forms A (264 KB in
+ * fp64 at K = 128, beyond shared memory): each product with A is
+ * H^H (H v) + sigma^2 v in fp64 from H itself, the block-Jacobi blocks and b
+ * are formed from H; a reference mode, slower than the others.
  */
 FPCG_API int fpcg_detect(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
                 int32_t n_rx, int32_t k, int64_t batch, int32_t iters,

@@ -20,6 +20,13 @@
 //      matrix with compensated double-fp32 / fp64 sums), a correction solve
 //      with step 3, x += d.
 //   5. rel_res = ||b - A x|| / ||b||, the Gray-QAM decision, bit errors.
+//
+// The fp64 mode for K > 64 (IMP = 1): A = H^H H + sigma^2 I in fp64 does not
+// fit in shared memory (264 KB at K = 128), so it is never formed.  Every
+// product with A is H^H (H v) + sigma^2 v in fp64 straight from H in global
+// memory (antennas in chunks of kIC), the block-Jacobi blocks are formed from
+// H, and b = H^H y likewise.  The same operator in exact arithmetic; the
+// rounding differs at the level of fp64 sums.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +39,7 @@ namespace {
 
 constexpr int NT = 256;   // threads per CTA
 constexpr int TS = 4;     // Gram tile edge
+constexpr int kIC = 256;  // antennas per chunk of an implicit (IMP) product with A
 
 template <typename T>
 struct Smem {
@@ -58,14 +66,15 @@ __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(
 template <typename T>
 __host__ __device__ inline int chunk_rows() { return sizeof(T) == 8 ? 16 : 32; }
 
+// IMP: no A; Hs only as the refinement's scratch (2K), ys as the chunk of H v (kIC).
 template <typename T>
-__host__ __device__ inline size_t smem_bytes(int K, int L, int mv) {
+__host__ __device__ inline size_t smem_bytes(int K, int L, int mv, bool imp = false) {
   const int CH = chunk_rows<T>();
   const int NB = (2 * K + 31) / 32;
   size_t s = 0;
-  s += align16<T>(sizeof(cplx<T>) * (size_t)K * (K + 1));
-  s += align16<T>(sizeof(cplx<T>) * (size_t)CH * (K + 1));
-  s += align16<T>(sizeof(cplx<T>) * (size_t)CH);
+  s += align16<T>(sizeof(cplx<T>) * (imp ? 0 : (size_t)K * (K + 1)));
+  s += align16<T>(sizeof(cplx<T>) * (imp ? (size_t)2 * K : (size_t)CH * (K + 1)));
+  s += align16<T>(sizeof(cplx<T>) * (size_t)(imp ? kIC : CH));
   s += 7 * align16<T>(sizeof(cplx<T>) * (size_t)K);
   s += align16<T>(sizeof(cplx<T>) * (size_t)K * (L > 0 ? L : 1));
   s += align16<T>(sizeof(float) * (size_t)K * NB);
@@ -77,15 +86,15 @@ __host__ __device__ inline size_t smem_bytes(int K, int L, int mv) {
 }
 
 template <typename T>
-__device__ inline Smem<T> carve(unsigned char* base, int K, int L) {
+__device__ inline Smem<T> carve(unsigned char* base, int K, int L, bool imp = false) {
   const int CH = chunk_rows<T>();
   const int NB = (2 * K + 31) / 32;
   Smem<T> s;
   size_t o = 0;
   auto take = [&](size_t bytes) { unsigned char* ptr = base + o; o += align16<T>(bytes); return ptr; };
-  s.A = (cplx<T>*)take(sizeof(cplx<T>) * (size_t)K * (K + 1));
-  s.Hs = (cplx<T>*)take(sizeof(cplx<T>) * (size_t)CH * (K + 1));
-  s.ys = (cplx<T>*)take(sizeof(cplx<T>) * (size_t)CH);
+  s.A = (cplx<T>*)take(sizeof(cplx<T>) * (imp ? 0 : (size_t)K * (K + 1)));
+  s.Hs = (cplx<T>*)take(sizeof(cplx<T>) * (imp ? (size_t)2 * K : (size_t)CH * (K + 1)));
+  s.ys = (cplx<T>*)take(sizeof(cplx<T>) * (size_t)(imp ? kIC : CH));
   s.b = (cplx<T>*)take(sizeof(cplx<T>) * K);
   s.x = (cplx<T>*)take(sizeof(cplx<T>) * K);
   s.r = (cplx<T>*)take(sizeof(cplx<T>) * K);
@@ -320,16 +329,17 @@ __device__ bool load_shared(const SimtParams& P, const Smem<T>& S, int64_t sys) 
 // Returns nonzero (in every thread) if some pivot was not positive.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ int bj_phase(const SimtParams& P, const Smem<T>& S) {
+__device__ int bj_phase(const SimtParams& P, const Smem<T>& S, bool imp = false) {
   const int K = P.K, L = P.L, AS = K + 1;
   const int d = K / L;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (threadIdx.x == 0) S.flags[0] = 0;
-  for (int idx = threadIdx.x; idx < K * L; idx += NT) {
-    const int k = idx / L, j = idx % L;
-    const int blk = k / L;
-    S.Md[idx] = S.A[k * AS + blk * L + j];
-  }
+  if (!imp)  // IMP: the blocks were formed from H (gram_phase_imp)
+    for (int idx = threadIdx.x; idx < K * L; idx += NT) {
+      const int k = idx / L, j = idx % L;
+      const int blk = k / L;
+      S.Md[idx] = S.A[k * AS + blk * L + j];
+    }
   __syncthreads();
   for (int blk = wid; blk < d; blk += NT / 32) {
     cplx<T>* M = S.Md + (size_t)blk * L * L;  // M[i*L + j]
@@ -382,6 +392,84 @@ __device__ int bj_phase(const SimtParams& P, const Smem<T>& S) {
   return f;
 }
 
+// IMP: b = H^H y and (L > 0) the diagonal blocks of A = H^H H + sigma^2 I
+// (Im of the diagonal 0), in fp64 from H, y in global memory; thread per
+// entry.  Md[k L + j] = A[k][blk L + j] with blk = k / L, as bj_phase expects.
+template <typename T>
+__device__ void gram_phase_imp(const SimtParams& P, const Smem<T>& S, int64_t sys) {
+  const int K = P.K, N = P.N, L = P.L;
+  const float2* Hg = P.H + (size_t)sys * K * N;
+  const float2* yg = P.y + (size_t)sys * N;
+  const T s2 = (T)P.sigma2[sys];
+  for (int k = threadIdx.x; k < K; k += NT) {
+    const float2* hk = Hg + (size_t)k * N;
+    T re = T(0), im = T(0);
+    for (int n = 0; n < N; ++n) {  // conj(h) y
+      const float2 h = hk[n], v = yg[n];
+      re = fma((T)h.x, (T)v.x, fma((T)h.y, (T)v.y, re));
+      im = fma((T)h.x, (T)v.y, fma(-(T)h.y, (T)v.x, im));
+    }
+    S.b[k] = cplx<T>{re, im};
+  }
+  if (L > 0)
+    for (int idx = threadIdx.x; idx < K * L; idx += NT) {
+      const int k = idx / L, l = (k / L) * L + idx % L;
+      const float2* hk = Hg + (size_t)k * N;
+      const float2* hl = Hg + (size_t)l * N;
+      T re = T(0), im = T(0);
+      for (int n = 0; n < N; ++n) {  // conj(h_k) h_l
+        const float2 a = hk[n], c = hl[n];
+        re = fma((T)a.x, (T)c.x, fma((T)a.y, (T)c.y, re));
+        im = fma((T)a.x, (T)c.y, fma(-(T)a.y, (T)c.x, im));
+      }
+      if (l == k) {
+        re = re + s2;
+        im = T(0);
+      }
+      S.Md[idx] = cplx<T>{re, im};
+    }
+  __syncthreads();
+}
+
+// IMP: w = H^H (H v) + sigma^2 v in fp64, H from global memory in chunks of
+// kIC antennas (t = H v of the chunk in S.ys, then w += H^H t).  K <= NT.
+template <typename T>
+__device__ void matvec_imp(const SimtParams& P, const Smem<T>& S, const cplx<T>* v, cplx<T>* w) {
+  const int K = P.K, N = P.N, tid = threadIdx.x;
+  const int64_t sys = blockIdx.x;
+  const float2* Hg = P.H + (size_t)sys * K * N;
+  T wr = T(0), wi = T(0);
+  for (int n0 = 0; n0 < N; n0 += kIC) {
+    const int cn = min(kIC, N - n0);
+    for (int i = tid; i < cn; i += NT) {  // t_i = sum_k H[k][n0 + i] v_k
+      T tr = T(0), ti = T(0);
+      for (int k = 0; k < K; ++k) {
+        const float2 h = Hg[(size_t)k * N + n0 + i];
+        const cplx<T> q = v[k];
+        tr = fma((T)h.x, q.re, fma(-(T)h.y, q.im, tr));
+        ti = fma((T)h.x, q.im, fma((T)h.y, q.re, ti));
+      }
+      S.ys[i] = cplx<T>{tr, ti};
+    }
+    __syncthreads();
+    if (tid < K) {  // w_k += sum_i conj(H[k][n0 + i]) t_i
+      const float2* hk = Hg + (size_t)tid * N + n0;
+      for (int i = 0; i < cn; ++i) {
+        const float2 h = hk[i];
+        const cplx<T> t = S.ys[i];
+        wr = fma((T)h.x, t.re, fma((T)h.y, t.im, wr));
+        wi = fma((T)h.x, t.im, fma(-(T)h.y, t.re, wi));
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < K) {
+    const T s2 = (T)P.sigma2[sys];
+    const cplx<T> q = v[tid];
+    w[tid] = cplx<T>{fma(s2, q.re, wr), fma(s2, q.im, wi)};
+  }
+}
+
 // e4m3 scales of A's rows (blocks of 16 complex = 32 real components).
 template <typename T>
 __device__ void fp8_scales_A(const SimtParams& P, const Smem<T>& S) {
@@ -423,7 +511,7 @@ __device__ inline void apply_precond(const SimtParams& P, const Smem<T>& S, cons
 // on right-hand side S.b (main solve) or S.z-initialised rhs.  The solution
 // is left in S.x.  Returns the status bits of this solve.
 // ---------------------------------------------------------------------------
-template <typename T, int MV>
+template <typename T, int MV, bool IMP = false>
 __device__ int cg_phase(const SimtParams& P, const Smem<T>& S, const cplx<T>* rhs, int iters,
                         float* hist, float* coef = nullptr) {
   const int K = P.K, AS = K + 1, L = P.L, NB = (2 * K + 31) / 32;
@@ -480,7 +568,9 @@ __device__ int cg_phase(const SimtParams& P, const Smem<T>& S, const cplx<T>* rh
     }
     __syncthreads();
     // varpi = A p (u_MV); every lane takes part in the shuffles
-    {
+    if constexpr (IMP) {
+      matvec_imp(P, S, S.pq, S.w);
+    } else {
       T wr = T(0), wi = T(0);
       const cplx<T>* Arow = S.A + (size_t)(row_ok ? row : 0) * AS;
       for (int l = part; row_ok && l < K; l += tpr) {
@@ -575,14 +665,20 @@ __device__ int cg_phase(const SimtParams& P, const Smem<T>& S, const cplx<T>* rh
 // itself and the sums are fp64-accurate -- compensated double-fp32 in the fp32
 // modes (FMA TwoProd + TwoSum), plain fp64 in the fp64 mode.
 // ---------------------------------------------------------------------------
-template <typename T, int MV>
+template <typename T, int MV, bool IMP = false>
 __device__ void residual(const SimtParams& P, const Smem<T>& S, cplx<T>* out, double& nr2, double& nb2) {
   const int K = P.K, AS = K + 1, tid = threadIdx.x, NB = (2 * K + 31) / 32;
   int tpr = 32;
   while (tpr > 1 && tpr * K > NT) tpr >>= 1;
   const int row = tid / tpr, part = tid % tpr;
   const bool row_ok = row < K;  // every lane of a warp takes part in the shuffles
-  {
+  if constexpr (IMP) {  // out = b - (H^H (H x) + sigma^2 x), fp64
+    matvec_imp(P, S, S.x, out);
+    if (tid < K) {
+      const cplx<T> bb = S.b[tid], v = out[tid];
+      out[tid] = cplx<T>{bb.re - v.re, bb.im - v.im};
+    }
+  } else {
     const cplx<T>* Arow = S.A + (size_t)(row_ok ? row : 0) * AS;
     if (sizeof(T) == 8) {
       double sr = 0.0, si = 0.0;
@@ -658,12 +754,12 @@ __device__ void residual(const SimtParams& P, const Smem<T>& S, cplx<T>* out, do
   nb2 = c;
 }
 
-template <typename T, int MV>
+template <typename T, int MV, bool IMP = false>
 __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t sys = blockIdx.x;
   if (sys >= P.batch) return;
-  Smem<T> S = carve<T>(smem_raw, P.K, P.L);
+  Smem<T> S = carve<T>(smem_raw, P.K, P.L, IMP);
   const int K = P.K;
   int st = 0;
 
@@ -682,6 +778,8 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
     }
   } else if (P.Ain) {
     load_gram(P, S, sys);
+  } else if constexpr (IMP) {
+    gram_phase_imp(P, S, sys);
   } else {
     gram_phase(P, S, sys);
   }
@@ -693,7 +791,7 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
     return;
   }
 
-  if (P.L > 0 && bj_phase(P, S)) st |= 8;  // FPCG_ST_BJ_FAIL
+  if (P.L > 0 && bj_phase(P, S, IMP)) st |= 8;  // FPCG_ST_BJ_FAIL
   if (MV == E4M3) {
     fp8_scales_A(P, S);
     __syncthreads();
@@ -703,7 +801,7 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
   if (coef)  // a solve that stops early leaves zeros
     for (int k = threadIdx.x; k < 2 * P.iters; k += NT) coef[k] = 0.f;
   __syncthreads();
-  st |= cg_phase<T, MV>(P, S, S.b, P.iters, hist, coef);
+  st |= cg_phase<T, MV, IMP>(P, S, S.b, P.iters, hist, coef);
 
   // refinement: x_hat += solve(A, b - A x_hat)
   for (int rs = 0; rs < P.refine_steps; ++rs) {
@@ -711,7 +809,7 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
     for (int k = threadIdx.x; k < K; k += NT) S.w[k] = S.x[k];
     __syncthreads();
     double nr2, nb2;
-    residual<T, MV>(P, S, S.z, nr2, nb2);  // S.x still holds x_hat
+    residual<T, MV, IMP>(P, S, S.z, nr2, nb2);  // S.x still holds x_hat
     // the correction solve overwrites x, r, p, z, w, pq: move rhs and x_hat out
     // of the way into the staging buffer (free after the Gram phase)
     cplx<T>* xs = S.Hs;
@@ -721,7 +819,7 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
       rhs[k] = S.z[k];
     }
     __syncthreads();
-    st |= cg_phase<T, MV>(P, S, rhs, P.refine_iters, nullptr) & 1;
+    st |= cg_phase<T, MV, IMP>(P, S, rhs, P.refine_iters, nullptr) & 1;
     for (int k = threadIdx.x; k < K; k += NT) {
       cplx<T> v = xs[k];
       const cplx<T> d = S.x[k];
@@ -733,7 +831,7 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
   }
 
   double nr2, nb2;
-  residual<T, MV>(P, S, S.z, nr2, nb2);
+  residual<T, MV, IMP>(P, S, S.z, nr2, nb2);
   if (threadIdx.x == 0 && P.rel_res) P.rel_res[sys] = nb2 > 0.0 ? sqrt(nr2 / nb2) : 0.0;
 
   // outputs
@@ -775,23 +873,27 @@ __global__ void __launch_bounds__(NT) detect_simt_kernel(SimtParams P) {
   if (threadIdx.x == 0 && P.status) P.status[sys] = st;
 }
 
-template <typename T, int MV>
+template <typename T, int MV, bool IMP = false>
 cudaError_t launch_one(const SimtParams& P, cudaStream_t stream) {
-  const size_t smem = smem_bytes<T>(P.K, P.L, MV);
-  cudaError_t e = cudaFuncSetAttribute(detect_simt_kernel<T, MV>,
+  const size_t smem = smem_bytes<T>(P.K, P.L, MV, IMP);
+  cudaError_t e = cudaFuncSetAttribute(detect_simt_kernel<T, MV, IMP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  detect_simt_kernel<T, MV><<<(unsigned)P.batch, NT, smem, stream>>>(P);
+  detect_simt_kernel<T, MV, IMP><<<(unsigned)P.batch, NT, smem, stream>>>(P);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t simt_smem_bytes(int fp64, int K, int L, int mv) {
-  return fp64 ? smem_bytes<double>(K, L, mv) : smem_bytes<float>(K, L, mv);
+  return fp64 ? smem_bytes<double>(K, L, mv, K > 64) : smem_bytes<float>(K, L, mv);
 }
 
 cudaError_t launch_detect_simt(const SimtParams& P, int fp64, int mv, cudaStream_t stream) {
+  if (fp64 && P.K > 64) {  // A too large for shared memory: products from H (not for given A)
+    if (P.Ain || P.A_out || !P.H) return cudaErrorInvalidValue;
+    return launch_one<double, F64, true>(P, stream);
+  }
   if (fp64) return launch_one<double, F64>(P, stream);
   switch (mv) {
     case F32: return launch_one<float, F32>(P, stream);

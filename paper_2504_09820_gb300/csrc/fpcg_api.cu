@@ -114,7 +114,7 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
   if (!Ain && (n_rx < k || n_rx > 65536)) return FPCG_EINVAL;
   if (Ain ? (!bin) : (!H || !y || !sigma2)) return FPCG_EINVAL;
   const int fp64 = prec->w == FPCG_FP64;
-  if (fp64 && k > 64) return FPCG_ENOTSUP;
+  if (fp64 && k > 64 && Ain) return FPCG_ENOTSUP;  // K > 64 in fp64: products from H only
   const int refine_iters = prec->refine_iters < 0 ? iters : prec->refine_iters;
   cudaStream_t s = (cudaStream_t)stream;
   if (bit_errors && reset_bits) {

@@ -64,7 +64,8 @@ def test_argument_validation_needs_no_gpu(so):
     assert L.fpcg_detect(1, 1, 1, 1, 64, 16, 1, 4, ctypes.byref(bad), 1, nul, nul, nul, nul, nul, nul, nul) == F.EINVAL
     # fp64 mode beyond K = 64
     p64 = F.precision(w="fp64")
-    assert L.fpcg_detect(1, 1, 1, 1, 256, 96, 1, 4, ctypes.byref(p64), 1, nul, nul, nul, nul, nul, nul, nul) == F.ENOTSUP
+    # (fp64 mode beyond K = 64 runs from H; on a given Gram matrix it is not supported)
+    assert L.fpcg_solve_gram(1, 1, 96, 1, 4, 0, ctypes.byref(p64), 1, nul, nul, nul, nul) == F.ENOTSUP
     # e4m3 with an unsupported block
     p8 = F.precision(mv="e4m3", fp8_block=16)
     assert L.fpcg_detect(1, 1, 1, 1, 64, 16, 1, 4, ctypes.byref(p8), 1, nul, nul, nul, nul, nul, nul, nul) == F.ENOTSUP

@@ -71,6 +71,31 @@ def test_fp64_mode_larger_systems(N, K, rho, snr):
     _labels_consistent(res, d, "fp64")
 
 
+@pytest.mark.parametrize("N,K,L,rho", [(256, 128, None, 0.3), (512, 128, 8, 0.5), (384, 96, 4, 0.0)])
+def test_fp64_mode_beyond_k64(N, K, L, rho):
+    """The fp64 mode where A does not fit in shared memory (K > 64): every
+    product with A is H^H (H v) + sigma^2 v from H, the block-Jacobi blocks and
+    b are formed from H.  Against the oracle's explicit fp64 Gram matrix: x_hat
+    within 1e-10 after 2K iterations (the fp64 floor), labels bit-exact outside
+    a counted margin, rel_res at the roundoff floor, also with a refinement pass."""
+    d = wl.generate(wl.Spec(N=N, K=K, batch=40, rho=rho, qam=16, snr_db=15.0, seed=3100 + K + N))
+    for pk in (dict(w="fp64"), dict(w="fp64", refine_steps=1, refine_iters=K)):
+        res = gpu_detect(d, 2 * K, pk, L=L)
+        ref = oracle_detect(d, 2 * K, pk, L=L)
+        e = rel_err(res["x"], ref["x"])
+        assert e.max() < 1e-10, (pk, e.max())
+        mask = near_threshold(ref["x"], 16, "fp64", 1e-8)
+        assert mask.sum() <= 2
+        assert np.array_equal(res["sym"][~mask], ref["sym"][~mask])
+        assert np.max(np.abs(res["rel_res"] - ref["rel_res"])) < 1e-12
+        assert np.all(res["status"] & ~F.ST_RHO_ZERO == 0)
+        _labels_consistent(res, d, "fp64")
+    # a few iterations, far from convergence: the operator is the same, the sums differ only at fp64 rounding
+    res = gpu_detect(d, 5, dict(w="fp64"), L=L)
+    ref = oracle_detect(d, 5, dict(w="fp64"), L=L)
+    assert rel_err(res["x"], ref["x"]).max() < 1e-10
+
+
 def test_fp32_comparator_at_the_benchmark_configuration():
     """The plain fp32 CG the benchmark compares against (N=256, K=64, rho=0.7,
     18 dB, 20 iterations, fp32 Gram): relative residual within 1e-5 of the
