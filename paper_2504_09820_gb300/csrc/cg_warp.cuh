@@ -324,7 +324,7 @@ struct CgWarp {
 
   // F8: v as e4m3 B fragments.  k-tile kt holds entries 16kt..16kt+15 (the
   // real components 32kt..32kt+31 of v, Re and Im interleaved), divided by
-  // their block's scale sp[kt] (e4m3_scale of the block's largest |component|)
+  // their block's scale S.sv[kt] (e4m3_scale of the block's largest |component|)
   // and rounded to e4m3.  Column 0 holds (Re v_l, -Im v_l) pairs and column 1
   // (Im v_l, Re v_l), so that a row of A8 (Re, Im interleaved) times them gives
   // Re and Im of (A v)_k.  Word ((kt*2 + col)*4 + tt)*2 + h holds rows
@@ -372,7 +372,7 @@ struct CgWarp {
   }
 
   // F8 residual: x = s0 sum_i 2^(-4i) q_i, q_i in e4m3, six pieces per entry:
-  // s0 = sp[kt] is the e4m3 scale of the block, and piece i + 1 quantises the
+  // s0 = S.sv[kt] is the e4m3 scale of the block, and piece i + 1 quantises the
   // exact remainder of piece i in units 16 times smaller.  The remainder of an
   // e4m3 rounding is at most 2^-4 of the value (subnormals: 2^-10), so no
   // piece saturates, and what is left after six is below 2^-24 of the block's

@@ -1,7 +1,8 @@
 """e4m3 A p on the tensor cores (the fused detector's F8 mode: mma.sync
 m16n8k32 e4m3 with one power-of-two scale per row and 16-column block of A
 and per 16-entry block of p, fp32 partial sums scaled exactly and accumulated
-in fp32; residuals from bf16 pieces of A_mv or of the fp32 Gram) against the
+in fp32; residuals on A8 with x in six e4m3 pieces, plus bf16 pieces of
+A - A_mv against the fp32 Gram) against the
 oracle's emulation of the same quantisation (oracle.formats.quant_e4m3_rows,
 blocks of 32 interleaved real components).  Bars: one or two iterations, where
 the iterate is a short closed form of the quantised products, within 1e-4
@@ -66,7 +67,8 @@ def test_first_iterations_tight(K, L, iters):
 
 
 CASES = [
-    # K, L, iters, refine, resid ("fp64": against the fp32 Gram, three bf16 pieces; "fp32": A_mv, one)
+    # K, L, iters, refine, resid ("fp64": against the fp32 Gram, A8 and two bf16 remainder pieces;
+    # "fp32": against A_mv, A8 alone)
     (64, 4, 6, 1, "fp64"),
     (64, 8, 6, 1, "fp64"),
     (64, 8, 5, 1, "fp32"),
