@@ -357,6 +357,9 @@ typedef struct fpcg_class_info {
                              * that share a fused launch share it (a two-pass class's Gram pass is a
                              * launch of its own before it) */
   double kappa;             /* fpcg_plan_autoprec's condition-number estimate, 0 before */
+  int32_t cg_warps;         /* FPCG_PATH_TENSOR_CORE: CG warps per CTA of the fused kernel (6, or 8
+                             * for K <= 32: the default choice, or fpcg_plan_autotune's); else 0 */
+  int32_t reserved;
 } fpcg_class_info;
 
 /* Builds a plan (host only, no GPU work).  FPCG_EINVAL for a bad descriptor,
@@ -371,8 +374,10 @@ FPCG_API int fpcg_plan_layout(const fpcg_plan* plan, int64_t* order, int64_t* h_
 FPCG_API int fpcg_plan_classes(const fpcg_plan* plan, int32_t* n_classes, fpcg_class_info* info);
 
 /* Times, for every class that both kernels can run, each kernel on the given
- * inputs (plan order; outputs are overwritten) and keeps the faster.  Issues
- * work on `stream` and synchronises it.  Drops a captured graph. */
+ * inputs (plan order; outputs are overwritten) and keeps the faster -- on the
+ * fused kernel for K <= 32 with six and with eight CG warps per CTA (the
+ * results are the same; fpcg_class_info.cg_warps reports the choice).
+ * Issues work on `stream` and synchronises it.  Drops a captured graph. */
 FPCG_API int fpcg_plan_autotune(fpcg_plan* plan, const void* H, const void* y, const double* sigma2,
                                 const int32_t* qam_order, void* x_hat, uint8_t* sym_idx,
                                 double* rel_res, int32_t* status, void* stream);

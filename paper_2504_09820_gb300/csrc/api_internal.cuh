@@ -14,13 +14,17 @@ namespace fpcg {
 // it).  reset_bits: zero *bit_errors first (a plan zeroes it once for all of
 // its classes).  status_or (given Gram matrices, tensor-core solver): OR the
 // solve's status bits into status[], which the Gram pass filled, instead of
-// overwriting them.
+// overwriting them.  cg_warps: the fused kernel's CG warps (fused_cg_warps).
 int run_uniform(const void* H, const void* y, const double* sigma2, const int32_t* qam_order,
                 const void* Ain, const void* bin, int32_t n_rx, int32_t k, int64_t batch, int32_t iters,
                 int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
                 double* rel_res, float* res_hist, const uint8_t* tx_idx,
                 unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits,
-                bool status_or = false, float* coeffs = nullptr);
+                bool status_or = false, float* coeffs = nullptr, int cg_warps = 0);
+
+// CG warps per CTA of the fused kernel for a class: `preset` (6, or 8 for
+// K <= 32) if valid, else the default choice for (K, N).
+int fused_cg_warps(int k, int n, int preset);
 
 // One class of a fused multi-class launch: its inputs and outputs (device
 // pointers at the class's first system), N, K and batch size.
@@ -36,6 +40,7 @@ struct FusedClass {
   double* rel_res;
   const uint8_t* tx;
   int32_t* status;
+  int cg_warps;  // 0: the default choice (fused_cg_warps)
 };
 
 // Whether a class can join a fused multi-class launch: the fused kernel's

@@ -442,9 +442,10 @@ __global__ void __launch_bounds__(kThreads, 1) detect_tc_multi_kernel(const __gr
   }
 }
 
-// The launch settings of one class: CG warps, slots, FP32 stage size.
+// The launch settings of one class: CG warps (a valid preset -- 6, or 8 for
+// K <= 32 -- is kept, anything else replaced by tc_cg_warps), slots, FP32 stage size.
 inline void class_settings(DetectTcParams& P, int K, bool f8) {
-  P.ncg = tc_cg_warps(K, P.pipe.N);
+  if (!(P.ncg == 6 || (P.ncg == 8 && K <= 32))) P.ncg = tc_cg_warps(K, P.pipe.N);
   P.nslots = tc_num_slots(K, P.L, f8);
   if (P.nslots > P.ncg) P.nslots = P.ncg;
   P.pipe.s32b = tc_stage32_bytes(K);

@@ -106,7 +106,7 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
                 int32_t block_L, const fpcg_precision* prec, void* x_hat, uint8_t* sym_idx,
                 double* rel_res, float* res_hist, const uint8_t* tx_idx,
                 unsigned long long* bit_errors, int32_t* status, void* stream, int path, bool reset_bits,
-                bool status_or, float* coeffs) {
+                bool status_or, float* coeffs, int cg_warps) {
   int rc = check_prec(prec);
   if (rc) return rc;
   rc = check_detect_args(k, batch, iters, block_L, x_hat, sym_idx, qam_order, tx_idx, bit_errors);
@@ -170,6 +170,7 @@ int run_uniform(const void* H, const void* y, const double* sigma2, const int32_
     cg_params(T, qam_order, iters, block_L, prec, refine_iters, x_hat, sym_idx, rel_res, res_hist, tx_idx,
               bit_errors, status);
     T.resid_gram = prec->resid == FPCG_FP64;
+    T.ncg = cg_warps;
     cudaError_t e = fpcg::launch_detect_tc(T, sms, prec->mv, s);
     return e == cudaSuccess ? FPCG_OK : cuda_fail(e);
   }
@@ -214,6 +215,10 @@ bool fused_multi_capable(const FusedClass& c, int32_t block_L, const fpcg_precis
          !force_simt() && tc_capable(c.k, block_L, prec) && c.batch > 0 && c.x_hat &&
          fpcg::tma_pipe_ok(c.H, c.y, c.n) && !check_detect_args(c.k, c.batch, 0, block_L, c.x_hat, c.sym, c.qam,
                                                                 c.tx, c.tx ? (const unsigned long long*)1 : nullptr);
+}
+
+int fused_cg_warps(int k, int n, int preset) {
+  return preset == 6 || (preset == 8 && k <= 32) ? preset : fpcg::tc_cg_warps(k, n);
 }
 
 int prepare_fused_pools(void* stream) {
@@ -266,6 +271,7 @@ int run_fused_multi(const FusedClass* cls, int n, int32_t iters, int32_t block_L
     cg_params(T, f.qam, iters, block_L, prec, refine_iters, f.x_hat, f.sym, f.rel_res, nullptr, f.tx,
               f.tx ? bit_errors : nullptr, f.status);
     T.resid_gram = prec->resid == FPCG_FP64;
+    T.ncg = f.cg_warps;
     const size_t sm = fpcg::detect_tc_smem_bytes(f.k, block_L);
     smem = sm > smem ? sm : smem;
   }

@@ -15,6 +15,7 @@
 struct fpcg_plan {
   struct Class {
     int32_t n, k, L, path;         // path: -1 = default choice, else FPCG_PATH_*
+    int32_t ncg = 0;               // fused kernel's CG warps (0: the default choice)
     fpcg_precision prec;           // the plan's, or the one fpcg_plan_autoprec chose for the class
     double kappa = 0.0;            // fpcg_plan_autoprec's estimate (0: none)
     int64_t first, count;          // plan positions
@@ -95,7 +96,7 @@ int run_class(fpcg_plan* p, const fpcg_plan::Class& c, int path, const void* H, 
   return fpcg::run_uniform(Hc, yc, sigma2 + c.first, qam ? qam + c.first : nullptr, nullptr, nullptr, c.n, c.k,
                            c.count, p->iters, c.L, &c.prec, xc, sym ? sym + c.x0 : nullptr,
                            rel_res ? rel_res + c.first : nullptr, nullptr, tx ? tx + c.x0 : nullptr, bits,
-                           status ? status + c.first : nullptr, s, path, false);
+                           status ? status + c.first : nullptr, s, path, false, false, nullptr, c.ncg);
 }
 
 // A class that may share one launch of the fused kernel with others: the
@@ -125,6 +126,7 @@ fpcg::FusedClass fused_class(const fpcg_plan::Class& c, const void* H, const voi
   f.rel_res = rel_res ? rel_res + c.first : nullptr;
   f.tx = tx ? tx + c.x0 : nullptr;
   f.status = status ? status + c.first : nullptr;
+  f.cg_warps = c.ncg;
   return f;
 }
 
@@ -289,6 +291,8 @@ int fpcg_plan_classes(const fpcg_plan* p, int32_t* n_classes, fpcg_class_info* i
       info[c].count = k.count;
       info[c].mv = k.prec.mv;
       info[c].launch = ids[c];
+      info[c].cg_warps = info[c].path == FPCG_PATH_TENSOR_CORE ? fpcg::fused_cg_warps(k.k, k.n, k.ncg) : 0;
+      info[c].reserved = 0;
       info[c].kappa = k.kappa;
     }
   }
@@ -318,9 +322,23 @@ int fpcg_plan_autotune(fpcg_plan* p, const void* H, const void* y, const double*
       c.path = FPCG_PATH_SIMT;
       continue;
     }
+    // candidates: (path, CG warps of the fused kernel); K <= 32 on the fused
+    // kernel tries both six and eight CG warps per CTA
+    int cpath[3], cncg[3], nc = 0;
+    cpath[nc] = cand[0];
+    cncg[nc++] = 0;
+    if (cand[0] == FPCG_PATH_TENSOR_CORE && c.k <= 32) {
+      cncg[0] = 6;
+      cpath[nc] = FPCG_PATH_TENSOR_CORE;
+      cncg[nc++] = 8;
+    }
+    cpath[nc] = FPCG_PATH_SIMT;
+    cncg[nc++] = 0;
     float best = -1.f;
-    int best_path = cand[0];
-    for (int path : cand) {
+    int best_path = cand[0], best_ncg = 0;
+    for (int ci = 0; ci < nc; ++ci) {
+      const int path = cpath[ci];
+      c.ncg = cncg[ci];
       float ms = 0.f;
       for (int rep = 0; rep < 4 && rc == FPCG_OK; ++rep) {  // one warm-up, three timed
         if (rep == 1) cudaEventRecord(e0, s);
@@ -341,10 +359,12 @@ int fpcg_plan_autotune(fpcg_plan* p, const void* H, const void* y, const double*
       if (best < 0.f || ms < best) {
         best = ms;
         best_path = path;
+        best_ncg = cncg[ci];
       }
     }
     if (rc) break;
     c.path = best_path;
+    c.ncg = best_ncg;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

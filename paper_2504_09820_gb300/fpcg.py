@@ -68,7 +68,8 @@ class BatchDesc(ctypes.Structure):
 class ClassInfo(ctypes.Structure):
     _fields_ = [("n_rx", ctypes.c_int32), ("k", ctypes.c_int32), ("block_L", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("first", ctypes.c_int64), ("count", ctypes.c_int64),
-                ("mv", ctypes.c_int32), ("launch", ctypes.c_int32), ("kappa", ctypes.c_double)]
+                ("mv", ctypes.c_int32), ("launch", ctypes.c_int32), ("kappa", ctypes.c_double),
+                ("cg_warps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 PLAN_GRAPH = 1
@@ -455,7 +456,7 @@ class Plan:
         info = (ClassInfo * n.value)()
         _check(lib().fpcg_plan_classes(self._h, ctypes.byref(n), info), "fpcg_plan_classes")
         return [dict(n_rx=c.n_rx, k=c.k, block_L=c.block_L, path=c.path, first=c.first, count=c.count,
-                     mv=FORMAT_NAME[c.mv], kappa=c.kappa, launch=c.launch) for c in info]
+                     mv=FORMAT_NAME[c.mv], kappa=c.kappa, launch=c.launch, cg_warps=c.cg_warps) for c in info]
 
     def autoprec(self, H, y, sigma2, tol=1e-3, stream=None):
         """Per-class matvec format and FP-CG / FP-BJ-CG choice (fpcg_plan_autoprec)."""

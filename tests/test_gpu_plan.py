@@ -101,9 +101,23 @@ def test_graph_replay_and_new_pointers(mixed):
 
 def test_autotune_keeps_results(mixed):
     d, p, g = mixed
+    before = {(c["n_rx"], c["k"]): c for c in p.classes()}
     base = _run(p, g)
     tuned = _run(p, g, autotune=True)
     cls = p.classes()
+    # the CG warps per CTA of the fused kernel: six or eight for K <= 32 (the
+    # autotuner's choice), six at K = 64; a class that stays on the fused
+    # kernel gives the same bits with either (each system's arithmetic is its own)
+    xb0 = p.unpack(base["x"], d["k"])
+    xt0 = p.unpack(tuned["x"], d["k"])
+    for c in cls:
+        if c["path"] == F.PATH_TENSOR_CORE:
+            assert c["cg_warps"] in ((6, 8) if c["k"] <= 32 else (6,)), c
+            if before[(c["n_rx"], c["k"])]["path"] == F.PATH_TENSOR_CORE:
+                idx = p.order[c["first"]:c["first"] + c["count"]]
+                assert all(np.array_equal(xb0[i], xt0[i]) for i in idx), c
+        else:
+            assert c["cg_warps"] == 0, c
     assert all(c["path"] in (F.PATH_SIMT, F.PATH_TENSOR_CORE, F.PATH_TWO_PASS) for c in cls)
     assert all(c["path"] in (F.PATH_SIMT, F.PATH_TWO_PASS) for c in cls if c["k"] in (8, 128))
     # same algorithm on either kernel: within the sum of both kernels' parity bounds
