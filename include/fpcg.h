@@ -112,14 +112,18 @@ enum {
  *                 fl32(A) - A16 (one for fp16: 22 of the 24 significand bits,
  *                 two for bf16: all 24), products exact, fp32 sums, so the
  *                 residual is within about 2^-22 |A||x| of the exact one; the
- *                 SIMT kernel uses compensated double-fp32 products and sums
- *                 (fp64-accurate; GB300's fp64 units are far slower).
+ *                 tensor-core solvers for given Gram matrices (fpcg_solve_gram,
+ *                 fpcg_detect_shared, fpcg_detect_grouped, two-pass plan
+ *                 classes, fpcg_detect_noalloc) read the fp32 A again from
+ *                 global memory and form b - A x with fp32 products and sums
+ *                 (within about (K/32 + 5) u32 |A||x|); the SIMT kernel uses
+ *                 compensated double-fp32 products and sums (fp64-accurate;
+ *                 GB300's fp64 units are far slower).
  *                 FPCG_FP32 = A is the matvec matrix (A rounded to u_MV) and
  *                 the sums are fp32: refinement then removes the CG iteration
- *                 error only, not the rounding of A (cheaper; both kernels,
- *                 and the only mode of the solvers for given Gram matrices'
- *                 tensor-core paths).  rel_res is always the ratio of the two
- *                 norms formed in fp64.  The fp64 mode always uses fp64.
+ *                 error only, not the rounding of A (cheaper; every kernel).
+ *                 rel_res is always the ratio of the two norms formed in fp64.
+ *                 The fp64 mode always uses fp64.
  */
 typedef struct fpcg_precision {
   int32_t gram;
@@ -203,7 +207,7 @@ FPCG_API int fpbjcg_detect(const void* H, const void* y, const double* sigma2, c
  * and status are nullable.  Runs on the tensor-core solver (one warp per
  * system, four for K = 128; A rounded to the matvec format in shared
  * memory) for mv in {BF16,
- * FP16}, w = resid = FP32, K in {8, 16, 32, 64, 128} (K = 8 in 16-wide slots
+ * FP16}, w = FP32, resid in {FP32, FP64}, K in {8, 16, 32, 64, 128} (K = 8 in 16-wide slots
  * holding diag(A, I), b padded with zeros: the same iterates), block_L in {0,
  * 4, 8, 16} and 16-byte aligned A, b; else on the SIMT kernel.
  */
@@ -256,7 +260,7 @@ FPCG_API int fpcg_path(int32_t n_rx, int32_t k, int32_t block_L, const fpcg_prec
  * Gram of its group g = rb_index[s]: its own matched filter b_s = fl(H_g)^H
  * fl(y_s) (eq. inversion, rounded to prec->gram like the Gram), then Algorithm
  * 2 (block_L = 0) or Algorithm 3 (block_L > 0), refinement, slicing, as in
- * fpcg_detect.  Tensor-core modes (w = resid = FP32, mv = BF16 | FP16) with
+ * fpcg_detect.  Tensor-core modes (w = FP32, resid in {FP32, FP64}, mv = BF16 | FP16) with
  * K in {8, 16, 32, 64, 128} and block_L in {0, 4, 8, 16} run on the
  * tensor-core solver: one warp per received vector, the group's 16-bit A and
  * inverted blocks reloaded only when rb_index changes between consecutive
@@ -287,8 +291,8 @@ FPCG_API int fpcg_detect_shared(const void* A, const void* H, const void* y, con
  *   group_start  device [n_groups + 1] int64, non-decreasing, group_start[0] = 0,
  *                group_start[n_groups] = n_rhs (not checked on the device)
  * Runs on the tensor-core solver when K in {8, 16, 32, 64, 128} (8: padded as
- * in fpcg_solve_gram), block_L in {0, 4, 8, 16}, mv in {BF16, FP16}, w = resid
- * = FP32 and A is 16-byte aligned:
+ * in fpcg_solve_gram), block_L in {0, 4, 8, 16}, mv in {BF16, FP16}, w = FP32,
+ * resid in {FP32, FP64} and A is 16-byte aligned:
  * the eight warps of a CTA share one group's A (rounded to the matvec format)
  * and inverted diagonal blocks, and each warp detects one received vector at a
  * time.  Otherwise the SIMT kernel (one CTA per received vector).
@@ -415,7 +419,7 @@ FPCG_API int fpcg_plan_destroy(fpcg_plan* plan);
  * Same arguments and results as fpbjcg_detect (block_L > 0) or fpcg_detect
  * (block_L = 0).  Configurations that run in two passes (Gram matrices first,
  * then the tensor-core solver: K = 8 and K = 128 with a 16-bit matvec, w =
- * resid = FP32, gram in {BF16, FP16}) keep their Gram matrices and matched filters in one
+ * FP32, gram in {BF16, FP16}) keep their Gram matrices and matched filters in one
  * fixed 64 MiB device array of the library; every other configuration takes
  * the ordinary path, which allocates nothing either.
  *   - Limit: batch * K * (K + 1) * 8 bytes <= 64 MiB (K = 128: 508 systems per

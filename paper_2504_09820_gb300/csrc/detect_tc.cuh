@@ -16,7 +16,7 @@ struct DetectTcParams {
   int iters, L, refine_steps, refine_iters, alpha_num, ip;
   int nslots;      // systems in flight per CTA (tc_num_slots)
   int ncg;         // CG warps (tc_cg_warps); the converters are the 10 - ncg warps after them
-  int resid_gram;  // fused kernel: residuals against the fp32 Gram (remainder pieces in global scratch)
+  int resid_gram;  // residuals against the fp32 Gram (fused kernel: remainder pieces in global scratch; solvers: the given A)
   int status_or;   // OR the status bits into status[] instead of storing them (a Gram pass wrote it first)
   float2* x_hat;
   uint8_t* sym;

@@ -81,6 +81,7 @@ void cg_params(fpcg::DetectTcParams& T, const int32_t* qam_order, int32_t iters,
   T.refine_iters = refine_iters;
   T.alpha_num = prec->alpha_num;
   T.ip = prec->ip;
+  T.resid_gram = prec->resid == FPCG_FP64;
   T.x_hat = (float2*)x_hat;
   T.sym = sym_idx;
   T.rel_res = rel_res;
@@ -92,9 +93,12 @@ void cg_params(fpcg::DetectTcParams& T, const int32_t* qam_order, int32_t iters,
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
-// Precisions the CG warp runs: 16-bit matvec, fp32 vectors, residual with the matvec matrix.
+// Precisions the solvers for given Gram matrices run on the tensor cores:
+// 16-bit matvec, fp32 vectors, the residual against the matvec matrix (resid
+// FP32) or the given fp32 Gram matrix (FP64).
 bool tc_prec_ok(const fpcg_precision* p) {
-  return p->w == FPCG_FP32 && p->resid == FPCG_FP32 && (p->mv == FPCG_BF16 || p->mv == FPCG_FP16);
+  return p->w == FPCG_FP32 && (p->resid == FPCG_FP32 || p->resid == FPCG_FP64) &&
+         (p->mv == FPCG_BF16 || p->mv == FPCG_FP16);
 }
 
 }  // namespace

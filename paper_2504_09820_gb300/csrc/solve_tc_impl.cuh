@@ -14,7 +14,9 @@
 // right-hand side is either given or the system's matched filter
 // b = fl(H_g)^H fl(y_s) (eq. inversion; lanes over antennas, four rows of b at
 // a time, warp reductions).  Then CgWarp::detect: Algorithm 2 or 3,
-// refinement, slicing, outputs.
+// refinement, slicing, outputs.  With D.resid_gram the refinement residuals
+// and rel_res use the group's fp32 A itself, read again from global memory
+// (CgWarp RM = 2); else the matvec copy in the slot.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(solve_warps(KR) * 32, 1) solve_tc_kernel(const
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
   const Slot S = slot_carve(base + warp * tc_slot_bytes(K, LT), K, LT);
-  CgWarp<K, BF, LT, KR> W(P.D, S, lane);
+  CgWarp<K, BF, LT, KR, 1, 1, 2> W(P.D, S, lane);
   const int64_t tw = (int64_t)gridDim.x * NW, gw = (int64_t)blockIdx.x * NW + warp;
   const int64_t chunk = (P.n + tw - 1) / tw;
   const int64_t s0 = gw * chunk, s1 = min(P.n, s0 + chunk);
@@ -190,6 +192,7 @@ __global__ void __launch_bounds__(solve_warps(KR) * 32, 1) solve_tc_kernel(const
       fill_A<K, KR, BF, LT>(P.A + (size_t)g * KR * KR, S, lane, 32);
       __syncwarp();
       st_bj = W.bj_setup();
+      W.agram = P.D.resid_gram ? P.A + (size_t)g * KR * KR : nullptr;
       cur = g;
     }
     if (P.b) load_b<K, KR>(P.b + (size_t)s * KR, S, lane);
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(kSplitWarps * kSplitGroups * 32, 1)
   uint8_t* base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
   uint8_t* gbase = base + grp * split_group_bytes(K, LT);
   const Slot S = slot_carve(gbase, K, LT);
-  CgWarp<K, BF, LT, KR, 1, kSplitWarps> W(P.D, S, lane);
+  CgWarp<K, BF, LT, KR, 1, kSplitWarps, 2> W(P.D, S, lane);
   W.sj = sj;
   W.bar_id = 1 + grp;
   W.rst = reinterpret_cast<float2*>(gbase + tc_slot_bytes(K, LT) + sj * sizeof(float2) * K);
@@ -264,6 +267,7 @@ __global__ void __launch_bounds__(kSplitWarps * kSplitGroups * 32, 1)
           prefetch_l2(P.A + (size_t)gn * KR * KR, (uint32_t)(sizeof(float2) * KR * KR));
       }
       st_bj = W.bj_setup();
+      W.agram = P.D.resid_gram ? P.A + (size_t)g * KR * KR : nullptr;
       cur = g;
     }
     if (P.b) {
@@ -305,13 +309,14 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 2) solve_grouped_kernel(cons
   S.W = reinterpret_cast<float2*>(vbase + warp * VST + 8 * K);
   S.Pk = reinterpret_cast<uint32_t*>(vbase + kSolveWarps * VST);
   volatile int* flag = reinterpret_cast<volatile int*>(vbase + kSolveWarps * VST + grouped_pk_bytes(K));
-  CgWarp<K, BF, LT, KR, kSolveWarps> W(P.D, S, lane);
+  CgWarp<K, BF, LT, KR, kSolveWarps, 1, 2> W(P.D, S, lane);
   W.vw = warp;
   W.vbase = vbase;
   W.vst = VST;
   for (int64_t g = blockIdx.x; g < P.n_groups; g += gridDim.x) {
     const int64_t s0 = P.group_start[g], s1 = P.group_start[g + 1];
     if (s1 <= s0) continue;
+    W.agram = P.D.resid_gram ? P.A + (size_t)g * KR * KR : nullptr;
     __syncthreads();  // the previous group's vectors are done with the slot
     fill_A<K, KR, BF, LT>(P.A + (size_t)g * KR * KR, S, threadIdx.x, NT);  // A -> [Re A; Im A], blocks
     if (threadIdx.x == 0) *flag = 0;

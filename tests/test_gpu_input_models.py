@@ -72,7 +72,7 @@ def test_gauss_markov_step_and_kept_gram():
     x = torch.empty((B, K), dtype=torch.complex64, device=dev)
     sym = torch.empty((B, K), dtype=torch.uint8, device=dev)
     gs = torch.arange(B + 1, dtype=torch.int64, device=dev)
-    pk_tc = dict(pk, resid="fp32")   # the grouped solver's tensor-core residual
+    pk_tc = dict(pk)   # the grouped solver's residual against the kept Gram matrix
     F.fpcg_detect_grouped(A, H0, torch.from_numpy(h1["y"]).to(dev), gs, torch.from_numpy(h1["qam"]).to(dev),
                           7, 4, F.precision(**pk_tc), x, sym_idx=sym)
     torch.cuda.synchronize()

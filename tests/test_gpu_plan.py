@@ -149,6 +149,39 @@ def test_two_pass_class_equals_gram_then_solve(mixed):
         assert np.array_equal(xs.cpu().numpy(), np.stack([x[i] for i in idx])), c
 
 
+def test_two_pass_classes_with_the_gram_residual():
+    """resid = FP64 in a plan: the K = 8 and 128 classes still run in two passes
+    (the solver reads the fp32 Gram matrices of the plan's workspace again for
+    its residuals), equal to fpcg_gram + fpcg_solve_gram bit for bit, and agree
+    with the oracle's residual on its Gram matrix."""
+    d = wl.generate_mixed(wl.MixedSpec(batch=300, seed=21))
+    pk = dict(PREC, resid="fp64")
+    p = F.Plan(d["n"], d["k"], ITERS, F.precision(**pk), block_L=L, graph=True)
+    g = p.pack(d["H"], d["y"], d["sigma2"], d["qam"], d["tx"])
+    out = _run(p, g)
+    x = p.unpack(out["x"], d["k"])
+    rel = p.unpack(out["rel"], d["k"], per_system=True)
+    two = [c for c in p.classes() if c["path"] == F.PATH_TWO_PASS]
+    assert {c["k"] for c in two} == {8, 128}
+    for c in two:
+        idx = np.sort(p.order[c["first"]:c["first"] + c["count"]])
+        cd = _class_data(d, idx)
+        t = {k: torch.from_numpy(v).cuda() for k, v in cd.items()}
+        n, K = len(idx), c["k"]
+        A = torch.empty((n, K, K), dtype=torch.complex64, device="cuda")
+        b = torch.empty((n, K), dtype=torch.complex64, device="cuda")
+        F.fpcg_gram(t["H"], t["y"], t["sigma2"], pk["gram"], A, b)
+        xs = torch.empty((n, K), dtype=torch.complex64, device="cuda")
+        rs = torch.empty(n, dtype=torch.float64, device="cuda")
+        F.fpcg_solve_gram(A, b, ITERS, c["block_L"], F.precision(**pk), xs, rel_res=rs)
+        torch.cuda.synchronize()
+        xg = np.stack([x[i] for i in idx])
+        assert np.array_equal(xs.cpu().numpy(), xg), c
+        assert np.array_equal(rs.cpu().numpy(), np.array([rel[i] for i in idx])), c
+        ref = oracle_detect(cd, ITERS, pk, L=c["block_L"])
+        check_reduced_parity(cd, xg, ref["x"], ITERS, pk, L=c["block_L"])
+
+
 def test_fused_classes_share_one_launch(mixed):
     """The one-pass classes of K in {16, 32, 64} (one block size, one set of
     precisions) run in one launch of the fused kernel; the results are those

@@ -227,3 +227,137 @@ def test_grouped_lockstep_independence(K):
     assert np.array_equal(a["x"][others], b["x"][others])
     assert np.array_equal(a["rel"][others], b["rel"][others])
     assert np.all(b["x"][z] == 0) and np.all(b["st"][z] == F.ST_RHO_ZERO)
+
+
+# ---- resid = FP64 on the tensor-core solvers: the residual against the given fp32 A ----
+
+GR = dict(PREC, resid="fp64")
+
+
+def _own_rel(A, b, x):
+    """||b - A x|| / ||b|| in float64 for the given fp32 A, b and the returned
+    x, and the bound of the solvers' fp32 residual on it: per row, 2E fp32
+    multiply-adds in a lane (E = max(1, K/32)), five tree additions and the
+    subtraction from b, so |error| <= (2E + 6) u32 (sum |re|,|im| products + |b|)."""
+    A, b, x = (np.asarray(v, dtype=np.complex128) for v in (A, b, x))
+    K = A.shape[-1]
+    E = max(1, K // 32)
+    r = b - np.einsum("bkl,bl->bk", A, x)
+    nb = np.linalg.norm(b, axis=1)
+    aA = np.abs(A.real) + np.abs(A.imag)
+    ax = np.abs(x.real) + np.abs(x.imag)
+    mag = np.einsum("bkl,bl->bk", aA, ax) + np.abs(b)
+    return np.linalg.norm(r, axis=1) / nb, (2 * E + 6) * 2.0 ** -24 * np.linalg.norm(mag, axis=1) / nb
+
+
+def _solve(A, b, iters, L, pk):
+    n, K = b.shape
+    x = torch.empty((n, K), dtype=torch.complex64, device="cuda")
+    rel = torch.empty(n, dtype=torch.float64, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    F.fpcg_solve_gram(A, b, iters, L, F.precision(**pk), x, rel_res=rel, status=st)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), rel.cpu().numpy(), st.cpu().numpy()
+
+
+@pytest.mark.parametrize("N,K,L,iters", [(64, 8, 4, 6), (128, 16, 0, 12), (256, 64, 8, 6), (512, 128, 8, 6),
+                                         (512, 128, 16, 5)])
+def test_solve_gram_gram_residual(N, K, L, iters, monkeypatch):
+    """fpcg_solve_gram with resid = FP64 on the tensor-core solver (the refinement
+    residual and rel_res against the given fp32 A, read again from global
+    memory): against the oracle with its residual on its own Gram matrix,
+    against the SIMT kernel's compensated residual, and rel_res against
+    b - A x of the returned x in float64 within the fp32 residual's bound."""
+    d = wl.generate(wl.Spec(N=N, K=K, batch=300, rho=0.7, qam=64, snr_db=18.0, seed=13 + K + L))
+    H = torch.from_numpy(d["H"]).cuda()
+    A = torch.empty((300, K, K), dtype=torch.complex64, device="cuda")
+    b = torch.empty((300, K), dtype=torch.complex64, device="cuda")
+    F.fpcg_gram(H, torch.from_numpy(d["y"]).cuda(), torch.from_numpy(d["sigma2"]).cuda(), "bf16", A, b)
+    pk = dict(GR, mv="bf16") if L == 16 else GR
+    x, rel, st = _solve(A, b, iters, L, pk)
+    ref = oracle_detect(d, iters, pk, L=(L or None))
+    check_reduced_parity(d, x, ref["x"], iters, pk, L=(L or None))
+    own, bound = _own_rel(A.cpu().numpy(), b.cpu().numpy(), x)
+    assert np.all(np.abs(rel - own) <= 2e-3 * own + bound), np.max(np.abs(rel - own) / (2e-3 * own + bound))
+    allowed = F.ST_RHO_ZERO | (F.ST_BREAKDOWN if L == K else 0)
+    assert np.all(st & ~allowed == 0)
+    monkeypatch.setenv("FPCG_FORCE_SIMT", "1")
+    xs, _, _ = _solve(A, b, iters, L, pk)
+    e = rel_err(x, xs)
+    assert np.quantile(e, 0.99) < 4e-3 and e.max() < 2e-2
+
+
+@pytest.mark.parametrize("K", [16, 128])
+def test_gram_residual_refines_past_the_matvec_matrix(K):
+    """Converged solves (2K iterations, plain CG, one refinement pass of 2K more):
+    with the residual against the matvec copy of A the refinement stops at the
+    rounding of A to fp16, with the residual against A itself it goes on; b - A x
+    against the given A (float64) is far smaller with resid = FP64."""
+    N = 4 * K
+    d = wl.generate(wl.Spec(N=N, K=K, batch=200, rho=0.5, qam=16, snr_db=20.0, seed=31 + K))
+    H = torch.from_numpy(d["H"]).cuda()
+    A = torch.empty((200, K, K), dtype=torch.complex64, device="cuda")
+    b = torch.empty((200, K), dtype=torch.complex64, device="cuda")
+    F.fpcg_gram(H, torch.from_numpy(d["y"]).cuda(), torch.from_numpy(d["sigma2"]).cuda(), "bf16", A, b)
+    An, bn = A.cpu().numpy(), b.cpu().numpy()
+    x64, rel64, _ = _solve(A, b, 2 * K, 0, GR)
+    x32, _, _ = _solve(A, b, 2 * K, 0, dict(GR, resid="fp32"))
+    own64, bound = _own_rel(An, bn, x64)
+    own32, _ = _own_rel(An, bn, x32)
+    assert np.median(own32) > 10 * np.median(own64), (np.median(own32), np.median(own64))
+    assert np.all(np.abs(rel64 - own64) <= 2e-3 * own64 + bound)
+
+
+@pytest.mark.parametrize("N,K,L", [(64, 16, 4), (256, 64, 8), (64, 8, 0), (512, 128, 8)])
+def test_grouped_gram_residual(N, K, L, monkeypatch):
+    """fpcg_detect_grouped with resid = FP64 on the tensor-core solver (eight
+    vectors in lockstep; each warp forms its own residual from the group's fp32
+    A): against the oracle, the SIMT kernel, and b - A x in float64."""
+    d = wl.generate_rb(wl.RBSpec(N=N, K=K, n_rb=7, res_per_rb=40, seed=190 + K + L))
+    res = _grouped(d, 6, L, GR)
+    pv = _per_vector(d)
+    ref = oracle_detect(pv, 6, GR, L=(L or None))
+    check_reduced_parity(pv, res["x"], ref["x"], 6, GR, L=(L or None))
+    assert int(res["be"][0]) == Q.bit_errors(res["sym"], d["tx"])
+    allowed = F.ST_RHO_ZERO | (F.ST_BREAKDOWN if L == K else 0)
+    assert np.all(res["st"] & ~allowed == 0)
+    # b - A x in float64 with the group's fp32 A as the library forms it and the
+    # exact matched filter of the rounded inputs; the kernel's own b (fp32 sums
+    # on the tensor cores) is not returned, so the check allows three times the
+    # distance of another fp32 summation of b (fpcg_gram per vector) from the exact one
+    n_rb = d["H"].shape[0]
+    A = torch.empty((n_rb, K, K), dtype=torch.complex64, device="cuda")
+    bz = torch.empty((n_rb, K), dtype=torch.complex64, device="cuda")
+    F.fpcg_gram(torch.from_numpy(d["H"]).cuda(), torch.zeros((n_rb, N), dtype=torch.complex64, device="cuda"),
+                torch.from_numpy(d["sigma2"]).cuda(), "bf16", A, bz)
+    A = A.cpu().numpy()[d["rb_index"]]
+    from oracle.formats import flc
+    b = np.einsum("bkn,bn->bk", np.conj(flc(pv["H"], "bf16")), flc(pv["y"], "bf16"))
+    n = len(d["rb_index"])
+    Av = torch.empty((n, K, K), dtype=torch.complex64, device="cuda")
+    bv = torch.empty((n, K), dtype=torch.complex64, device="cuda")
+    F.fpcg_gram(torch.from_numpy(pv["H"]).cuda(), torch.from_numpy(pv["y"]).cuda(),
+                torch.from_numpy(pv["sigma2"]).cuda(), "bf16", Av, bv)
+    del Av
+    db = np.linalg.norm(bv.cpu().numpy() - b, axis=1) / np.linalg.norm(b, axis=1)
+    own, bound = _own_rel(A, b, res["x"])
+    assert np.all(np.abs(res["rel"] - own) <= 2e-3 * own + bound + 3 * db + 1e-7), \
+        np.max(np.abs(res["rel"] - own) - 2e-3 * own - bound - 3 * db)
+    monkeypatch.setenv("FPCG_FORCE_SIMT", "1")
+    simt = _grouped(d, 6, L, GR)
+    e2 = rel_err(res["x"], simt["x"])
+    assert np.quantile(e2, 0.99) < 4e-3 and e2.max() < 2e-2
+
+
+@pytest.mark.parametrize("N,K,L", [(64, 8, 4), (512, 128, 8)])
+def test_shared_gram_residual(N, K, L):
+    """fpcg_detect_shared with resid = FP64 on the tensor-core solver (vectors in
+    random block order: the warps refill their slots and residual matrices)."""
+    d = wl.generate_rb(wl.RBSpec(N=N, K=K, n_rb=6, res_per_rb=30, seed=270 + K))
+    perm = np.random.default_rng(2).permutation(len(d["rb_index"]))
+    d = dict(d, y=d["y"][perm], rb_index=d["rb_index"][perm], qam=d["qam"][perm], tx=d["tx"][perm])
+    res = _shared(d, 6, L, GR)
+    ref = oracle_detect(_per_vector(d), 6, GR, L=L)
+    check_reduced_parity(_per_vector(d), res["x"], ref["x"], 6, GR, L=L)
+    assert int(res["be"][0]) == Q.bit_errors(res["sym"], d["tx"])
+    assert np.all(res["st"] & ~F.ST_RHO_ZERO == 0)

@@ -28,40 +28,44 @@ def _data(N, K, B, seed):
     return d, {k: torch.from_numpy(d[k]).cuda() for k in ("H", "y", "sigma2", "qam", "tx")}
 
 
-def _noalloc(g, K, L, iters=6):
+def _noalloc(g, K, L, iters=6, pk=PREC):
     B = g["H"].shape[0]
     out = {"x": torch.empty((B, K), dtype=torch.complex64, device="cuda"),
            "sym": torch.empty((B, K), dtype=torch.uint8, device="cuda"),
            "rel": torch.empty(B, dtype=torch.float64, device="cuda"),
            "st": torch.full((B,), 7, dtype=torch.int32, device="cuda"),
            "be": torch.zeros(1, dtype=torch.int64, device="cuda")}
-    F.fpcg_detect_noalloc(g["H"], g["y"], g["sigma2"], g["qam"], iters, L, F.precision(**PREC), out["x"],
+    F.fpcg_detect_noalloc(g["H"], g["y"], g["sigma2"], g["qam"], iters, L, F.precision(**pk), out["x"],
                           sym_idx=out["sym"], rel_res=out["rel"], tx_idx=g["tx"], bit_errors=out["be"],
                           status=out["st"])
     torch.cuda.synchronize()
     return {k: v.cpu() for k, v in out.items()}
 
 
-def _gram_then_solve(g, K, L):
+def _gram_then_solve(g, K, L, pk=PREC):
     B = g["H"].shape[0]
     A = torch.empty((B, K, K), dtype=torch.complex64, device="cuda")
     b = torch.empty((B, K), dtype=torch.complex64, device="cuda")
     F.fpcg_gram(g["H"], g["y"], g["sigma2"], "bf16", A, b)
     x = torch.empty((B, K), dtype=torch.complex64, device="cuda")
     rel = torch.empty(B, dtype=torch.float64, device="cuda")
-    F.fpcg_solve_gram(A, b, 6, L, F.precision(**PREC), x, rel_res=rel)
+    F.fpcg_solve_gram(A, b, 6, L, F.precision(**pk), x, rel_res=rel)
     torch.cuda.synchronize()
     return x.cpu(), rel.cpu()
 
 
+@pytest.mark.parametrize("resid", ["fp32", "fp64"])
 @pytest.mark.parametrize("N,K,L", [(256, 128, 8), (64, 8, 4)])
-def test_two_calls_equal_gram_then_solve(N, K, L):
+def test_two_calls_equal_gram_then_solve(N, K, L, resid):
+    """resid = "fp64": the solve's residual against the Gram matrix in the
+    library's array (read again by the solver)."""
+    pk = dict(PREC, resid=resid)
     d, g = _data(N, K, 200, 41)
-    first = _noalloc(g, K, L)
-    second = _noalloc(g, K, L)
+    first = _noalloc(g, K, L, pk=pk)
+    second = _noalloc(g, K, L, pk=pk)
     for k in first:
         assert torch.equal(first[k], second[k]), k
-    x, rel = _gram_then_solve(g, K, L)
+    x, rel = _gram_then_solve(g, K, L, pk=pk)
     assert torch.equal(first["x"], x) and torch.equal(first["rel"], rel)
     assert np.array_equal(Q.slice_symbols(first["x"].numpy(), 64, "fp32"), first["sym"].numpy())
     assert int(first["be"][0]) == Q.bit_errors(first["sym"].numpy(), d["tx"])
