@@ -196,8 +196,9 @@ __device__ __noinline__ float round_ip(float v, int fmt) { return round_to(v, fm
 //
 // RM = 2: a residual trip reads the fp32 Gram matrix itself from global
 // memory (`agram`, KR x KR row-major; skipped while agram is null): b - A x
-// with x in fp32, fp32 products and sums (apply_gram), within about
-// (KR/32 + 5) u32 |A||x| of the exact residual.  For the solvers of given
+// with x in fp32, fp32 products and sums (apply_gram), within
+// (2E + 6) u32 (|A||x| + |b|) of the exact residual; NV = 8: one CTA-wide pass
+// over A for the eight vectors (apply_gram_cta).  For the solvers of given
 // Gram matrices, which keep no remainder pieces.
 //
 // F8 = 1 (with BF, NV = NS = 1): the matvec of a CG iteration runs in e4m3
@@ -660,66 +661,12 @@ struct CgWarp {
     }
   }
 
-  // RM = 2: W = b - A x from the fp32 Gram matrix in global memory, then
-  // w = W (x arrives in w).  Lane j holds x_j (j = lane + 32e), so the loads of
-  // one row are coalesced.  RB rows at a time: every lane sums its columns'
-  // products, then log2(RB) exchange steps (lane distance 16, 8, ...) each
-  // keep half of the rows and hand the other half to the partner lane, so
-  // that row i0 + r, r = the top log2(RB) bits of the lane, ends up summed
-  // over RB lanes, and plain shuffles add the remaining 32 / RB.  RB = 4 for
-  // K = 128 (fewer loads in flight, fewer registers).  NS > 1: the row blocks
-  // are split over the warps of the system.  Padding rows (KR..K-1) are zero.
-  __device__ __forceinline__ void apply_gram(float2 (&w)[E]) {
-    constexpr int RB = E >= 4 ? 4 : 8;   // rows per block
-    constexpr int LB = RB == 8 ? 3 : 2;  // exchange steps
-    constexpr int GU = E <= 2 ? 2 : 1;   // row blocks whose loads are in flight together
-    gsync();  // NS > 1: every warp has read the previous trip's W
-    const int r = lane >> (5 - LB);
-#pragma unroll GU
-    for (int i0 = RB * sj; i0 < KR; i0 += RB * NS) {
-      float re[RB], im[RB];
-#pragma unroll
-      for (int u = 0; u < RB; ++u) re[u] = im[u] = 0.f;
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int j = lane + 32 * e;
-        if (j < KR) {
-          const float2 xv = w[e];
-#pragma unroll
-          for (int u = 0; u < RB; ++u) {
-            const float2 a = __ldg(agram + (size_t)(i0 + u) * KR + j);
-            re[u] = fmaf(a.x, xv.x, fmaf(-a.y, xv.y, re[u]));
-            im[u] = fmaf(a.x, xv.y, fmaf(a.y, xv.x, im[u]));
-          }
-        }
-      }
-#pragma unroll
-      for (int h = RB / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {  // keep h of 2h rows, send the others
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int u = 0; u < h; ++u) {
-          const float sr = up ? re[u] : re[u + h], si = up ? im[u] : im[u + h];
-          const float kr = up ? re[u + h] : re[u], ki = up ? im[u + h] : im[u];
-          re[u] = kr + __shfl_xor_sync(0xffffffffu, sr, o);
-          im[u] = ki + __shfl_xor_sync(0xffffffffu, si, o);
-        }
-      }
-#pragma unroll
-      for (int o = 16 >> LB; o > 0; o >>= 1) {
-        re[0] += __shfl_xor_sync(0xffffffffu, re[0], o);
-        im[0] += __shfl_xor_sync(0xffffffffu, im[0], o);
-      }
-      if ((lane & ((32 >> LB) - 1)) == 0) {
-        const float2 bv = S.b[i0 + r];
-        S.W[i0 + r] = make_float2(bv.x - re[0], bv.y - im[0]);
-      }
-    }
-    __syncwarp();
-    gsync();  // NS > 1: every row block of W is written
-#pragma unroll
-    for (int e = 0; e < E; ++e) w[e] = vout(e) ? S.W[lane + 32 * e] : make_float2(0.f, 0.f);
-    __syncwarp();
-  }
+  // RM = 2: W = b - A x from the fp32 Gram matrix in global memory, then w = W
+  // (x arrives in w); one warp (NS warps) per system, or (NV = 8) one
+  // CTA-wide pass for the eight vectors.  Defined in gram_resid.cuh, which
+  // the solvers for given Gram matrices include.
+  __device__ __forceinline__ void apply_gram(float2 (&w)[E]);
+  __device__ __forceinline__ void apply_gram_cta(float2 (&w)[E]);
 
   // W = A v (res = false) or W = b - A v (res = true: the three column pairs
   // of v are summed), one m-tile (16 rows of Re A and of Im A) at a time; lane
@@ -729,7 +676,8 @@ struct CgWarp {
   __device__ __forceinline__ void apply(bool res, float2 (&w)[E], bool last = false) {
     if constexpr (RM == 2)
       if (res && agram != nullptr) {  // the same on every warp of a CTA (NV > 1) or system (NS > 1)
-        apply_gram(w);
+        if constexpr (NV > 1) apply_gram_cta(w);
+        else apply_gram(w);
         return;
       }
     if constexpr (NV > 1) {

@@ -22,6 +22,7 @@
 
 #include "cg_warp.cuh"
 #include "common.cuh"
+#include "gram_resid.cuh"
 #include "solve_tc.cuh"
 
 namespace fpcg {
