@@ -107,3 +107,23 @@ def check_reduced_parity(d, x_gpu, x_ref, iters, prec_kw, L=None, sel=None, tol=
                 break
         assert np.all(best <= bar), ("max", e[out], best, sp.max(), idx)
     return e, sp
+
+
+def gram_resid_rel(A, b, x):
+    """||b - A x|| / ||b|| in float64 for fp32 A, b and a returned x, and the
+    bound on how far the solvers' fp32 residual against a given Gram matrix
+    (resid = FP64 on the tensor-core solvers) may move it: per row, 2E fp32
+    multiply-adds in a lane (E = max(1, K/32)), five pairwise tree additions
+    over the lanes and the subtraction from b, so each of Re and Im of the
+    residual is off by at most (2E + 6) u32 times the sum of the magnitudes of
+    its terms; in norm, (2E + 6) u32 || (|Re A| + |Im A|)(|Re x| + |Im x|)
+    + |Re b| + |Im b| || / ||b||."""
+    A, b, x = (np.asarray(v, dtype=np.complex128) for v in (A, b, x))
+    K = A.shape[-1]
+    E = max(1, K // 32)
+    r = b - np.einsum("bkl,bl->bk", A, x)
+    nb = np.linalg.norm(b, axis=1)
+    aA = np.abs(A.real) + np.abs(A.imag)
+    ax = np.abs(x.real) + np.abs(x.imag)
+    mag = np.einsum("bkl,bl->bk", aA, ax) + np.abs(b.real) + np.abs(b.imag)
+    return np.linalg.norm(r, axis=1) / nb, (2 * E + 6) * 2.0 ** -24 * np.linalg.norm(mag, axis=1) / nb

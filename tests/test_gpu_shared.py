@@ -8,7 +8,7 @@ from oracle import qam as Q
 from paper_2504_09820_gb300 import fpcg as F
 from paper_2504_09820_gb300 import workload as wl
 
-from gpu_helpers import check_reduced_parity, oracle_detect, rel_err
+from gpu_helpers import check_reduced_parity, gram_resid_rel, oracle_detect, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -234,22 +234,6 @@ def test_grouped_lockstep_independence(K):
 GR = dict(PREC, resid="fp64")
 
 
-def _own_rel(A, b, x):
-    """||b - A x|| / ||b|| in float64 for the given fp32 A, b and the returned
-    x, and the bound of the solvers' fp32 residual on it: per row, 2E fp32
-    multiply-adds in a lane (E = max(1, K/32)), five tree additions and the
-    subtraction from b, so |error| <= (2E + 6) u32 (sum |re|,|im| products + |b|)."""
-    A, b, x = (np.asarray(v, dtype=np.complex128) for v in (A, b, x))
-    K = A.shape[-1]
-    E = max(1, K // 32)
-    r = b - np.einsum("bkl,bl->bk", A, x)
-    nb = np.linalg.norm(b, axis=1)
-    aA = np.abs(A.real) + np.abs(A.imag)
-    ax = np.abs(x.real) + np.abs(x.imag)
-    mag = np.einsum("bkl,bl->bk", aA, ax) + np.abs(b)
-    return np.linalg.norm(r, axis=1) / nb, (2 * E + 6) * 2.0 ** -24 * np.linalg.norm(mag, axis=1) / nb
-
-
 def _solve(A, b, iters, L, pk):
     n, K = b.shape
     x = torch.empty((n, K), dtype=torch.complex64, device="cuda")
@@ -277,7 +261,7 @@ def test_solve_gram_gram_residual(N, K, L, iters, monkeypatch):
     x, rel, st = _solve(A, b, iters, L, pk)
     ref = oracle_detect(d, iters, pk, L=(L or None))
     check_reduced_parity(d, x, ref["x"], iters, pk, L=(L or None))
-    own, bound = _own_rel(A.cpu().numpy(), b.cpu().numpy(), x)
+    own, bound = gram_resid_rel(A.cpu().numpy(), b.cpu().numpy(), x)
     assert np.all(np.abs(rel - own) <= 2e-3 * own + bound), np.max(np.abs(rel - own) / (2e-3 * own + bound))
     allowed = F.ST_RHO_ZERO | (F.ST_BREAKDOWN if L == K else 0)
     assert np.all(st & ~allowed == 0)
@@ -302,8 +286,8 @@ def test_gram_residual_refines_past_the_matvec_matrix(K):
     An, bn = A.cpu().numpy(), b.cpu().numpy()
     x64, rel64, _ = _solve(A, b, 2 * K, 0, GR)
     x32, _, _ = _solve(A, b, 2 * K, 0, dict(GR, resid="fp32"))
-    own64, bound = _own_rel(An, bn, x64)
-    own32, _ = _own_rel(An, bn, x32)
+    own64, bound = gram_resid_rel(An, bn, x64)
+    own32, _ = gram_resid_rel(An, bn, x32)
     assert np.median(own32) > 10 * np.median(own64), (np.median(own32), np.median(own64))
     assert np.all(np.abs(rel64 - own64) <= 2e-3 * own64 + bound)
 
@@ -340,7 +324,7 @@ def test_grouped_gram_residual(N, K, L, monkeypatch):
                 torch.from_numpy(pv["sigma2"]).cuda(), "bf16", Av, bv)
     del Av
     db = np.linalg.norm(bv.cpu().numpy() - b, axis=1) / np.linalg.norm(b, axis=1)
-    own, bound = _own_rel(A, b, res["x"])
+    own, bound = gram_resid_rel(A, b, res["x"])
     assert np.all(np.abs(res["rel"] - own) <= 2e-3 * own + bound + 3 * db + 1e-7), \
         np.max(np.abs(res["rel"] - own) - 2e-3 * own - bound - 3 * db)
     monkeypatch.setenv("FPCG_FORCE_SIMT", "1")
