@@ -17,9 +17,12 @@ def _lib():
 PREC = dict(gram="bf16", mv="fp16", refine_steps=1)
 
 
-def test_layout_invariants():
+@pytest.mark.parametrize("resid", ["fp32", "fp64"])
+def test_layout_invariants(resid):
+    """resid = "fp64" (the residual against the Gram matrix) keeps the same
+    paths: the K = 8 and 128 classes run in two passes on the tensor cores."""
     n, k, _, _ = wl.mixed_params(wl.MixedSpec(batch=500, seed=7))
-    p = F.Plan(n, k, 6, F.precision(**PREC), block_L=8)
+    p = F.Plan(n, k, 6, F.precision(**PREC, resid=resid), block_L=8)
     # order is a permutation that groups by (K, N), caller order kept inside a class
     assert sorted(p.order.tolist()) == list(range(500))
     keys = [(int(k[i]), int(n[i])) for i in p.order]
